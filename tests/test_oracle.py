@@ -1,0 +1,381 @@
+"""Pins for the CPU oracle (oracle/chp.c) against things other than itself:
+Pauli matrix algebra, unitary conjugation, brute-force statevector simulation,
+closed-form circuits, tableau invariants and the noiseless surface-code
+detectors.  No GPU."""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_03092_gb300 import circuit as C
+from paper_2507_03092_gb300 import streams as S
+from tests import statevec as SV
+
+P_OF = {(0, 0): "I", (1, 0): "X", (1, 1): "Y", (0, 1): "Z"}
+
+
+def pauli_matrix(bits):
+    return SV.MAT[P_OF[bits]]
+
+
+# ---------------------------------------------------------------- g, f, phase
+
+def test_g_is_power_of_i_in_pauli_products():
+    """Appendix B: g(x1,z1,x2,z2) is the exponent e with P1 P2 = i^e P3."""
+    for x1, z1, x2, z2 in itertools.product((0, 1), repeat=4):
+        e = oracle.g(x1, z1, x2, z2)
+        lhs = pauli_matrix((x1, z1)) @ pauli_matrix((x2, z2))
+        rhs = (1j ** e) * pauli_matrix((x1 ^ x2, z1 ^ z2))
+        assert np.allclose(lhs, rhs), (x1, z1, x2, z2, e)
+        assert e in (-1, 0, 1)
+
+
+def test_alg1_phase_polynomial_equals_g():
+    """Alg. 1's branch-free polynomial is the same function as g."""
+    def f(xp, zp, xh, zh):
+        return xp * (zp * (zh - xh) + (1 - zp) * zh * (2 * xh - 1)) + (1 - xp) * zp * xh * (1 - 2 * zh)
+    for args in itertools.product((0, 1), repeat=4):
+        assert f(*args) == oracle.g(*args)
+
+
+def test_word_parallel_phase_identity():
+    """sum_j g over packed words == popc(x1&z1)+popc(x2&z2)+2popc(z1&x2)-popc(x3&z3)
+    (mod 4): the identity the CUDA rowsum uses, checked on random words."""
+    rng = np.random.default_rng(1)
+    pc = lambda v: bin(v).count("1")
+    for _ in range(300):
+        x1, z1, x2, z2 = (int(v) for v in rng.integers(0, 2 ** 63, 4))
+        ref = sum(oracle.g((x1 >> j) & 1, (z1 >> j) & 1, (x2 >> j) & 1, (z2 >> j) & 1)
+                  for j in range(63))
+        got = pc(x1 & z1) + pc(x2 & z2) + 2 * pc(z1 & x2) - pc((x1 ^ x2) & (z1 ^ z2))
+        assert (ref - got) % 4 == 0
+
+
+def test_ordered_product_closed_form():
+    """Sign of an ordered product of commuting Paulis from the closed form
+    2 sum r + sum popc(x_b&z_b) + 2 sum_{a<b} popc(z_a&x_b) - popc(X&Z) equals
+    the sign obtained by multiplying the matrices (brute force, 3 qubits)."""
+    rng = np.random.default_rng(7)
+    pc = lambda v: bin(v).count("1")
+    nq = 3
+
+    def mat(x, z, r):
+        M = np.array([[1.0 + 0j]])
+        for j in reversed(range(nq)):
+            M = np.kron(M, pauli_matrix(((x >> j) & 1, (z >> j) & 1)))
+        return (-1) ** r * M
+
+    for _ in range(200):
+        k = int(rng.integers(1, 5))
+        rows = [(int(rng.integers(0, 8)), int(rng.integers(0, 8)), int(rng.integers(0, 2)))
+                for _ in range(k)]
+        prod = np.eye(2 ** nq, dtype=complex)
+        for x, z, r in rows:
+            prod = prod @ mat(x, z, r)
+        X = Z = 0
+        e = 0
+        for b, (x, z, r) in enumerate(rows):
+            e += 2 * r + pc(x & z)
+            for a in range(b):
+                e += 2 * pc(rows[a][1] & x)
+            X ^= x
+            Z ^= z
+        e -= pc(X & Z)
+        assert np.allclose(prod, (1j ** e) * mat(X, Z, 0))
+
+
+# ---------------------------------------------------------------- gate rules
+
+def _gate_unitary(kind):
+    U = np.zeros((4, 4), dtype=complex)
+    for col in range(4):
+        sv = SV.StateVector(2)
+        sv.psi[:] = 0
+        sv.psi[col] = 1
+        if kind in (C.H, C.S, C.X, C.Y, C.Z):
+            sv.apply1(SV.MAT[C.KIND_NAMES[kind]], 0)
+        elif kind == C.CX:
+            sv.apply_cx(0, 1)
+        elif kind == C.CZ:
+            sv.apply_cz(0, 1)
+        elif kind == C.SWAP:
+            sv.apply_swap(0, 1)
+        U[:, col] = sv.psi
+    return U
+
+
+def _row_matrix(x, z, r):
+    # qubit 1 is the more significant tensor factor
+    return (-1) ** r * np.kron(pauli_matrix((int(x[1]), int(z[1]))),
+                               pauli_matrix((int(x[0]), int(z[0]))))
+
+
+@pytest.mark.parametrize("kind", [C.H, C.S, C.X, C.Y, C.Z, C.CX, C.CZ, C.SWAP])
+def test_gate_rule_is_conjugation(kind):
+    """Each tableau gate rule maps every signed 2-qubit Pauli P to U P U^dag
+    (Sec. 2.4 Table; derived gates checked the same way)."""
+    n = 16                            # 32 rows: every Pauli on qubits 0,1, both signs
+    t = oracle.Tableau(n)
+    x = np.zeros((2 * n, t.W), np.uint64)
+    z = np.zeros((2 * n, t.W), np.uint64)
+    r = np.zeros(2 * n, np.uint8)
+    combos = list(itertools.product((0, 1), repeat=5))
+    for i, (x0, z0, x1, z1, s) in enumerate(combos):
+        x[i, 0] = x0 | (x1 << 1)
+        z[i, 0] = z0 | (z1 << 1)
+        r[i] = s
+    t.set(x, z, r)
+    b = C.Builder(n)
+    if kind in C.TWO_QUBIT_GATES:
+        b.gate2(kind, 0, 1)
+    else:
+        b.gate1(kind, 0)
+    t.run(b.build())
+    x2, z2, r2 = t.get()
+    U = _gate_unitary(kind)
+    for i, (x0, z0, x1, z1, s) in enumerate(combos):
+        want = U @ _row_matrix((x0, x1), (z0, z1), s) @ U.conj().T
+        xb = [int(x2[i, 0]) & 1, (int(x2[i, 0]) >> 1) & 1]
+        zb = [int(z2[i, 0]) & 1, (int(z2[i, 0]) >> 1) & 1]
+        got = _row_matrix(xb, zb, int(r2[i]))
+        assert np.allclose(want, got), (C.KIND_NAMES[kind], (x0, z0, x1, z1, s))
+        assert int(x2[i, 0]) >> 2 == 0 and int(z2[i, 0]) >> 2 == 0
+
+
+# ---------------------------------------------------------------- statevector
+
+def _streams(c, seed, shot=0):
+    return (S.coin_words(seed, [shot], c.coin_words)[0],
+            S.noise_words(seed, [shot], c.noise_words)[0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7])
+def test_oracle_matches_statevector(n):
+    """Records equal the brute-force statevector's for the same coins and
+    noise draws; random/deterministic agreement is forced by using two
+    different coin streams per circuit."""
+    for seed in range(40 if n <= 4 else 15):
+        circ = C.random_small_circuit(n, 40, seed=seed + 100 * n)
+        for cs in (seed, seed + 1000):
+            coins, noise = _streams(circ, cs)
+            rec = oracle.run(circ, coins, noise)
+            bits = oracle.record_bits(rec, circ.n_meas).tolist()
+            sv_bits, _ = SV.run(circ, coins, noise)
+            assert bits == sv_bits, (n, seed, cs)
+
+
+def test_random_outcomes_have_probability_half():
+    """Every measurement the statevector finds random has p = 1/2 exactly,
+    deterministic ones p in {0, 1} (asserted inside SV.measure); and the
+    oracle's record follows the coin exactly for the random ones."""
+    circ = C.random_small_circuit(6, 60, seed=5, noise=False)
+    coins0 = np.zeros(circ.coin_words, np.uint64)
+    coins1 = np.full(circ.coin_words, np.uint64(2 ** 64 - 1))
+    r0 = oracle.record_bits(oracle.run(circ, coins0), circ.n_meas)
+    r1 = oracle.record_bits(oracle.run(circ, coins1), circ.n_meas)
+    _, rnd = SV.run(circ, coins0, np.zeros(1, np.uint32))
+    m_flags = [r for (k, r) in rnd if int(circ.ops[k]["kind"]) == C.M]
+    assert len(m_flags) == circ.n_meas
+    # the first random M follows its coin; before it, records agree
+    first = next((i for i, f in enumerate(m_flags) if f), None)
+    if first is not None:
+        assert (r0[:first] == r1[:first]).all()
+        assert r0[first] == 0 and r1[first] == 1
+
+
+# ---------------------------------------------------------------- invariants
+
+def _symplectic_ok(x, z, n):
+    W = x.shape[1]
+    xb = np.unpackbits(x.view(np.uint8).reshape(2 * n, 8 * W), axis=1, bitorder="little")[:, :n].astype(np.int64)
+    zb = np.unpackbits(z.view(np.uint8).reshape(2 * n, 8 * W), axis=1, bitorder="little")[:, :n].astype(np.int64)
+    inner = (xb @ zb.T + zb @ xb.T) % 2
+    J = np.zeros((2 * n, 2 * n), np.int64)
+    J[np.arange(n), np.arange(n) + n] = 1
+    J[np.arange(n) + n, np.arange(n)] = 1
+    return np.array_equal(inner, J)
+
+
+def test_invariants_after_every_op():
+    """D_i anticommutes with S_i only; all other pairs commute (this also
+    implies the 2n rows are independent) -- after every single op."""
+    for seed in range(6):
+        n = 9
+        circ = C.random_small_circuit(n, 80, seed=seed)
+        coins, noise = _streams(circ, seed)
+        t = oracle.Tableau(n)
+        ci = li = 0
+        for k in range(len(circ.ops)):
+            one = C.Circuit(n, circ.ops[k:k + 1], circ.params)
+            kind = int(circ.ops[k]["kind"])
+            c1 = np.array([(int(coins[ci >> 6]) >> (ci & 63)) & 1], np.uint64)
+            nw = 3 if kind == C.RESET_ERR else 1
+            n1 = np.array(noise[li:li + nw] if kind in C.NOISE_KINDS else [0], np.uint32)
+            t.run(one, c1, n1)
+            ci += kind in (C.M, C.R)
+            li += nw if kind in C.NOISE_KINDS else 0
+            x, z, _ = t.get()
+            assert _symplectic_ok(x, z, n), (seed, k, C.KIND_NAMES[kind])
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_ghz_outcomes_equal_first_coin():
+    for n in (2, 5, 33, 70):
+        c = C.ghz(n)
+        for coin in (0, 1):
+            rec = oracle.run(c, np.array([coin], np.uint64) if c.coin_words == 1 else
+                             np.array([coin] + [0] * (c.coin_words - 1), np.uint64))
+            bits = oracle.record_bits(rec, n)
+            assert (bits == coin).all()
+
+
+def test_single_qubit_closed_forms():
+    b = C.Builder(3)
+    b.measure(0)                     # |0> -> 0 deterministic
+    b.gate1(C.X, 1).measure(1)       # X|0> -> 1
+    b.gate1(C.H, 2).measure(2)       # |+> -> coin
+    b.reset(1).measure(1)            # reset -> 0
+    b.gate1(C.H, 0).gate1(C.S, 0).gate1(C.S, 0).gate1(C.H, 0).measure(0)  # HSSH = X
+    c = b.build()
+    for coins in (0b000000, 0b111111):
+        bits = oracle.record_bits(oracle.run(c, np.array([coins], np.uint64)), c.n_meas)
+        assert bits.tolist() == [0, 1, coins & 1, 0, 1]
+
+
+def test_gate_identities_on_tableau():
+    """S^4 = I, H^2 = I, CX^2 = I leave the tableau bit-identical."""
+    circ = C.random_small_circuit(5, 30, seed=3, noise=False, allow=(C.H, C.S, C.CX, C.CZ))
+    t = oracle.Tableau(5)
+    t.run(circ)
+    ref = t.get()
+    b = C.Builder(5)
+    for _ in range(4):
+        b.gate1(C.S, 2)
+    b.gate1(C.H, 1).gate1(C.H, 1).gate2(C.CX, 3, 4).gate2(C.CX, 3, 4)
+    t.run(b.build())
+    for u, v in zip(ref, t.get()):
+        assert np.array_equal(u, v)
+
+
+# ---------------------------------------------------------------- surface code
+
+@pytest.mark.parametrize("d,rounds", [(3, 1), (3, 3), (5, 2), (5, 5), (7, 7)])
+def test_surface_code_noiseless_detectors_zero(d, rounds):
+    c = C.surface_code_memory(d, rounds)
+    for seed in (0, 1):
+        coins, noise = _streams(c, seed)
+        bits = oracle.record_bits(oracle.run(c, coins, noise), c.n_meas)
+        for det in c.meta["detectors"]:
+            assert int(np.bitwise_xor.reduce(bits[det])) == 0
+        assert int(np.bitwise_xor.reduce(bits[c.meta["observable"]])) == 0
+
+
+def test_surface_code_counts():
+    for d in (3, 5, 11):
+        c = C.surface_code_memory(d)
+        cnt = c.counts()
+        assert c.n == 2 * d * d - 1
+        assert cnt["CX"] == 4 * d * (d - 1) * d
+        assert cnt["H"] == (d * d - 1) * d
+        assert cnt["M"] == (d * d - 1) * d + d * d
+        assert len(c.meta["layout"].x_anc) == len(c.meta["layout"].z_anc) == (d * d - 1) // 2
+
+
+def test_noisy_surface_code_flags_errors():
+    c = C.surface_code_memory(5, p=0.02)
+    coins, noise = _streams(c, 3)
+    bits = oracle.record_bits(oracle.run(c, coins, noise), c.n_meas)
+    nz = sum(int(np.bitwise_xor.reduce(bits[det])) for det in c.meta["detectors"])
+    assert nz > 0
+
+
+# ---------------------------------------------------------------- noise draws
+
+@pytest.mark.parametrize("p", [0.0, 1e-9, 1e-3, 1 / 3, 0.5, 0.999999, 1.0])
+def test_threshold_is_exact_floor(p):
+    want = min(int(Fraction(p) * 2 ** 32), 2 ** 32)
+    assert SV.threshold(p) == want
+
+
+def test_noise_draw_boundaries():
+    """An X error before M flips the outcome; the event test is u < T."""
+    for p in (1e-3, 0.3):
+        T = SV.threshold(p)
+        b = C.Builder(1)
+        b.pauli_channel1(0, p, 0.0, 0.0).measure(0)
+        c = b.build()
+        for u, want in ((0, 1), (T - 1, 1), (T, 0), (2 ** 32 - 1, 0)):
+            bits = oracle.record_bits(oracle.run(c, np.zeros(1, np.uint64),
+                                                 np.array([u], np.uint32)), 1)
+            assert int(bits[0]) == want, (p, u)
+
+
+def test_depolarize_index_nearly_uniform():
+    T = SV.threshold(1e-3)
+    for K in (3, 15):
+        counts = np.bincount([(u * K) // T for u in range(0, T, 997)], minlength=K)
+        assert counts.max() - counts.min() <= 2 + counts.max() // 1000
+
+
+# ---------------------------------------------------------------- errors
+
+def test_oracle_rejects_bad_input():
+    b = C.Builder(2)
+    b.gate2(C.CX, 0, 0)
+    with pytest.raises(oracle.OracleError):
+        oracle.run(b.build())
+    b = C.Builder(2)
+    b.gate1(C.H, 5)
+    with pytest.raises(oracle.OracleError):
+        oracle.run(b.build())
+    b = C.Builder(2)
+    for _ in range(70):
+        b.measure(0)
+    c = b.build()
+    with pytest.raises(oracle.OracleError):
+        t = oracle.Tableau(2)
+        t.run(c, np.zeros(1, np.uint64))     # 70 coin slots need 2 words
+
+
+def test_sample_threads_match_single():
+    c = C.surface_code_memory(3, p=0.05)
+    coins, noise = S.streams_for(c, 0, range(64))
+    r1, _ = oracle.sample(c, coins, noise, threads=1)
+    r4, _ = oracle.sample(c, coins, noise, threads=4)
+    assert np.array_equal(r1, r4)
+    for s in (0, 17, 63):
+        assert np.array_equal(r1[s], oracle.run(c, coins[s], noise[s]))
+
+
+# ---------------------------------------------------------------- generators
+
+def test_splitmix64_published_first_output():
+    # SplitMix64 with state 0: first output 0xE220A8397B1DCDAF
+    assert int(S.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+    assert int(S.splitmix64(0, 2)[1]) == S.mix64_int(2 * S.GAMMA)
+
+
+def test_streams_are_keyed_by_shot():
+    a = S.coin_words(0, [0, 1, 2], 4)
+    b = S.coin_words(0, [2], 4)
+    assert np.array_equal(a[2], b[0])
+    assert not np.array_equal(a[0], a[1])
+
+
+def test_random_measurement_moves_pivot_row_to_destabilizer():
+    """Sec. 2.4: after a random measurement the old pivot stabilizer (sign
+    included) is stored in its destabilizer and the pivot becomes +-Z_a.
+    Worked by hand: H then Z on |0> gives D=Z, S=-X; measuring gives D=-X,
+    S=(-1)^coin Z."""
+    b = C.Builder(1)
+    b.gate1(C.H, 0).gate1(C.Z, 0).measure(0)
+    c = b.build()
+    for coin in (0, 1):
+        t = oracle.Tableau(1)
+        t.run(c, np.array([coin], np.uint64))
+        x, z, r = t.get()
+        assert (int(x[0, 0]), int(z[0, 0]), int(r[0])) == (1, 0, 1)
+        assert (int(x[1, 0]), int(z[1, 0]), int(r[1])) == (0, 1, coin)
