@@ -1,0 +1,228 @@
+/*
+ * stab.h -- C ABI of libstab.so, a GB300 (sm_103a) CHP stabilizer-tableau
+ * simulator (arXiv 2507.03092, "STABSim", hot path).
+ *
+ * All arithmetic is exact GF(2) / mod-4 integer work.  Every entry point
+ * returns STAB_OK (0) or a negative STAB_ERR_* code; nothing is thrown across
+ * the ABI.  stab_last_error() returns a thread-local message for the last
+ * failing call on the calling thread.  Host-side validation (qubit indices,
+ * distinct 2-qubit operands, stream lengths, sizes) happens before any launch.
+ *
+ * Ownership: buffers passed in are owned by the caller (device buffers are
+ * typically torch tensors); the library owns only its contexts, compiled
+ * circuits and tableau storage.  Launches are asynchronous on the context's
+ * CUDA stream and stream-ordered with the caller's work on that stream;
+ * stab_sync() waits for them and reports device-side error flags.
+ *
+ * Conventions shared with the CPU oracle (each side implements them itself):
+ *  - Tableau (Sec. 2.3, "The CHP Formalism"): 2n rows, rows 0..n-1
+ *    destabilizers, n..2n-1 stabilizers, each x[0..n), z[0..n) and sign r.
+ *    Initial state |0...0>: destabilizer i = X_i, stabilizer i = Z_i.
+ *  - Coins: the m-th M/R op (circuit order) reads bit m%64 of coin word m/64
+ *    of its shot, and only if its outcome is random (Sec. 2.4: "a random phase
+ *    bit ... is chosen").  Outcome 1 means eigenvalue -1.
+ *  - Records: bit k of a shot's record is the outcome of the k-th M op.
+ *  - Noise: the l-th noise op reads uint32 word l of its shot's noise stream
+ *    (RESET_ERROR reads words l, l+1, l+2).  T(p) = floor(p * 2^32).
+ *    DEPOLARIZE1(p): error iff u < T, Pauli (u*3)/T = X, Y, Z.
+ *    DEPOLARIZE2(p): error iff u < T, m = (u*15)/T + 1, Pauli m/4 on q0 and
+ *    m%4 on q1 (0 I, 1 X, 2 Y, 3 Z).  PAULI_CHANNEL_1(px,py,pz): X if
+ *    u < T(px), Y if u < T(px)+T(py), Z if u < T(px)+T(py)+T(pz).
+ *    RESET_ERROR(gamma, q): if u0 < T(gamma) reset the qubit with coin u1&1,
+ *    then Z if u2 < T(q) (composite relaxation/dephasing, Sec. 4.2).
+ *  - SEEDED streams: coin word k of shot s = SplitMix64 output k of
+ *    key(seed, s, 1); noise word l = (output l of key(seed, s, 2)) >> 32, where
+ *    key(seed, s, kind) = mix64(mix64(seed + kind*G) + (s+1)*G), G the
+ *    SplitMix64 increment (Steele, Lea & Flood 2014).
+ */
+#ifndef LIBSTAB_STAB_H_
+#define LIBSTAB_STAB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define STAB_OK 0
+#define STAB_ERR_ARG (-1)          /* invalid argument (index, size, pointer) */
+#define STAB_ERR_OOM (-2)          /* device or host allocation failed / footprint too large */
+#define STAB_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define STAB_ERR_STREAM_SHORT (-4) /* a coin/noise/record buffer is shorter than the circuit needs */
+#define STAB_ERR_TIMEOUT (-5)      /* a bounded wait gave up (device flag or host poll) */
+#define STAB_ERR_BUSY (-6)         /* the request queue or slot table is full */
+#define STAB_ERR_INTERNAL (-7)     /* a device-side consistency check failed (odd phase, bad product) */
+#define STAB_ERR_NOT_FOUND (-8)    /* unknown circuit or request id */
+#define STAB_ERR_UNSUPPORTED (-9)  /* size outside what the chosen engine supports */
+
+/* ---- op kinds (values are part of the ABI) ---- */
+enum stab_kind {
+    STAB_NOP = 0,
+    STAB_H = 1, STAB_S = 2, STAB_X = 3, STAB_Y = 4, STAB_Z = 5, /* one-qubit Cliffords, Sec. 2.4 Table */
+    STAB_CX = 6,      /* q0 control, q1 target */
+    STAB_CZ = 7, STAB_SWAP = 8,
+    STAB_M = 9,       /* Z-basis measurement, recorded */
+    STAB_R = 10,      /* reset to |0>: measure (not recorded), then X if the outcome is 1 */
+    STAB_DEP1 = 11,   /* DEPOLARIZE1(p): params[arg] = (p, -, -) */
+    STAB_DEP2 = 12,   /* DEPOLARIZE2(p) on (q0, q1): params[arg] = (p, -, -) */
+    STAB_PC1 = 13,    /* PAULI_CHANNEL_1: params[arg] = (px, py, pz) */
+    STAB_TICK = 14,   /* layer hint, no effect */
+    STAB_RESET_ERR = 15 /* RESET_ERROR: params[arg] = (gamma, q, -) */
+};
+
+/* One op: 16 bytes, little-endian, identical to the Python OP_DTYPE. */
+typedef struct stab_op {
+    uint8_t kind;
+    uint8_t rsv0;
+    uint16_t rsv1;
+    uint32_t q0;
+    uint32_t q1;
+    uint32_t arg; /* noise ops: row index into the params table */
+} stab_op;
+
+/* ---- coin / noise streams ---- */
+#define STAB_STREAM_BUFFER 0u /* caller-provided device buffers, one row per shot */
+#define STAB_STREAM_SEEDED 1u /* generated on the device from (seed, shot_offset + shot) */
+
+typedef struct stab_streams {
+    uint32_t mode;
+    uint32_t rsv;
+    uint64_t seed;          /* SEEDED */
+    uint64_t shot_offset;   /* SEEDED: stream shot index of the call's first shot */
+    const uint64_t *coins;  /* BUFFER: device pointer, [shots][coin_words] */
+    uint64_t coin_words;    /* BUFFER: row stride in uint64 words */
+    const uint32_t *noise;  /* BUFFER: device pointer, [shots][noise_words] */
+    uint64_t noise_words;   /* BUFFER: row stride in uint32 words */
+} stab_streams;
+
+typedef struct stab_circuit_info {
+    uint32_t n;              /* qubits */
+    uint32_t n_layers;       /* compiled layers (gate layers + measurement layers) */
+    uint64_t n_ops;          /* ops excluding NOP/TICK */
+    uint64_t n_gates;        /* unitary gates */
+    uint64_t n_meas;         /* M ops = record bits */
+    uint64_t n_coin;         /* M + R ops = coin slots */
+    uint64_t n_noise_words;  /* noise words one shot reads */
+    uint64_t record_words;   /* ceil(n_meas / 64), at least 1 */
+    uint64_t coin_words;     /* ceil(n_coin / 64), at least 1 */
+    uint32_t n_gate_layers;
+    uint32_t n_meas_layers;
+    uint32_t n_gate_runs;    /* maximal runs of consecutive gate layers */
+    uint32_t max_layer_meas; /* largest measurement layer */
+} stab_circuit_info;
+
+/* engines for stab_sample */
+#define STAB_ENGINE_AUTO 0u
+#define STAB_ENGINE_LAYERED 1u  /* tableau in HBM/L2, one launch per gate run / measurement layer */
+#define STAB_ENGINE_RESIDENT 2u /* tableau in shared memory, whole circuit in one persistent launch */
+
+typedef struct stab_ctx stab_ctx;
+
+/* Context bound to CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream), e.g. torch.cuda.current_stream().cuda_stream. */
+int stab_create(stab_ctx **out, int device, void *cuda_stream);
+void stab_destroy(stab_ctx *ctx);
+int stab_set_stream(stab_ctx *ctx, void *cuda_stream);
+const char *stab_last_error(void);
+/* Wait for the context's stream; returns a device-side error flag if one was set. */
+int stab_sync(stab_ctx *ctx);
+
+/* Compile a flat op list (host memory, copied) over n qubits into layers of
+ * pairwise-disjoint ops (the paper's sim2d chunking done at generation time,
+ * Sec. 3.1.4).  params: host float64 [n_params][3]. */
+int stab_compile(stab_ctx *ctx, uint32_t n, const stab_op *ops, size_t n_ops,
+                 const double *params, size_t n_params, uint64_t *circuit_id);
+int stab_circuit_info_get(stab_ctx *ctx, uint64_t circuit_id, stab_circuit_info *out);
+int stab_release_circuit(stab_ctx *ctx, uint64_t circuit_id);
+
+/* ---- resident tableaux: tableau_init(n), apply_circuit(...) ---- */
+
+/* (Re)allocate `count` resident tableaux of n qubits on the device, each |0...0>
+ * (Sec. 2.3; 4n^2+2n bits each, stored twice: column-packed and row-packed). */
+int stab_tableau_init(stab_ctx *ctx, uint32_t n, uint32_t count);
+/* Evolve every resident tableau i through the circuit (tableau i reads stream
+ * row / shot i).  d_record: device [count][record_words] uint64, overwritten. */
+int stab_apply_circuit(stab_ctx *ctx, uint64_t circuit_id, const stab_streams *streams,
+                       uint64_t *d_record, uint64_t record_words);
+/* Copy resident tableau `index` to host in row-major form: x, z as uint64
+ * [2n][ceil(n/64)] (bit j of row i = qubit j), r as uint8 [2n].  Synchronizes. */
+int stab_get_tableau(stab_ctx *ctx, uint32_t index, uint64_t *host_x, uint64_t *host_z,
+                     uint8_t *host_r);
+int stab_set_tableau(stab_ctx *ctx, uint32_t index, const uint64_t *host_x,
+                     const uint64_t *host_z, const uint8_t *host_r);
+
+/* ---- sample(shots, streams) -> records: every shot from |0...0> ---- */
+
+/* d_record: device [shots][record_words] uint64, overwritten. */
+int stab_sample(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, const stab_streams *streams,
+                uint64_t *d_record, uint64_t record_words, uint32_t engine);
+/* Same with HOST buffers: copies coins/noise to the device, runs, copies the
+ * records back, and synchronizes.  host_noise may be NULL for noiseless circuits. */
+int stab_sample_host(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots,
+                     const uint64_t *host_coins, uint64_t coin_words,
+                     const uint32_t *host_noise, uint64_t noise_words,
+                     uint64_t *host_record, uint64_t record_words, uint32_t engine);
+
+/* ---- batched form: many circuits (uneven sizes) in one persistent launch ---- */
+typedef struct stab_job_group {
+    uint64_t circuit_id;
+    uint32_t shots;
+    uint32_t rsv;
+    stab_streams streams;
+    uint64_t *d_record;     /* device [shots][record_words] */
+    uint64_t record_words;
+} stab_job_group;
+
+int stab_sample_batch(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
+
+/* Resident-engine launch shape, chosen per qubit-count bucket by the autotuner. */
+typedef struct stab_tune {
+    uint32_t group_threads;    /* threads per tableau: 32, 64, 128 or 256 */
+    uint32_t tableaux_per_cta; /* tableaux resident per CTA */
+    uint32_t words_per_thread; /* 32-bit tableau words per thread per gate item: 1, 2 or 4 */
+    uint32_t rsv;
+} stab_tune;
+
+/* Time the candidate shapes on `shots` shots of each circuit and store the
+ * fastest per bucket (bucket = ceil(n/32)).  Synchronizes. */
+int stab_autotune(stab_ctx *ctx, const uint64_t *circuit_ids, size_t n_circuits, uint32_t shots);
+int stab_get_tune(stab_ctx *ctx, uint32_t n, stab_tune *out);
+int stab_set_tune(stab_ctx *ctx, uint32_t n, const stab_tune *tune);
+
+/* ---- served form: continuous batching with HBM-footprint admission ---- */
+typedef struct stab_serve_config {
+    uint64_t hbm_budget_bytes; /* admission limit for resident request state */
+    uint32_t max_inflight;     /* concurrently admitted requests (slots) */
+    uint32_t n_streams;        /* device streams the loop spreads launches over */
+    uint32_t max_batch_requests; /* small requests merged into one resident launch */
+    uint32_t rsv;
+} stab_serve_config;
+
+typedef struct stab_request_status {
+    uint64_t req_id;
+    int32_t status;         /* STAB_OK or an error code */
+    uint32_t shots;
+    double t_submit;        /* seconds, CLOCK_MONOTONIC */
+    double t_admit;
+    double t_done;
+} stab_request_status;
+
+int stab_serve_start(stab_ctx *ctx, const stab_serve_config *cfg);
+/* Queue a request: `shots` shots of a compiled circuit with SEEDED streams
+ * (seed, shot_offset); records land in d_record ([shots][record_words], device,
+ * caller-owned, must stay valid until the request completes). */
+int stab_serve_submit(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, uint64_t seed,
+                      uint64_t shot_offset, uint64_t *d_record, uint64_t record_words,
+                      uint64_t *req_id);
+/* Collect up to `cap` completed requests (non-blocking). */
+int stab_serve_poll(stab_ctx *ctx, stab_request_status *done, size_t cap, size_t *n_done);
+/* Wait until every submitted request completed or `timeout_s` elapsed. */
+int stab_serve_drain(stab_ctx *ctx, double timeout_s);
+int stab_serve_stop(stab_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBSTAB_STAB_H_ */

@@ -77,9 +77,10 @@ class Circuit:
         return int(np.count_nonzero((k == M) | (k == R)))
 
     @property
-    def n_noise(self) -> int:           # noise draws (one uint32 per noise op)
+    def n_noise(self) -> int:           # noise draws: one uint32 per noise op, three for RESET_ERROR
         k = self.ops["kind"]
-        return int(np.count_nonzero(np.isin(k, NOISE_KINDS)))
+        return int(np.count_nonzero(np.isin(k, (DEP1, DEP2, PC1)))
+                   + 3 * np.count_nonzero(k == RESET_ERR))
 
     @property
     def record_words(self) -> int:

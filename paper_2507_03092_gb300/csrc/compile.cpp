@@ -1,0 +1,219 @@
+// compile.cpp -- circuit compiler: flat op list -> layers of disjoint ops.
+//
+// The paper's sim2d (Sec. 3.1.4) runs independent gates of pre-flagged chunks
+// concurrently and notes that scheduling at run time did not pay off; here the
+// chunking is done once, at compile time, exactly: an op joins the current
+// layer iff it is of the same class (unitary/noise vs. measurement) and touches
+// no qubit already used in the layer.  Noise ops directly following a gate on
+// the same qubits are attached to that gate's item, so the ubiquitous
+// "gate, then its noise channel" pattern does not split layers.
+#include "internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+
+namespace stab {
+
+static unsigned long long threshold(double p) {
+    if (!(p > 0.0)) return 0ull;
+    if (p >= 1.0) return 1ull << 32;
+    return (unsigned long long)(p * 4294967296.0);   // exact scaling, truncation = floor
+}
+
+static bool is_gate(uint8_t k) { return k >= STAB_H && k <= STAB_SWAP; }
+static bool is_two(uint8_t k) { return k == STAB_CX || k == STAB_CZ || k == STAB_SWAP || k == STAB_DEP2; }
+static bool is_noise(uint8_t k) { return k == STAB_DEP1 || k == STAB_DEP2 || k == STAB_PC1; }
+static bool is_meas_class(uint8_t k) { return k == STAB_M || k == STAB_R || k == STAB_RESET_ERR; }
+
+int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
+                    size_t n_params, HostProg &P, std::string *err) {
+    if (n == 0) { *err = "n must be positive"; return STAB_ERR_ARG; }
+    if (n_ops && !ops) { *err = "ops is NULL"; return STAB_ERR_ARG; }
+    if (n_params && !params) { *err = "params is NULL"; return STAB_ERR_ARG; }
+    P.n = n;
+    P.H = (n + 31) / 32;
+    P.CW = 2 * P.H;
+    P.thr.resize(n_params ? n_params : 1);
+    for (size_t i = 0; i < n_params; i++) {
+        for (int k = 0; k < 3; k++) {
+            double v = params[3 * i + k];
+            if (!(v >= 0.0) || v > 1.0) {
+                *err = "noise parameter row " + std::to_string(i) + " outside [0, 1]";
+                return STAB_ERR_ARG;
+            }
+            P.thr[i].t[k] = threshold(v);
+        }
+    }
+    // ---- validate ----
+    for (size_t k = 0; k < n_ops; k++) {
+        const stab_op &o = ops[k];
+        if (o.kind > STAB_RESET_ERR) { *err = "op " + std::to_string(k) + ": unknown kind"; return STAB_ERR_ARG; }
+        if (o.kind == STAB_NOP || o.kind == STAB_TICK) continue;
+        if (o.q0 >= n) { *err = "op " + std::to_string(k) + ": qubit out of range"; return STAB_ERR_ARG; }
+        if (is_two(o.kind) && (o.q1 >= n || o.q1 == o.q0)) {
+            *err = "op " + std::to_string(k) + ": two-qubit op needs two distinct qubits < n";
+            return STAB_ERR_ARG;
+        }
+        if ((is_noise(o.kind) || o.kind == STAB_RESET_ERR) && o.arg >= n_params) {
+            *err = "op " + std::to_string(k) + ": parameter row out of range";
+            return STAB_ERR_ARG;
+        }
+        if (o.kind == STAB_PC1) {
+            const double *pp = params + 3 * (size_t)o.arg;
+            if (P.thr[o.arg].t[0] + P.thr[o.arg].t[1] + P.thr[o.arg].t[2] > (1ull << 32) ||
+                pp[0] + pp[1] + pp[2] > 1.0 + 1e-12) {
+                *err = "op " + std::to_string(k) + ": PAULI_CHANNEL_1 probabilities sum above 1";
+                return STAB_ERR_ARG;
+            }
+        }
+    }
+    // ---- layer ----
+    // owner[q] = index of the item in the current layer touching q, or -1
+    std::vector<int64_t> owner(n, -1);
+    std::vector<uint32_t> touched;
+    int cur = -1;          // current layer type, -1 = none
+    uint32_t first = 0;
+    uint64_t m_ord = 0, c_ord = 0, l_ord = 0, n_gates = 0, n_real = 0;
+    auto close_layer = [&]() {
+        if (cur < 0) return;
+        Layer L{};
+        L.type = (uint32_t)cur;
+        L.first = first;
+        L.count = (cur == LT_GATE ? (uint32_t)P.gitems.size() : (uint32_t)P.mitems.size()) - first;
+        L.has_cond = 0;
+        if (cur == LT_MEAS)
+            for (uint32_t i = L.first; i < L.first + L.count; i++)
+                if (P.mitems[i].flags) L.has_cond = 1;
+        if (L.count) P.layers.push_back(L);
+        for (uint32_t q : touched) owner[q] = -1;
+        touched.clear();
+        cur = -1;
+    };
+    auto open_layer = [&](int type) {
+        close_layer();
+        cur = type;
+        first = type == LT_GATE ? (uint32_t)P.gitems.size() : (uint32_t)P.mitems.size();
+    };
+    auto touch = [&](uint32_t q, int64_t item) { owner[q] = item; touched.push_back(q); };
+
+    for (size_t k = 0; k < n_ops; k++) {
+        const stab_op &o = ops[k];
+        uint8_t kind = o.kind;
+        if (kind == STAB_NOP || kind == STAB_TICK) continue;
+        n_real++;
+        uint32_t a = o.q0, b = is_two(kind) ? o.q1 : o.q0;
+        if (is_meas_class(kind)) {
+            if (cur != LT_MEAS || owner[a] >= 0) open_layer(LT_MEAS);
+            MItem m{};
+            m.q = a;
+            m.rec = 0xffffffffu;
+            if (kind == STAB_RESET_ERR) {
+                m.flags = MF_RESET_ERR;
+                m.nl = (uint32_t)l_ord;
+                m.np = o.arg;
+                l_ord += 3;
+            } else {
+                m.coin = (uint32_t)c_ord++;
+                if (kind == STAB_M) m.rec = (uint32_t)m_ord++;
+                else m.flags = MF_RESET;
+            }
+            touch(a, (int64_t)P.mitems.size());
+            P.mitems.push_back(m);
+            continue;
+        }
+        if (is_gate(kind)) {
+            n_gates++;
+            bool free_ = cur == LT_GATE && owner[a] < 0 && owner[b] < 0;
+            if (!free_) open_layer(LT_GATE);
+            GItem g{};
+            g.a = a; g.b = b; g.gate = kind;
+            int64_t idx = (int64_t)P.gitems.size();
+            touch(a, idx);
+            if (b != a) touch(b, idx);
+            P.gitems.push_back(g);
+            continue;
+        }
+        // noise op
+        uint32_t nl = (uint32_t)l_ord++;
+        bool attached = false;
+        if (cur == LT_GATE) {
+            int64_t oa = owner[a], ob = owner[b];
+            if (oa >= 0 && (b == a || ob == oa)) {
+                GItem &g = P.gitems[(size_t)oa];
+                if (g.nn < 2) {
+                    uint8_t t;
+                    if (b == a) t = (a == g.a) ? NT_A : NT_B;
+                    else t = (a == g.a) ? NT_AB : NT_BA;
+                    g.nk[g.nn] = kind; g.nt[g.nn] = t; g.nl[g.nn] = nl; g.np[g.nn] = o.arg;
+                    g.nn++;
+                    attached = true;
+                }
+            }
+        }
+        if (!attached) {
+            bool free_ = cur == LT_GATE && owner[a] < 0 && owner[b] < 0;
+            if (!free_) open_layer(LT_GATE);
+            GItem g{};
+            g.a = a; g.b = b; g.gate = 0; g.nn = 1;
+            g.nk[0] = kind; g.nt[0] = (b == a) ? NT_A : NT_AB; g.nl[0] = nl; g.np[0] = o.arg;
+            int64_t idx = (int64_t)P.gitems.size();
+            touch(a, idx);
+            if (b != a) touch(b, idx);
+            P.gitems.push_back(g);
+        }
+    }
+    close_layer();
+    if (m_ord > 0xfffffff0ull || c_ord > 0xfffffff0ull || l_ord > 0xfffffff0ull) {
+        *err = "circuit too long (more than 2^32 measurements or noise draws)";
+        return STAB_ERR_UNSUPPORTED;
+    }
+    // ---- runs for the layered engine ----
+    uint32_t max_meas = 0, max_g = 0, n_gl = 0, n_ml = 0;
+    for (uint32_t l = 0; l < P.layers.size(); l++) {
+        const Layer &L = P.layers[l];
+        if (L.type == LT_MEAS) {
+            P.runs.push_back(Run{LT_MEAS, l, l + 1});
+            max_meas = std::max(max_meas, L.count);
+            n_ml++;
+        } else {
+            if (!P.runs.empty() && P.runs.back().type == LT_GATE && P.runs.back().l1 == l)
+                P.runs.back().l1 = l + 1;
+            else
+                P.runs.push_back(Run{LT_GATE, l, l + 1});
+            max_g = std::max(max_g, L.count);
+            n_gl++;
+        }
+    }
+    stab_circuit_info &I = P.info;
+    memset(&I, 0, sizeof(I));
+    I.n = n;
+    I.n_layers = (uint32_t)P.layers.size();
+    I.n_ops = n_real;
+    I.n_gates = n_gates;
+    I.n_meas = m_ord;
+    I.n_coin = c_ord;
+    I.n_noise_words = l_ord;
+    I.record_words = std::max<uint64_t>(1, (m_ord + 63) / 64);
+    I.coin_words = std::max<uint64_t>(1, (c_ord + 63) / 64);
+    I.n_gate_layers = n_gl;
+    I.n_meas_layers = n_ml;
+    I.max_layer_meas = max_meas;
+    uint32_t n_runs_gate = 0;
+    for (auto &r : P.runs) n_runs_gate += r.type == LT_GATE;
+    I.n_gate_runs = n_runs_gate;
+    // work estimate: word-ops over the column-packed tableau
+    P.cost = (uint64_t)P.CW * (P.gitems.size() + 4 * P.mitems.size()) + P.layers.size() * 64;
+    P.dev.n = n; P.dev.H = P.H; P.dev.CW = P.CW;
+    P.dev.n_layers = (uint32_t)P.layers.size();
+    P.dev.record_words = (uint32_t)I.record_words;
+    P.dev.coin_words = (uint32_t)I.coin_words;
+    P.dev.noise_words = (uint32_t)std::max<uint64_t>(1, l_ord);
+    P.dev.max_meas = max_meas;
+    P.dev.max_gitems = max_g;
+    P.dev.n_gitems = (uint32_t)P.gitems.size();
+    P.dev.n_mitems = (uint32_t)P.mitems.size();
+    return STAB_OK;
+}
+
+}  // namespace stab

@@ -1,0 +1,175 @@
+// internal.h -- program format, device helpers and engine entry points shared
+// by the translation units of libstab.so.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <cuda_runtime.h>
+
+#include "../../include/stab.h"
+
+namespace stab {
+
+// ---------------------------------------------------------------------------
+// Compiled program
+// ---------------------------------------------------------------------------
+// A circuit is compiled into layers.  A gate layer holds items on pairwise
+// disjoint qubits; each item is an optional Clifford gate followed by up to two
+// noise ops on the same qubits.  A measurement layer holds M / R / RESET_ERROR
+// ops on pairwise disjoint qubits.  Ops inside one layer commute exactly, so
+// running a layer in parallel gives the same tableau, bit for bit, as running
+// its ops one by one in circuit order.
+
+enum LayerType : uint32_t { LT_GATE = 0, LT_MEAS = 1 };
+
+// noise target of an item's noise op
+enum : uint8_t { NT_A = 0, NT_B = 1, NT_AB = 2, NT_BA = 3 };
+// measurement item flags
+enum : uint32_t { MF_RESET = 1u, MF_RESET_ERR = 2u };
+
+struct GItem {            // 32 bytes
+    uint32_t a, b;        // qubits (b == a for one-qubit items)
+    uint8_t gate;         // stab_kind of the gate, 0 = none
+    uint8_t nn;           // noise ops attached (0..2)
+    uint8_t nk[2];        // their kinds (STAB_DEP1 / STAB_DEP2 / STAB_PC1)
+    uint8_t nt[2];        // their targets (NT_*)
+    uint16_t pad;
+    uint32_t nl[2];       // noise-draw ordinals
+    uint32_t np[2];       // parameter rows
+};
+static_assert(sizeof(GItem) == 32, "GItem layout");
+
+struct MItem {            // 24 bytes
+    uint32_t q;
+    uint32_t coin;        // coin ordinal (M / R); unused for RESET_ERR
+    uint32_t rec;         // record ordinal, 0xffffffff if not recorded
+    uint32_t flags;       // MF_*
+    uint32_t nl;          // RESET_ERR: ordinal of its first noise draw
+    uint32_t np;          // RESET_ERR: parameter row
+};
+static_assert(sizeof(MItem) == 24, "MItem layout");
+
+struct Layer {
+    uint32_t type, first, count, has_cond;   // has_cond: R or RESET_ERR items present
+};
+
+struct Thr {              // floor(p_i * 2^32) for the three parameters of a row
+    unsigned long long t[3];
+};
+
+struct DevProg {          // by-value descriptor handed to kernels
+    uint32_t n, H, CW, n_layers;
+    const Layer *layers;
+    const GItem *gitems;
+    const MItem *mitems;
+    const Thr *thr;
+    uint32_t record_words, coin_words, noise_words, max_meas;
+    uint32_t max_gitems, n_gitems, n_mitems, pad;
+};
+
+struct Run {              // layered engine schedule entry
+    uint32_t type;        // LT_GATE: layers [l0, l1); LT_MEAS: layer l0
+    uint32_t l0, l1;
+};
+
+struct HostProg {
+    uint64_t id = 0;
+    uint32_t n = 0, H = 0, CW = 0;
+    std::vector<Layer> layers;
+    std::vector<GItem> gitems;
+    std::vector<MItem> mitems;
+    std::vector<Thr> thr;
+    std::vector<Run> runs;
+    stab_circuit_info info{};
+    uint64_t cost = 0;          // rough work estimate (for scheduling)
+    void *dmem = nullptr;       // device copy of the arrays
+    DevProg dev{};
+};
+
+// Compile ops -> HostProg (host only).  Returns STAB_OK or an error code and
+// writes a message to *err.
+int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
+                    size_t n_params, HostProg &out, std::string *err);
+
+// ---------------------------------------------------------------------------
+// Streams
+// ---------------------------------------------------------------------------
+struct DevStreams {
+    uint32_t mode, pad;
+    unsigned long long seed, shot_offset;
+    const unsigned long long *coins;
+    unsigned long long coin_stride;
+    const uint32_t *noise;
+    unsigned long long noise_stride;
+};
+
+// ---------------------------------------------------------------------------
+// Layered engine storage (one batch of tableaux with the same n)
+// ---------------------------------------------------------------------------
+// Column-packed copy ("QM"): for tableau t, plane x then plane z, each
+// [CW][n] 32-bit words; word w of column j holds rows 32w..32w+31 of column j.
+// Row-packed copy ("RM"): [64H rows][2H words] (x words then z words).
+// Row slots: destabilizer i -> slot i, stabilizer i -> slot 32H + i.
+// Sign bits r: [CW] words over row slots.  dirty[w] = 1 when the row-packed
+// copy of rows 32w..32w+31 is newer than the column-packed one.
+struct Batch {
+    uint32_t n = 0, H = 0, CW = 0, count = 0;
+    uint32_t *qm = nullptr;  size_t qm_stride = 0;   // words per tableau
+    uint32_t *rm = nullptr;  size_t rm_stride = 0;
+    uint32_t *r = nullptr;
+    uint8_t *dirty = nullptr;
+    bool rm_valid = false;
+    void *mem = nullptr;
+    size_t bytes = 0;
+};
+
+struct MeasScratch {
+    uint32_t *cols = nullptr;     // [count][max_meas][CW]
+    uint8_t *stat = nullptr;      // [count][max_meas]
+    uint8_t *out = nullptr;       // [count][max_meas]
+    size_t cap_words = 0, cap_items = 0;
+};
+
+struct LaunchCfg {
+    int sm_count = 0;
+    size_t smem_optin = 0;
+};
+
+size_t batch_bytes(uint32_t n, uint32_t count);
+int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err);
+void batch_free(Batch &b);
+
+// Layered engine (layered.cu)
+cudaError_t layered_init(Batch &b, cudaStream_t s);
+cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
+                        unsigned long long *record, size_t rec_stride, int *d_err,
+                        const LaunchCfg &lc, cudaStream_t s);
+cudaError_t layered_sync_qm(Batch &b, cudaStream_t s);
+size_t layered_gate_smem(uint32_t n);
+int layered_supported(uint32_t n, const LaunchCfg &lc);
+
+// Resident engine (resident.cu)
+struct ResJob {               // one shot
+    const DevProg *prog;      // device pointer
+    DevStreams st;            // streams of its group (shot index below)
+    unsigned long long *record;
+    unsigned long long rec_stride;
+    uint32_t shot;            // shot index within its group
+    uint32_t pad;
+};
+size_t resident_smem_per_tableau(uint32_t n);
+int resident_supported(uint32_t n, const LaunchCfg &lc);
+cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
+                         const stab_tune &tune, unsigned int *d_counter, int *d_err,
+                         const LaunchCfg &lc, cudaStream_t s);
+
+// device error flag values
+enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,
+             DERR_BOUNDS = 4 };
+
+}  // namespace stab

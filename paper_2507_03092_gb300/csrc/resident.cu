@@ -1,0 +1,286 @@
+// resident.cu -- the resident engine: each tableau lives in shared memory for
+// its whole circuit; a persistent launch runs many shots of many circuits
+// (uneven qubit counts) at once.  A CTA holds `tableaux_per_cta` groups of
+// `group_threads` threads; each group pulls shots from a device work counter,
+// simulates the shot from |0...0> to its last op, writes its record and pulls
+// the next one.  Synchronisation is group-local (warp sync or a named barrier).
+//
+// Per shot the circuit is the same CHP evolution as the layered engine
+// (Sec. 2.4 gate table, Appendix B rowsum, Sec. 2.4 measurement rules), here on
+// a column-packed tableau in shared memory: x[j][w], z[j][w] hold rows
+// 32w..32w+31 of column j, so a gate touches CW contiguous words per column.
+#include "device_common.cuh"
+
+#include <algorithm>
+
+namespace stab {
+
+struct GroupCtx {
+    uint32_t gtid, G, gid;
+};
+
+__device__ __forceinline__ void gsync(const GroupCtx &g) {
+    if (g.G == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(g.gid + 1), "r"(g.G) : "memory");
+}
+
+// smem layout per group (32-bit words): x[n*CW], z[n*CW], r[CW], cnt[64H] (int),
+// acol[CW] (snapshot of the measured column), prow[n] (pivot row Pauli per
+// column), misc[8]
+__host__ __device__ __forceinline__ size_t res_words(uint32_t n) {
+    const size_t H = (n + 31) / 32, CW = 2 * H;
+    return 2 * (size_t)n * CW + CW + 64 * H + CW + n + 8;
+}
+
+size_t resident_smem_per_tableau(uint32_t n) { return 4 * res_words(n); }
+
+int resident_supported(uint32_t n, const LaunchCfg &lc) {
+    return resident_smem_per_tableau(n) + 64 <= lc.smem_optin;
+}
+
+// Z measurement of qubit a in the group's shared-memory tableau.
+// Returns the outcome; `coin` is used only if the outcome is random.
+__device__ uint32_t res_measure(const GroupCtx &g, uint32_t n, uint32_t H, uint32_t CW,
+                                uint32_t *X, uint32_t *Z, uint32_t *r, int *cnt, uint32_t *acol,
+                                uint32_t *prow, uint32_t *misc, uint32_t a, uint32_t coin, int *err) {
+    // ---- pivot search: first stabilizer word of column a with a set bit
+    if (g.gtid == 0) misc[0] = 0x7fffffffu;
+    gsync(g);
+    for (uint32_t w = g.gtid; w < H; w += g.G)
+        if (X[(size_t)a * CW + H + w]) atomicMin(&misc[0], w);
+    gsync(g);
+    const uint32_t pw = misc[0];
+    if (pw == 0x7fffffffu) {
+        // ---- deterministic: sign of prod of stabilizers selected by the
+        // destabilizer half of column a (ordered-product closed form)
+        if (g.gtid == 0) { misc[1] = 0; misc[2] = 0; }
+        gsync(g);
+        int acc = 0;
+        uint32_t bad = 0;
+        const uint32_t *K = X + (size_t)a * CW;         // destabilizer words [0, H)
+        for (uint32_t j = g.gtid; j < n; j += g.G) {
+            const uint32_t *xj = X + (size_t)j * CW + H, *zj = Z + (size_t)j * CW + H;
+            uint32_t carry = 0, px = 0, pz = 0;
+            for (uint32_t w = 0; w < H; w++) {
+                const uint32_t k = K[w];
+                if (!k) continue;
+                const uint32_t kx = xj[w] & k, kz = zj[w] & k;
+                uint32_t pre = kz;
+                pre ^= pre << 1; pre ^= pre << 2; pre ^= pre << 4; pre ^= pre << 8; pre ^= pre << 16;
+                pre <<= 1;                                 // exclusive prefix xor
+                acc += __popc(kx & kz) + 2 * ((__popc(kx & pre) + (int)(carry & __popc(kx))) & 1);
+                carry ^= __popc(kz) & 1u;
+                px ^= __popc(kx) & 1u;
+                pz ^= __popc(kz) & 1u;
+            }
+            bad |= px | (pz ^ (j == a ? 1u : 0u));
+        }
+        for (uint32_t w = g.gtid; w < H; w += g.G) acc += 2 * __popc(r[H + w] & K[w]);
+        for (int o = 16; o; o >>= 1) {
+            acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            bad |= __shfl_xor_sync(FULL_MASK, bad, o);
+        }
+        if ((g.gtid & 31) == 0) {
+            atomicAdd(&misc[1], (uint32_t)acc);
+            if (bad) misc[2] = 1;
+        }
+        gsync(g);
+        const uint32_t e = misc[1] & 3u;
+        if (g.gtid == 0) {
+            if (e & 1u) set_err(err, DERR_ODD_PHASE);
+            if (misc[2]) set_err(err, DERR_BAD_PRODUCT);
+        }
+        gsync(g);
+        return (e >> 1) & 1u;
+    }
+    // ---- random
+    const uint32_t pbit = __ffs(X[(size_t)a * CW + H + pw]) - 1;
+    const uint32_t q = 32 * pw + pbit, p = 32 * H + q;
+    const uint32_t pwd = p >> 5, qwd = q >> 5;
+    const uint32_t pm = 1u << (p & 31), qm = 1u << (q & 31);
+    // pivot row Pauli per column (2 bits), snapshot of column a (the rowsum
+    // below rewrites it), zero the row counters
+    for (uint32_t w = g.gtid; w < CW; w += g.G) acol[w] = X[(size_t)a * CW + w];
+    for (uint32_t j = g.gtid; j < n; j += g.G)
+        prow[j] = ((X[(size_t)j * CW + pwd] & pm) ? 1u : 0u) | ((Z[(size_t)j * CW + pwd] & pm) ? 2u : 0u);
+    for (uint32_t s = g.gtid; s < 64 * H; s += g.G) cnt[s] = 0;
+    gsync(g);
+    // rowsum(s, p) for all s in A = column a minus {p, q}: x/z update and
+    // per-row power of i, column by column (g of Appendix B per bit)
+    const uint32_t *colA = acol;
+    for (uint32_t idx = g.gtid; idx < n * CW; idx += g.G) {
+        const uint32_t j = idx / CW, w = idx - j * CW;
+        const uint32_t P = prow[j];
+        if (!P) continue;
+        uint32_t M = colA[w];
+        if (w == pwd) M &= ~pm;
+        if (w == qwd) M &= ~qm;
+        if (!M) continue;
+        uint32_t &xw = X[(size_t)j * CW + w], &zw = Z[(size_t)j * CW + w];
+        const uint32_t x = xw, z = zw;
+        uint32_t plus, minus;
+        if (P == 1) { plus = z & x; minus = z & ~x; }          // pivot X: g = z(2x-1)
+        else if (P == 3) { plus = z & ~x; minus = x & ~z; }    // pivot Y: g = z - x
+        else { plus = x & ~z; minus = x & z; }                 // pivot Z: g = x(1-2z)
+        plus &= M; minus &= M;
+        if (P & 1u) xw = x ^ M;
+        if (P & 2u) zw = z ^ M;
+        while (plus) { const int b = __ffs(plus) - 1; plus &= plus - 1; atomicAdd(&cnt[32 * w + b], 1); }
+        while (minus) { const int b = __ffs(minus) - 1; minus &= minus - 1; atomicAdd(&cnt[32 * w + b], -1); }
+    }
+    gsync(g);
+    const uint32_t rp = (r[pwd] & pm) ? 1u : 0u;
+    for (uint32_t w = g.gtid; w < CW; w += g.G) {
+        uint32_t M = colA[w];
+        if (w == pwd) M &= ~pm;
+        if (w == qwd) M &= ~qm;
+        uint32_t flip = 0;
+        while (M) {
+            const int b = __ffs(M) - 1;
+            M &= M - 1;
+            const uint32_t rs = (r[w] >> b) & 1u;
+            const int e = (int)(2 * rs + 2 * rp) + cnt[32 * w + b];
+            if (e & 1) set_err(err, DERR_ODD_PHASE);
+            if ((uint32_t)((e & 3) >> 1) != rs) flip |= 1u << b;
+        }
+        if (flip) r[w] ^= flip;          // each word owned by one thread here
+    }
+    gsync(g);
+    // row q <- row p, row p <- +-Z_a (column by column; bits p and q of a
+    // column are handled by one thread)
+    for (uint32_t j = g.gtid; j < n; j += g.G) {
+        const uint32_t P = prow[j];
+        uint32_t *xq = X + (size_t)j * CW + qwd, *zq = Z + (size_t)j * CW + qwd;
+        *xq = (P & 1u) ? (*xq | qm) : (*xq & ~qm);
+        *zq = (P & 2u) ? (*zq | qm) : (*zq & ~qm);
+        X[(size_t)j * CW + pwd] &= ~pm;
+        if (j == a) Z[(size_t)j * CW + pwd] |= pm;
+        else Z[(size_t)j * CW + pwd] &= ~pm;
+    }
+    if (g.gtid == 0) {
+        r[qwd] = rp ? (r[qwd] | qm) : (r[qwd] & ~qm);
+        r[pwd] = coin ? (r[pwd] | pm) : (r[pwd] & ~pm);
+    }
+    gsync(g);
+    return coin;
+}
+
+template <int WPT>
+__global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, unsigned int *counter,
+                           int *err, uint32_t G, uint32_t group_words) {
+    extern __shared__ uint32_t smem[];
+    GroupCtx g;
+    g.G = G;
+    g.gid = threadIdx.x / G;
+    g.gtid = threadIdx.x - g.gid * G;
+    uint32_t *base = smem + (size_t)g.gid * group_words;
+    for (;;) {
+        if (g.gtid == 0) base[group_words - 1] = atomicAdd(counter, 1u);
+        gsync(g);
+        const uint32_t jid = base[group_words - 1];
+        gsync(g);
+        if (jid >= n_jobs) break;
+        const ResJob job = jobs[jid];
+        const DevProg P = *job.prog;
+        const uint32_t n = P.n, H = P.H, CW = P.CW;
+        uint32_t *X = base, *Z = X + (size_t)n * CW, *r = Z + (size_t)n * CW;
+        int *cnt = (int *)(r + CW);
+        uint32_t *acol = (uint32_t *)(cnt + 64 * H), *prow = acol + CW, *misc = prow + n;
+        // |0...0>: destabilizer i = X_i (slot i), stabilizer i = Z_i (slot 32H+i)
+        for (uint32_t e = g.gtid; e < n * CW; e += G) {
+            const uint32_t j = e / CW, w = e - j * CW;
+            X[e] = (w == (j >> 5)) ? (1u << (j & 31)) : 0u;
+            Z[e] = (w == H + (j >> 5)) ? (1u << (j & 31)) : 0u;
+        }
+        for (uint32_t w = g.gtid; w < CW; w += G) r[w] = 0;
+        gsync(g);
+        const uint32_t nch = (CW + WPT - 1) / WPT;
+        for (uint32_t l = 0; l < P.n_layers; l++) {
+            const Layer L = P.layers[l];
+            if (L.type == LT_GATE) {
+                const uint32_t total = L.count * nch;
+                for (uint32_t idx = g.gtid; idx < total; idx += G) {
+                    const uint32_t it_i = idx / nch, ch = idx - it_i * nch;
+                    const GItem it = P.gitems[L.first + it_i];
+                    const bool two = it.b != it.a;
+#pragma unroll
+                    for (int k = 0; k < WPT; k++) {
+                        const uint32_t w = ch * WPT + k;
+                        if (w >= CW) break;
+                        uint32_t xa = X[(size_t)it.a * CW + w], za = Z[(size_t)it.a * CW + w];
+                        uint32_t xb = 0, zb = 0;
+                        if (two) { xb = X[(size_t)it.b * CW + w]; zb = Z[(size_t)it.b * CW + w]; }
+                        const uint32_t rr = apply_item(it, xa, za, xb, zb, job.st, job.shot, P.thr);
+                        X[(size_t)it.a * CW + w] = xa; Z[(size_t)it.a * CW + w] = za;
+                        if (two) { X[(size_t)it.b * CW + w] = xb; Z[(size_t)it.b * CW + w] = zb; }
+                        if (rr) atomicXor(&r[w], rr);
+                    }
+                }
+                gsync(g);
+            } else {
+                for (uint32_t i = 0; i < L.count; i++) {
+                    const MItem m = P.mitems[L.first + i];
+                    uint32_t coin;
+                    if (m.flags & MF_RESET_ERR) {
+                        const uint32_t u0 = noise_word(job.st, job.shot, m.nl);
+                        if ((unsigned long long)u0 < P.thr[m.np].t[0]) {
+                            coin = noise_word(job.st, job.shot, m.nl + 1) & 1u;
+                            const uint32_t o = res_measure(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, m.q, coin, err);
+                            if (o) for (uint32_t w = g.gtid; w < CW; w += G) r[w] ^= Z[(size_t)m.q * CW + w];
+                            gsync(g);
+                        }
+                        const uint32_t u2 = noise_word(job.st, job.shot, m.nl + 2);
+                        if ((unsigned long long)u2 < P.thr[m.np].t[1]) {
+                            for (uint32_t w = g.gtid; w < CW; w += G) r[w] ^= X[(size_t)m.q * CW + w];
+                            gsync(g);
+                        }
+                        continue;
+                    }
+                    coin = coin_bit(job.st, job.shot, m.coin);
+                    const uint32_t o = res_measure(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, m.q, coin, err);
+                    if (m.rec != 0xffffffffu) {
+                        if (o && g.gtid == 0)
+                            atomicOr(&job.record[(unsigned long long)job.shot * job.rec_stride + (m.rec >> 6)],
+                                     1ull << (m.rec & 63));
+                    } else if (o) {                     // reset: X_a flips rows with z_a = 1
+                        for (uint32_t w = g.gtid; w < CW; w += G) r[w] ^= Z[(size_t)m.q * CW + w];
+                        gsync(g);
+                    }
+                }
+            }
+        }
+        gsync(g);
+    }
+}
+
+cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, const stab_tune &tune,
+                         unsigned int *d_counter, int *d_err, const LaunchCfg &lc, cudaStream_t s) {
+    const uint32_t G = tune.group_threads, tpc = tune.tableaux_per_cta;
+    const size_t gw = res_words(max_n);
+    const size_t smem = 4 * gw * tpc;
+    if (smem > lc.smem_optin || G * tpc > 1024 || (G != 32 && tpc > 15)) return cudaErrorInvalidConfiguration;
+    static bool attr[5] = {false, false, false, false, false};
+    cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s);
+    int occ = 0;
+    cudaError_t e = cudaSuccess;
+    auto launch = [&](auto kern, int slot) {
+        if (!attr[slot]) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lc.smem_optin);
+            attr[slot] = true;
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)(G * tpc), smem);
+        if (occ < 1) occ = 1;
+        uint32_t groups_needed = (n_jobs + tpc - 1) / tpc;
+        uint32_t grid = std::min<uint32_t>((uint32_t)(occ * lc.sm_count), std::max<uint32_t>(1, groups_needed));
+        kern<<<grid, G * tpc, smem, s>>>(d_jobs, n_jobs, d_counter, d_err, G, (uint32_t)gw);
+        e = cudaGetLastError();
+    };
+    switch (tune.words_per_thread) {
+    case 1: launch(k_resident<1>, 1); break;
+    case 2: launch(k_resident<2>, 2); break;
+    default: launch(k_resident<4>, 4); break;
+    }
+    return e;
+}
+
+}  // namespace stab

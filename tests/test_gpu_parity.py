@@ -1,0 +1,210 @@
+"""GPU path vs CPU oracle: measurement records (bit-exact) and full tableaux
+(x, z and every sign bit, including destabilizer signs), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_03092_gb300 import binding as B
+from paper_2507_03092_gb300 import circuit as C
+from paper_2507_03092_gb300 import streams as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s = B.Simulator(0)
+    yield s
+    s.close()
+
+
+def _apply_layered(sim, circ, coins, noise, count=1):
+    """Resident tableaux + apply_circuit (layered engine); returns records and
+    the tableaux."""
+    cid = sim.compile(circ)
+    B.stab_tableau_init(sim.ctx, circ.n, count)
+    dc, dn = sim.to_dev(coins.reshape(count, -1)), sim.to_dev(noise.reshape(count, -1))
+    rec = sim.record_buffer(count, circ.record_words)
+    B.stab_apply_circuit(sim.ctx, cid, B.make_streams(B.STREAM_BUFFER, coins=dc, noise=dn), rec)
+    sim.sync()
+    tabs = [B.stab_get_tableau(sim.ctx, i, circ.n) for i in range(count)]
+    B.stab_release_circuit(sim.ctx, cid)
+    return B.records_to_numpy(rec), tabs
+
+
+def _oracle(circ, coins, noise):
+    rec, tab, _ = oracle.run(circ, coins, noise, return_tableau=True)
+    return rec, tab
+
+
+def _assert_tableau_equal(got, want, tag):
+    for name, g, w in zip("xzr", got, want):
+        assert np.array_equal(g, w), f"{tag}: tableau {name} differs"
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 32, 33, 63, 64, 65, 97, 130])
+def test_layered_random_circuits_match_oracle(sim, n):
+    for seed in range(4):
+        circ = C.random_small_circuit(n, 12 * n + 40, seed=seed + 17 * n)
+        coins, noise = S.streams_for(circ, seed, [0])
+        rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+        orec, otab = _oracle(circ, coins[0], noise[0])
+        assert np.array_equal(rec[0][:circ.record_words], orec), (n, seed)
+        _assert_tableau_equal(tabs[0], otab, f"n={n} seed={seed}")
+
+
+def test_layered_multi_tableau_batch(sim):
+    circ = C.random_small_circuit(40, 600, seed=3)
+    shots = 6
+    coins, noise = S.streams_for(circ, 9, range(shots))
+    rec, tabs = _apply_layered(sim, circ, coins, noise, count=shots)
+    for s in range(shots):
+        orec, otab = _oracle(circ, coins[s], noise[s])
+        assert np.array_equal(rec[s], orec)
+        _assert_tableau_equal(tabs[s], otab, f"shot {s}")
+
+
+@pytest.mark.parametrize("d,p", [(3, 1e-3), (5, 0.02), (7, 1e-3), (9, 0.01), (15, 1e-3)])
+def test_layered_surface_code_matches_oracle(sim, d, p):
+    circ = C.surface_code_memory(d, p=p)
+    coins, noise = S.streams_for(circ, d, [0])
+    rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+    orec, otab = _oracle(circ, coins[0], noise[0])
+    assert np.array_equal(rec[0], orec)
+    _assert_tableau_equal(tabs[0], otab, f"d={d}")
+
+
+def test_random_clifford_layers_match_oracle(sim):
+    circ = C.random_clifford_layers(200, 30, seed=0)
+    coins, noise = S.streams_for(circ, 0, [0])
+    rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+    orec, otab = _oracle(circ, coins[0], noise[0])
+    assert np.array_equal(rec[0], orec)
+    _assert_tableau_equal(tabs[0], otab, "random clifford")
+
+
+@pytest.mark.parametrize("engine", [B.ENGINE_RESIDENT, B.ENGINE_LAYERED])
+def test_sample_engines_match_oracle(sim, engine):
+    circ = C.surface_code_memory(3, p=0.01)
+    shots = 300
+    coins, noise = S.streams_for(circ, 0, range(shots))
+    cid = sim.compile(circ)
+    rec = B.records_to_numpy(sim.sample(cid, circ, shots, coins, noise, engine=engine))
+    sim.sync()
+    orec, _ = oracle.sample(circ, coins, noise, threads=4)
+    assert np.array_equal(rec, orec)
+
+
+@pytest.mark.parametrize("n", [1, 17, 33, 64, 97, 200])
+def test_resident_random_circuits_match_oracle(sim, n):
+    circ = C.random_small_circuit(n, 10 * n + 30, seed=n)
+    shots = 16
+    coins, noise = S.streams_for(circ, 1, range(shots))
+    cid = sim.compile(circ)
+    rec = B.records_to_numpy(sim.sample(cid, circ, shots, coins, noise, engine=B.ENGINE_RESIDENT))
+    sim.sync()
+    orec, _ = oracle.sample(circ, coins, noise)
+    assert np.array_equal(rec, orec)
+
+
+def test_seeded_streams_match_generator(sim):
+    """On-device SplitMix64 streams equal the generator's buffers."""
+    circ = C.surface_code_memory(5, p=0.02)
+    shots = 64
+    coins, noise = S.streams_for(circ, 77, range(10, 10 + shots))
+    orec, _ = oracle.sample(circ, coins, noise)
+    cid = sim.compile(circ)
+    for eng in (B.ENGINE_RESIDENT, B.ENGINE_LAYERED):
+        rec = B.records_to_numpy(sim.sample(cid, circ, shots, seed=77, shot_offset=10, engine=eng))
+        sim.sync()
+        assert np.array_equal(rec, orec), eng
+
+
+def test_mixed_distance_batch_one_launch(sim):
+    """Many circuits of uneven qubit counts in one persistent launch."""
+    import torch
+    groups, want, bufs = [], [], []
+    for d, shots in ((3, 40), (5, 25), (7, 10), (9, 5), (11, 3)):
+        T = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
+        circ = C.surface_code_memory(d, t1t2=T)
+        cid = sim.compile(circ)
+        coins, noise = S.streams_for(circ, 5, range(shots))
+        orec, _ = oracle.sample(circ, coins, noise, threads=4)
+        rec = sim.record_buffer(shots, circ.record_words)
+        dc, dn = sim.to_dev(coins), sim.to_dev(noise)
+        bufs += [dc, dn, rec]
+        g = B.JobGroup()
+        g.circuit_id, g.shots = cid, shots
+        g.streams = B.make_streams(B.STREAM_BUFFER, coins=dc, noise=dn)
+        g.d_record, g.record_words = rec.data_ptr(), circ.record_words
+        groups.append(g)
+        want.append((rec, orec))
+    B.stab_sample_batch(sim.ctx, groups)
+    sim.sync()
+    for rec, orec in want:
+        assert np.array_equal(B.records_to_numpy(rec), orec)
+
+
+def test_reset_error_channel_matches_oracle(sim):
+    b = C.Builder(6)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        k = rng.integers(4)
+        q = int(rng.integers(6))
+        if k == 0:
+            b.gate1(C.H, q)
+        elif k == 1:
+            b.gate2(C.CX, q, (q + 1) % 6)
+        elif k == 2:
+            b.reset_error(q, 0.3, 0.2)
+        else:
+            b.measure(q)
+    circ = b.build()
+    shots = 32
+    coins, noise = S.streams_for(circ, 4, range(shots))
+    orec, _ = oracle.sample(circ, coins, noise)
+    cid = sim.compile(circ)
+    for eng in (B.ENGINE_RESIDENT, B.ENGINE_LAYERED):
+        rec = B.records_to_numpy(sim.sample(cid, circ, shots, coins, noise, engine=eng))
+        sim.sync()
+        assert np.array_equal(rec, orec), eng
+
+
+def test_empty_and_measure_only(sim):
+    b = C.Builder(4)
+    b.tick()
+    circ = b.build()
+    cid = sim.compile(circ)
+    rec = sim.sample(cid, circ, 3, np.zeros((3, 1), np.uint64), np.zeros((3, 1), np.uint32))
+    sim.sync()
+    assert not B.records_to_numpy(rec).any()
+    b = C.Builder(70)
+    for q in range(70):
+        b.measure(q)
+    circ = b.build()
+    cid = sim.compile(circ)
+    for eng in (B.ENGINE_RESIDENT, B.ENGINE_LAYERED):
+        rec = sim.sample(cid, circ, 2, np.full((2, 2), 2 ** 64 - 1, np.uint64),
+                         np.zeros((2, 1), np.uint32), engine=eng)
+        sim.sync()
+        assert not B.records_to_numpy(rec).any()
+
+
+def test_host_validation_errors(sim):
+    b = C.Builder(3)
+    b.gate2(C.CX, 1, 1)
+    with pytest.raises(B.StabError) as e:
+        sim.compile(b.build())
+    assert e.value.code == B.ERR_ARG
+    circ = C.ghz(5)
+    cid = sim.compile(circ)
+    short = sim.to_dev(np.zeros((2, 1), np.uint64))
+    rec = sim.record_buffer(2, 1)
+    st = B.make_streams(B.STREAM_BUFFER, coins=short)
+    st.coin_words = 0
+    with pytest.raises(B.StabError) as e:
+        B.stab_sample(sim.ctx, cid, 2, st, rec)
+    assert e.value.code == B.ERR_STREAM_SHORT
