@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark: rotated surface-code Z-memory at distance 71 (10081 qubits,
+71 syndrome rounds, DEPOLARIZE1/2 p=1e-3 after every H/CNOT), one shot per
+step, simulated end to end through the C ABI (stab_sample, layered engine):
+tableau init, every Clifford layer, noise, measurement and reset.
+
+Prints ONE JSON line: gate+measure ops/s (value: inputs resident in HBM;
+e2e: host buffers through stab_sample_host), the dominant kernel's roofline,
+the CPU oracle on a bounded sample, clocks, kernel launches, and the batched
+(mixed-distance, one persistent launch) vs plain shots/s comparison.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--serve]
+
+Under torchrun (N > 1) every rank simulates its own shots on its own GPU
+(replicas; no collective on the data path); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_03092_gb300 import circuit as C  # noqa: E402
+from paper_2507_03092_gb300 import streams as S  # noqa: E402
+
+METRIC = "surface-code d=71 gate+measure ops/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_ops_per_s(circ, coins, noise, budget_s=15.0):
+    """Time the CPU oracle on a prefix of the circuit made of whole syndrome
+    rounds, sized to about ``budget_s`` seconds from a one-round probe.
+    Returns (gate+measure ops/s, description, seconds)."""
+    import oracle
+    ends = circ.meta.get("round_end") or [len(circ.ops)]
+    pre = C.prefix(circ, ends[0])
+    t0 = time.perf_counter()
+    oracle.run(pre, coins, noise)
+    t_one = time.perf_counter() - t0
+    k = int(max(1, min(len(ends), budget_s // max(t_one, 1e-6))))
+    if k > 1:
+        pre = C.prefix(circ, ends[k - 1])
+        t0 = time.perf_counter()
+        oracle.run(pre, coins, noise)
+        dt = time.perf_counter() - t0
+    else:
+        dt = t_one
+    ops = C.gate_measure_ops(pre)
+    desc = (f"first {k} of {len(ends)} syndrome rounds of the d={circ.meta.get('d')} circuit "
+            f"({ops} gate+measure ops, {len(pre.ops)} ops incl. noise), 1 thread, {dt:.2f} s")
+    return ops / dt, desc, dt
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    d = args.d
+    circ = C.surface_code_memory(d, p=args.p)
+    coins, noise = S.streams_for(circ, 0, [0])
+    for _ in range(args.warmup):
+        oracle_ops_per_s(circ, coins[0], noise[0], budget_s=args.ref_step_s)
+    vals, descs, secs = [], [], []
+    for _ in range(args.steps):
+        v, dsc, dt = oracle_ops_per_s(circ, coins[0], noise[0], budget_s=args.ref_step_s)
+        vals.append(v)
+        descs.append(dsc)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ops/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"rotated surface-code Z-memory d={d}, {d} rounds, "
+                               f"depolarizing p={args.p}, single shot", "d": d, "n": circ.n},
+        "cpu_baseline": {"value": value, "unit": "ops/s", "cores": 1, "kind": "oracle",
+                         "sample": descs[-1]},
+        "e2e": {"value": value, "unit": "ops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ batched vs plain
+def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
+    T = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
+    dists = S.shot_distances(seed, shots)
+    groups, keep, circs = [], [], {}
+    for d in (3, 5, 7, 9, 11):
+        cnt = int(np.count_nonzero(dists == d))
+        circ = C.surface_code_memory(d, t1t2=T)
+        cid = sim.compile(circ)
+        circs[d] = (circ, cid)
+        rec = sim.record_buffer(cnt, circ.record_words)
+        g = B.JobGroup()
+        g.circuit_id, g.shots = cid, cnt
+        g.streams = B.make_streams(B.STREAM_SEEDED, seed=seed + d, shot_offset=0)
+        g.d_record, g.record_words = rec.data_ptr(), circ.record_words
+        groups.append(g)
+        keep.append(rec)
+    B.stab_autotune(sim.ctx, [circs[d][1] for d in circs], 256)
+    tunes = {d: B.stab_get_tune(sim.ctx, circs[d][0].n) for d in circs}
+    B.stab_sample_batch(sim.ctx, groups)            # warm-up
+    sim.sync()
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.stab_sample_batch(sim.ctx, groups)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    sim.sync()
+    batched = shots / float(np.median(ts))
+    # plain: one tableau per launch sequence (layered engine, one shot per call),
+    # on a proportional subset of the same mix
+    per_d = {d: max(1, int(round(plain_shots * np.count_nonzero(dists == d) / shots))) for d in circs}
+    tot = 0.0
+    n_plain = 0
+    for d, k in per_d.items():
+        circ, cid = circs[d]
+        rec = sim.record_buffer(1, circ.record_words)
+        sim.sample(cid, circ, 1, seed=seed + d, engine=B.ENGINE_LAYERED, out=rec)
+        sim.sync()
+        t0 = time.perf_counter()
+        for s in range(k):
+            sim.sample(cid, circ, 1, seed=seed + d, shot_offset=s, engine=B.ENGINE_LAYERED, out=rec)
+        sim.sync()
+        tot += (time.perf_counter() - t0) * (np.count_nonzero(dists == d) / k)
+        n_plain += k
+    plain = shots / tot
+    return {"workload": "4096 shots, d uniform in {3,5,7,9,11}, d rounds, twirled T1/T2 Pauli noise",
+            "batched_shots_per_s": batched, "plain_shots_per_s": plain,
+            "speedup": batched / plain, "plain_sample_shots": n_plain,
+            "tune": {str(k): v for k, v in tunes.items()}}
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--d", type=int, default=71)
+    ap.add_argument("--p", type=float, default=1e-3)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="also replay the serving trace")
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2507_03092_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    d, p = args.d, args.p
+    circ = C.surface_code_memory(d, p=p)
+    ops_per_step = C.gate_measure_ops(circ)
+    K, W = args.steps, args.warmup
+    shots_idx = [rank * (K + W) + s for s in range(K + W)]
+    coins, noise = S.streams_for(circ, 0, shots_idx)
+
+    sim = B.Simulator(local)
+    cid = sim.compile(circ)
+    info = sim.info(cid)
+    dc, dn = sim.to_dev(coins), sim.to_dev(noise)
+    rec = sim.record_buffer(K + W, circ.record_words)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=sim.device)
+
+    def step(s, profile=False):
+        st = B.make_streams(B.STREAM_BUFFER, coins=dc[s:s + 1], noise=dn[s:s + 1])
+        B.stab_sample(sim.ctx, cid, 1, st, rec[s:s + 1], B.ENGINE_LAYERED)
+
+    for s in range(W):
+        flush.fill_(s)
+        step(s)
+    sim.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    B.stab_launch_count(sim.ctx, reset=True)
+    B.stab_engine_counters(sim.ctx, reset=True)
+    B.stab_profile(sim.ctx, 0x1F)
+    for k in range(5):
+        B.stab_profile_read(sim.ctx, k, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    t_wall0 = time.perf_counter()
+    for s in range(W, W + K):
+        flush.fill_(s)                       # L2 flush between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(s)
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    sim.sync()
+    B.stab_profile(sim.ctx, 0)
+    launches = B.stab_launch_count(sim.ctx, reset=True)
+    counters = B.stab_engine_counters(sim.ctx, reset=True)
+    kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in range(5)}
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_dev], device=sim.device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = ops_per_step * K * world / t_dev
+
+    # parity spot check of the timed shots (first rounds, oracle) is done by the
+    # tests; here only the noiseless-free sanity: the record is non-trivial.
+    recs = B.records_to_numpy(rec)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region
+    pin_c = torch.from_numpy(coins.view(np.int64)).pin_memory()
+    pin_n = torch.from_numpy(noise.view(np.int32)).pin_memory()
+    cnp, nnp = pin_c.numpy().view(np.uint64), pin_n.numpy().view(np.uint32)
+    host_rec = np.zeros((1, circ.record_words), np.uint64)
+    import ctypes
+    lib = B.lib()
+    e2e_t = []
+    for s in range(min(K, 3) + 1):
+        flush.fill_(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = lib.stab_sample_host(sim.ctx, cid, 1, cnp[s].ctypes.data_as(ctypes.c_void_p), cnp.shape[1],
+                                  nnp[s].ctypes.data_as(ctypes.c_void_p), nnp.shape[1],
+                                  host_rec.ctypes.data_as(ctypes.c_void_p), circ.record_words,
+                                  B.ENGINE_LAYERED)
+        dt = time.perf_counter() - t0
+        B._check(rc)
+        if s:
+            e2e_t.append(dt)
+        if not np.array_equal(host_rec[0], recs[s]):
+            raise AssertionError("host-buffer call gave a different record than the device-buffer call")
+    e2e_val = ops_per_step * world / float(np.mean(e2e_t))
+
+    # ---- roofline of the dominant kernel
+    dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
+    ds = kstats[dom]
+    hbm, src = peaks()
+    roof = None
+    if ds["launches"] and ds["alg_bytes"] > 0:
+        ach = ds["alg_bytes"] / (ds["total_ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": src, "traffic": None,
+                "alg_bytes_per_launch": ds["alg_bytes"] / ds["launches"],
+                "avg_launch_us": 1e3 * ds["total_ms"] / ds["launches"]}
+    else:
+        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "peak_source": src, "traffic": None,
+                "note": "dominant kernel has no algorithmic-byte model in the library"}
+    gr = kstats.get("k_gate_run")
+    gate_roof = None
+    if gr and gr["launches"]:
+        ach = gr["alg_bytes"] / (gr["total_ms"] / 1e3) / 1e9
+        gate_roof = {"kernel": "k_gate_run", "achieved": ach, "peak": hbm, "frac": ach / hbm,
+                     "unit": "GB/s", "launches": gr["launches"],
+                     "avg_launch_us": 1e3 * gr["total_ms"] / gr["launches"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "ops/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"rotated surface-code Z-memory d={d}, {d} rounds, "
+                               f"depolarizing p={p}, single shot per step",
+                   "d": d, "n": circ.n, "ops_per_step": ops_per_step,
+                   "noise_ops_per_step": circ.n_noise, "layers": info["n_layers"],
+                   "engine": "layered", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "streams": "device-resident coin/noise buffers"},
+        "e2e": {"value": e2e_val, "unit": "ops/s",
+                "h2d_bytes_per_step": int(coins[0].nbytes + noise[0].nbytes),
+                "d2h_bytes_per_step": int(circ.record_words * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+        "roofline_gate_run": gate_roof,
+        "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()},
+        "engine_counters_per_step": {k: v / K for k, v in counters.items()},
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and not args.no_cpu:
+        v, desc, _ = oracle_ops_per_s(circ, coins[0], noise[0], budget_s=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": "ops/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0 and not args.no_extras:
+        try:
+            line["batched"] = batched_vs_plain(sim, B, torch)
+        except Exception as ex:       # report, do not hide
+            line["batched"] = {"error": repr(ex)}
+    if rank == 0 and args.serve:
+        from paper_2507_03092_gb300 import serve_trace
+        line["serve"] = serve_trace.replay(sim, B, torch)
+    sim.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

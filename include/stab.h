@@ -222,6 +222,38 @@ int stab_serve_poll(stab_ctx *ctx, stab_request_status *done, size_t cap, size_t
 int stab_serve_drain(stab_ctx *ctx, double timeout_s);
 int stab_serve_stop(stab_ctx *ctx);
 
+/* ---- instrumentation (benchmarks) ---- */
+#define STAB_KERNEL_GATE_RUN 0u  /* layered engine: run of gate layers on one 32-row slice */
+#define STAB_KERNEL_MEAS_DET 1u  /* layered engine: pivot test + deterministic outcomes */
+#define STAB_KERNEL_MEAS_RAND 2u /* layered engine: random measurements of a layer */
+#define STAB_KERNEL_OTHER 3u     /* layered engine: init, transposes, column gather, conditional Paulis */
+#define STAB_KERNEL_RESIDENT 4u  /* resident engine persistent launch */
+#define STAB_N_KERNEL_KINDS 5u
+
+typedef struct stab_kernel_stats {
+    uint64_t launches;    /* launches timed since the last reset */
+    double total_ms;      /* sum of their CUDA-event durations */
+    double alg_bytes;     /* algorithmic bytes those launches had to move (gate runs:
+                             every touched column's x and z read and written once, the
+                             sign column read and written, one 4-byte draw per noise op) */
+} stab_kernel_stats;
+
+/* Bracket every launch of the kernel kinds in `kind_mask` (bit k = kind k)
+ * with CUDA events on its stream; 0 disables. */
+int stab_profile(stab_ctx *ctx, uint32_t kind_mask);
+/* Synchronize and return the accumulated statistics of one kernel kind. */
+int stab_profile_read(stab_ctx *ctx, uint32_t kind, stab_kernel_stats *out, int reset);
+/* Kernel launches issued by this context since the last reset. */
+int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
+/* Layered-engine work counters since the last reset (synchronizes):
+ * [0] random-measurement waves, [1] random measurements applied in waves,
+ * [2] measurements found deterministic inside the random-measurement kernel,
+ * [3] deterministic measurements resolved by the batched kernel,
+ * [4] sum over deterministic measurements of |K| (stabilizer rows multiplied),
+ * [5] sum over random measurements of |A| (rows that received a rowsum),
+ * [6] cached pivots recomputed, [7] reserved.  n <= 8 entries are written. */
+int stab_engine_counters(stab_ctx *ctx, uint64_t *out, size_t n, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,21 @@ class Tune(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_[:3]}
 
 
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"launches": int(self.launches), "total_ms": float(self.total_ms),
+                "alg_bytes": float(self.alg_bytes)}
+
+
+KERNEL_GATE_RUN, KERNEL_MEAS_DET, KERNEL_MEAS_RAND, KERNEL_OTHER, KERNEL_RESIDENT = range(5)
+KERNEL_NAMES = {KERNEL_GATE_RUN: "k_gate_run", KERNEL_MEAS_DET: "k_meas_det",
+                KERNEL_MEAS_RAND: "k_meas_rand", KERNEL_OTHER: "other",
+                KERNEL_RESIDENT: "k_resident"}
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("n_streams", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
@@ -111,6 +126,10 @@ _SIGS = {
     "stab_serve_poll": (I32, [P, ctypes.POINTER(RequestStatus), SZ, ctypes.POINTER(SZ)]),
     "stab_serve_drain": (I32, [P, ctypes.c_double]),
     "stab_serve_stop": (I32, [P]),
+    "stab_profile": (I32, [P, U32]),
+    "stab_profile_read": (I32, [P, U32, ctypes.POINTER(KernelStats), I32]),
+    "stab_launch_count": (I32, [P, PU64, I32]),
+    "stab_engine_counters": (I32, [P, PU64, SZ, I32]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -294,6 +313,32 @@ def stab_serve_drain(ctx, timeout_s=600.0):
 
 def stab_serve_stop(ctx):
     _check(lib().stab_serve_stop(ctx))
+
+
+def stab_profile(ctx, kind_mask):
+    _check(lib().stab_profile(ctx, int(kind_mask)))
+
+
+def stab_profile_read(ctx, kind, reset=True) -> dict:
+    st = KernelStats()
+    _check(lib().stab_profile_read(ctx, int(kind), ctypes.byref(st), 1 if reset else 0))
+    return st.as_dict()
+
+
+def stab_launch_count(ctx, reset=True) -> int:
+    c = ctypes.c_uint64()
+    _check(lib().stab_launch_count(ctx, ctypes.byref(c), 1 if reset else 0))
+    return int(c.value)
+
+
+COUNTER_NAMES = ("waves", "wave_ops", "det_in_wave_kernel", "det", "sum_K", "sum_A",
+                 "pivot_recomputes", "reserved")
+
+
+def stab_engine_counters(ctx, reset=True) -> dict:
+    arr = (ctypes.c_uint64 * 8)()
+    _check(lib().stab_engine_counters(ctx, arr, 8, 1 if reset else 0))
+    return {k: int(v) for k, v in zip(COUNTER_NAMES, arr)}
 
 
 # ---------------------------------------------------------------- convenience

@@ -256,6 +256,7 @@ def surface_code_memory(d: int, rounds: int | None = None, p: float = 0.0,
     b.tick()
     meas_index = {}      # (round, ancilla) -> record ordinal
     rec = 0
+    round_end = []       # op count at the end of each round (prefix lengths)
     for rd in range(rounds):
         if rd > 0:
             for q in anc_sorted:
@@ -299,13 +300,14 @@ def surface_code_memory(d: int, rounds: int | None = None, p: float = 0.0,
         pc1(anc_sorted, tm)
         idle(anc_sorted, tm)
         b.tick()
+        round_end.append(len(b._ops))
     data_index = {}
     for q in lay.data:
         b.measure(q)
         data_index[q] = rec
         rec += 1
     c = b.build(kind="surface_code_memory", d=d, rounds=rounds, p=p,
-                t1t2=t1t2, layout=lay)
+                t1t2=t1t2, layout=lay, round_end=round_end)
     c.meta["detectors"] = surface_detectors(lay, rounds, meas_index, data_index)
     c.meta["observable"] = [data_index[q] for q in range(d)]   # Z along row 0
     return c
@@ -461,6 +463,17 @@ def ghz(n: int) -> Circuit:
     for q in range(n):
         b.measure(q)
     return b.build(kind="ghz")
+
+
+def prefix(c: Circuit, n_ops: int) -> Circuit:
+    """The first ``n_ops`` ops of ``c`` (same qubits and parameter table)."""
+    return Circuit(c.n, c.ops[:n_ops].copy(), c.params, {"prefix_of": c.meta.get("kind"), "n_ops": n_ops})
+
+
+def gate_measure_ops(c: Circuit) -> int:
+    """Clifford gates plus M and R ops (noise channels and TICKs excluded)."""
+    k = c.ops["kind"]
+    return int(np.count_nonzero(np.isin(k, ONE_QUBIT_GATES + TWO_QUBIT_GATES + (M, R))))
 
 
 def concat(circuits: list[Circuit]) -> Circuit:

@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 namespace stab {
@@ -39,6 +41,47 @@ void DevBuf::release() {
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
+}
+
+cudaEvent_t KernelProf::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void KernelProf::begin(uint32_t kind, cudaStream_t s, Rec &r) {
+    r.kind = kind;
+    r.e0 = take();
+    r.e1 = take();
+    r.bytes = 0.0;
+    cudaEventRecord(r.e0, s);
+}
+
+void KernelProf::end(Rec &r, cudaStream_t s, double b) {
+    cudaEventRecord(r.e1, s);
+    r.bytes = b;
+    pending.push_back(r);
+}
+
+int KernelProf::collect() {
+    for (auto &r : pending) {
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e) return cuda_fail(e, "waiting for a profiling event");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.e0, r.e1);
+        n[r.kind]++;
+        ms[r.kind] += t;
+        bytes[r.kind] += r.bytes;
+        pool.push_back(r.e0);
+        pool.push_back(r.e1);
+    }
+    pending.clear();
+    return STAB_OK;
 }
 
 const HostProg *find_prog(stab_ctx *ctx, uint64_t id) {
@@ -81,14 +124,33 @@ int check_streams(const HostProg &p, const stab_streams *s, uint32_t shots) {
 }
 
 static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t count) {
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t mm = std::max<uint32_t>(1, p.dev.max_meas);
     const size_t words = mm * p.CW * count, items = mm * count;
-    const size_t bytes = 4 * words + 2 * items + 512;
+    const size_t first_b = 3 * 4 * (size_t)64 * p.H * count;   // first-B, first-pivot, row claims
+    const size_t qmap_b = 4 * (size_t)p.n * count;
+    const size_t piv_b = 4 * items, bsz_b = 4 * items, stale_b = items;
+    const size_t sup_b = 2 * (size_t)SUPCAP * items;
+    const size_t detz_b = 4 * (size_t)32 * 2 * p.H * count;
+    const size_t ev_b = 4 * (size_t)std::max<uint32_t>(1, p.dev.ev_total) * count;
+    const size_t cnt_b = 4 * (size_t)std::max<size_t>(1, p.layers.size()) * count;
+    const size_t bytes = up(4 * words) + up(2 * items) + up(first_b) + up(ev_b) + up(cnt_b) +
+                         up(qmap_b) + up(detz_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b);
     int rc = buf.ensure(bytes);
     if (rc) return rc;
-    ms.cols = (uint32_t *)buf.p;
-    ms.stat = (uint8_t *)buf.p + ((4 * words + 255) & ~(size_t)255);
-    ms.out = ms.stat + items;
+    char *b = (char *)buf.p;
+    ms.cols = (uint32_t *)b; b += up(4 * words);
+    ms.stat = (uint8_t *)b;
+    ms.out = ms.stat + items; b += up(2 * items);
+    ms.first = (int *)b; b += up(first_b);
+    ms.ev = (uint32_t *)b; b += up(ev_b);
+    ms.ev_cnt = (uint32_t *)b; b += up(cnt_b);
+    ms.qmap = (int *)b; b += up(qmap_b);
+    ms.detz = (uint32_t *)b; b += up(detz_b);
+    ms.mpiv = (uint32_t *)b; b += up(piv_b);
+    ms.mbsz = (uint32_t *)b; b += up(bsz_b);
+    ms.mstale = (uint8_t *)b; b += up(stale_b);
+    ms.msup = (uint16_t *)b;
     ms.cap_words = words;
     ms.cap_items = items;
     return STAB_OK;
@@ -97,6 +159,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
 stab_tune default_tune(const stab_ctx *ctx, uint32_t n) {
     stab_tune t{};
     const uint32_t CW = 2 * ((n + 31) / 32);
+    (void)CW;
     t.words_per_thread = CW >= 8 ? 2 : 1;
     t.group_threads = n <= 64 ? 32 : (n <= 256 ? 64 : 128);
     const size_t per = resident_smem_per_tableau(n);
@@ -104,6 +167,7 @@ stab_tune default_tune(const stab_ctx *ctx, uint32_t n) {
     while (tpc > 1 && per * tpc > ctx->lc.smem_optin) tpc--;
     if (t.group_threads > 32) tpc = std::min<uint32_t>(tpc, 15);
     t.tableaux_per_cta = tpc;
+    while (t.tableaux_per_cta > 1 && !resident_shape_ok(n, t, ctx->lc)) t.tableaux_per_cta--;
     return t;
 }
 
@@ -113,38 +177,54 @@ stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n) {
     return default_tune(ctx, n);
 }
 
-static int upload_prog(HostProg &P) {
+// One device allocation holds every array of a compiled program, followed by
+// its DevProg descriptor (used by the resident engine's job table).
+static size_t prog_layout(const HostProg &P, size_t off[7]) {
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t bl = up(P.layers.size() * sizeof(Layer) + 1);
-    const size_t bg = up(P.gitems.size() * sizeof(GItem) + 1);
-    const size_t bm = up(P.mitems.size() * sizeof(MItem) + 1);
-    const size_t bt = up(P.thr.size() * sizeof(Thr) + 1);
-    const size_t bd = up(sizeof(DevProg));
-    if (cudaMalloc(&P.dmem, bl + bg + bm + bt + bd) != cudaSuccess) {
+    const size_t sz[6] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
+                          P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
+                          P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t)};
+    size_t o = 0;
+    for (int k = 0; k < 6; k++) {
+        off[k] = o;
+        o += up(sz[k] + 1);
+    }
+    off[6] = o;
+    return o + up(sizeof(DevProg));
+}
+
+static int upload_prog(HostProg &P) {
+    size_t off[7];
+    const size_t total = prog_layout(P, off);
+    if (cudaMalloc(&P.dmem, total) != cudaSuccess) {
         cudaGetLastError();
         P.dmem = nullptr;
         return fail(STAB_ERR_OOM, "cudaMalloc for the compiled circuit failed");
     }
     char *b = (char *)P.dmem;
-    P.dev.layers = (const Layer *)b;
-    P.dev.gitems = (const GItem *)(b + bl);
-    P.dev.mitems = (const MItem *)(b + bl + bg);
-    P.dev.thr = (const Thr *)(b + bl + bg + bm);
+    P.dev.layers = (const Layer *)(b + off[0]);
+    P.dev.gitems = (const GItem *)(b + off[1]);
+    P.dev.mitems = (const MItem *)(b + off[2]);
+    P.dev.thr = (const Thr *)(b + off[3]);
+    P.dev.sitems = (const SItem *)(b + off[4]);
+    P.dev.item_layer = (const uint32_t *)(b + off[5]);
+    const void *src[6] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
+                          P.sitems.data(), P.item_layer.data()};
+    const size_t sz[6] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
+                          P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
+                          P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t)};
     cudaError_t e = cudaSuccess;
-    if (!P.layers.empty()) e = cudaMemcpy(b, P.layers.data(), P.layers.size() * sizeof(Layer), cudaMemcpyHostToDevice);
-    if (!e && !P.gitems.empty()) e = cudaMemcpy(b + bl, P.gitems.data(), P.gitems.size() * sizeof(GItem), cudaMemcpyHostToDevice);
-    if (!e && !P.mitems.empty()) e = cudaMemcpy(b + bl + bg, P.mitems.data(), P.mitems.size() * sizeof(MItem), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(b + bl + bg + bm, P.thr.data(), P.thr.size() * sizeof(Thr), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(b + bl + bg + bm + bt, &P.dev, sizeof(DevProg), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 6 && !e; k++)
+        if (sz[k]) e = cudaMemcpy(b + off[k], src[k], sz[k], cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(b + off[6], &P.dev, sizeof(DevProg), cudaMemcpyHostToDevice);
     if (e) return cuda_fail(e, "uploading the compiled circuit");
     return STAB_OK;
 }
 
 static const DevProg *dev_desc(const HostProg &P) {
-    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t off = up(P.layers.size() * sizeof(Layer) + 1) + up(P.gitems.size() * sizeof(GItem) + 1) +
-                       up(P.mitems.size() * sizeof(MItem) + 1) + up(P.thr.size() * sizeof(Thr) + 1);
-    return (const DevProg *)((char *)P.dmem + off);
+    size_t off[7];
+    prog_layout(P, off);
+    return (const DevProg *)((char *)P.dmem + off[6]);
 }
 
 int run_layered_shots(stab_ctx *ctx, const HostProg &p, uint32_t shots, const stab_streams &st,
@@ -170,7 +250,7 @@ int run_layered_shots(stab_ctx *ctx, const HostProg &p, uint32_t shots, const st
         b.count = cnt;
         int rc = ensure_ms(ms, ms_buf, p, cnt);
         if (rc) return rc;
-        cudaError_t e = layered_init(b, s);
+        cudaError_t e = layered_init(b, s, &ctx->prof);
         if (e) return cuda_fail(e, "layered init");
         DevStreams ds = to_dev(st);
         if (st.mode == STAB_STREAM_SEEDED) ds.shot_offset += s0;
@@ -179,7 +259,7 @@ int run_layered_shots(stab_ctx *ctx, const HostProg &p, uint32_t shots, const st
             if (ds.noise) ds.noise += (size_t)s0 * ds.noise_stride;
         }
         e = layered_run(p, b, ms, ds, (unsigned long long *)(d_record + (size_t)s0 * record_words),
-                        record_words, ctx->d_err, ctx->lc, s);
+                        record_words, ctx->d_err, ctx->lc, s, &ctx->prof, ctx->d_stats);
         if (e) return cuda_fail(e, "layered run");
         work.rm_valid = b.rm_valid;
     }
@@ -232,7 +312,8 @@ int run_resident_groups(stab_ctx *ctx, const stab_job_group *groups, size_t n_gr
     e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "job table upload");
     stab_tune t = force ? *force : lookup_tune(ctx, max_n);
-    e = resident_run((const ResJob *)jobs.p, (uint32_t)flat.size(), max_n, t, counter, ctx->d_err, ctx->lc, s);
+    e = resident_run((const ResJob *)jobs.p, (uint32_t)flat.size(), max_n, t, counter, ctx->d_err, ctx->lc, s,
+                     &ctx->prof);
     if (e) return cuda_fail(e, "resident launch");
     return STAB_OK;
 }
@@ -281,7 +362,19 @@ int stab_create(stab_ctx **out, int device, void *cuda_stream) {
         return fail(STAB_ERR_OOM, "cudaMalloc for the error flag failed");
     }
     ctx->d_counter = (unsigned int *)((char *)ctx->d_err + 128);
+    ctx->d_stats = (unsigned long long *)((char *)ctx->d_err + 192);
     cudaMemset(ctx->d_err, 0, 256);
+    if (const char *env = getenv("STAB_WAVE_CAPS")) {
+        WaveCaps c;
+        unsigned v[5];
+        unsigned w6 = 0;
+        const int got = sscanf(env, "%u,%u,%u,%u,%u,%u", &v[0], &v[1], &v[2], &v[3], &v[4], &w6);
+        if (got >= 5) {
+            c.pcap = v[0]; c.wcap = v[1]; c.paircap = v[2]; c.jcap = v[3]; c.mark_budget = v[4];
+            if (got == 6) c.window = w6;
+            set_wave_caps(c);
+        }
+    }
     *out = ctx;
     return STAB_OK;
 }
@@ -304,6 +397,8 @@ void stab_destroy(stab_ctx *ctx) {
         ctx->stage_coins.release();
         ctx->stage_noise.release();
         ctx->stage_rec.release();
+        ctx->prof.collect();
+        for (auto e : ctx->prof.pool) cudaEventDestroy(e);
         if (ctx->d_err) cudaFree(ctx->d_err);
     }
     delete ctx;
@@ -379,7 +474,7 @@ int stab_tableau_init(stab_ctx *ctx, uint32_t n, uint32_t count) {
     cudaStreamSynchronize(ctx->stream);
     int rc = batch_alloc(ctx->resident, n, count, &err);
     if (rc) return fail(rc, err);
-    cudaError_t e = layered_init(ctx->resident, ctx->stream);
+    cudaError_t e = layered_init(ctx->resident, ctx->stream, &ctx->prof);
     if (e) return cuda_fail(e, "tableau init");
     return STAB_OK;
 }
@@ -401,7 +496,7 @@ int stab_apply_circuit(stab_ctx *ctx, uint64_t circuit_id, const stab_streams *s
     cudaError_t e = cudaMemsetAsync(d_record, 0, (size_t)b.count * record_words * 8, ctx->stream);
     if (e) return cuda_fail(e, "clearing records");
     e = layered_run(*p, b, ctx->ms, to_dev(*streams), (unsigned long long *)d_record, record_words,
-                    ctx->d_err, ctx->lc, ctx->stream);
+                    ctx->d_err, ctx->lc, ctx->stream, &ctx->prof, ctx->d_stats);
     if (e) return cuda_fail(e, "apply_circuit");
     return STAB_OK;
 }
@@ -543,7 +638,7 @@ int stab_set_tune(stab_ctx *ctx, uint32_t n, const stab_tune *t) {
     if (!t) return fail(STAB_ERR_ARG, "tune is NULL");
     const uint32_t G = t->group_threads, tpc = t->tableaux_per_cta, wpt = t->words_per_thread;
     if (!(G == 32 || G == 64 || G == 128 || G == 256) || tpc < 1 || G * tpc > 1024 ||
-        (G > 32 && tpc > 15) || !(wpt == 1 || wpt == 2 || wpt == 4))
+        (G > 32 && tpc > 15) || !(wpt == 1 || wpt == 2 || wpt == 4) || !resident_shape_ok(n, *t, ctx->lc))
         return fail(STAB_ERR_ARG, "invalid resident launch shape");
     if (resident_smem_per_tableau(n) * tpc > ctx->lc.smem_optin)
         return fail(STAB_ERR_ARG, "shape needs more shared memory than a CTA has");
@@ -580,6 +675,7 @@ int stab_autotune(stab_ctx *ctx, const uint64_t *circuit_ids, size_t n_circuits,
                     if (G * tpc > 1024 || (G > 32 && tpc > 15) || per * tpc > ctx->lc.smem_optin) continue;
                     if (wpt > p->CW) continue;
                     stab_tune t{G, tpc, wpt, 0};
+                    if (!resident_shape_ok(p->n, t, ctx->lc)) continue;
                     // one warm-up, then time
                     int rc2 = run_resident_groups(ctx, &g, 1, &t, ctx->stream, ctx->jobs_buf, ctx->d_counter);
                     if (rc2) { rec.release(); return rc2; }
@@ -598,6 +694,48 @@ int stab_autotune(stab_ctx *ctx, const uint64_t *circuit_ids, size_t n_circuits,
     }
     cudaStreamSynchronize(ctx->stream);
     rec.release();
+    return STAB_OK;
+}
+
+int stab_profile(stab_ctx *ctx, uint32_t kind_mask) {
+    CTX_GUARD;
+    ctx->prof.mask = kind_mask;
+    return STAB_OK;
+}
+
+int stab_profile_read(stab_ctx *ctx, uint32_t kind, stab_kernel_stats *out, int reset) {
+    CTX_GUARD;
+    if (!out || kind >= STAB_N_KERNEL_KINDS) return fail(STAB_ERR_ARG, "bad profile_read arguments");
+    int rc = ctx->prof.collect();
+    if (rc) return rc;
+    out->launches = ctx->prof.n[kind];
+    out->total_ms = ctx->prof.ms[kind];
+    out->alg_bytes = ctx->prof.bytes[kind];
+    if (reset) {
+        ctx->prof.n[kind] = 0;
+        ctx->prof.ms[kind] = 0.0;
+        ctx->prof.bytes[kind] = 0.0;
+    }
+    return STAB_OK;
+}
+
+int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset) {
+    CTX_GUARD;
+    if (!count) return fail(STAB_ERR_ARG, "count is NULL");
+    *count = ctx->prof.launches;
+    if (reset) ctx->prof.launches = 0;
+    return STAB_OK;
+}
+
+int stab_engine_counters(stab_ctx *ctx, uint64_t *out, size_t n, int reset) {
+    CTX_GUARD;
+    if (!out || n == 0) return fail(STAB_ERR_ARG, "bad counter buffer");
+    unsigned long long v[DC_N];
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (!e) e = cudaMemcpy(v, ctx->d_stats, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "reading engine counters");
+    for (size_t i = 0; i < n && i < (size_t)DC_N; i++) out[i] = v[i];
+    if (reset) cudaMemset(ctx->d_stats, 0, sizeof(v));
     return STAB_OK;
 }
 

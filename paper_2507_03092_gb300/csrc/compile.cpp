@@ -168,21 +168,70 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         *err = "circuit too long (more than 2^32 measurements or noise draws)";
         return STAB_ERR_UNSUPPORTED;
     }
+    if (n > 65535) {
+        // the packed items below hold 16-bit qubit indices; engines reject such n anyway
+    }
+    // ---- packed items, item -> layer map, noise-event capacities ----
+    P.sitems.resize(P.gitems.size());
+    P.item_layer.resize(P.gitems.size());
+    uint32_t ev_total = 0;
+    for (uint32_t l = 0; l < P.layers.size(); l++) {
+        Layer &L = P.layers[l];
+        L.ev_off = ev_total;
+        L.ev_cap = 0;
+        L.n_noisy = 0;
+        if (L.type != LT_GATE) continue;
+        for (uint32_t i = L.first; i < L.first + L.count; i++) {
+            const GItem &g = P.gitems[i];
+            P.sitems[i].ab = (g.a & 0xffffu) | ((g.b & 0xffffu) << 16);
+            P.sitems[i].g = g.gate;
+            P.item_layer[i] = l;
+            if (g.nn) L.n_noisy++;
+        }
+        // room for the expected events with a wide margin; a layer whose events
+        // overflow falls back to evaluating every draw in the slice kernel
+        if (L.n_noisy) L.ev_cap = std::min<uint32_t>(2 * L.n_noisy, 64 + L.n_noisy / 8);
+        ev_total += L.ev_cap;
+    }
+    P.dev.ev_total = ev_total;
     // ---- runs for the layered engine ----
     uint32_t max_meas = 0, max_g = 0, n_gl = 0, n_ml = 0;
     for (uint32_t l = 0; l < P.layers.size(); l++) {
         const Layer &L = P.layers[l];
         if (L.type == LT_MEAS) {
-            P.runs.push_back(Run{LT_MEAS, l, l + 1});
+            P.runs.push_back(Run{LT_MEAS, l, l + 1, 0.0});
             max_meas = std::max(max_meas, L.count);
             n_ml++;
         } else {
             if (!P.runs.empty() && P.runs.back().type == LT_GATE && P.runs.back().l1 == l)
                 P.runs.back().l1 = l + 1;
             else
-                P.runs.push_back(Run{LT_GATE, l, l + 1});
+                P.runs.push_back(Run{LT_GATE, l, l + 1, 0.0});
             max_g = std::max(max_g, L.count);
             n_gl++;
+        }
+    }
+    // Algorithmic bytes of a gate run (per tableau): every column the run
+    // touches has its x and z bits over the 2n rows read and written once, the
+    // sign column is read and written once, and each noise op reads one 4-byte
+    // draw.  (Column = 2n bits = n/4 bytes.)
+    {
+        std::vector<uint32_t> seen(n, 0xffffffffu);
+        const double col_bytes = 2.0 * n / 8.0;
+        for (uint32_t ri = 0; ri < P.runs.size(); ri++) {
+            Run &R = P.runs[ri];
+            if (R.type != LT_GATE) continue;
+            uint64_t cols = 0, draws = 0;
+            for (uint32_t l = R.l0; l < R.l1; l++) {
+                const Layer &L = P.layers[l];
+                for (uint32_t i = L.first; i < L.first + L.count; i++) {
+                    const GItem &g = P.gitems[i];
+                    if (seen[g.a] != ri) { seen[g.a] = ri; cols++; }
+                    if (seen[g.b] != ri) { seen[g.b] = ri; cols++; }
+                    draws += g.nn;
+                }
+            }
+            R.alg_bytes = (double)cols * 2 * 2 * col_bytes + 2 * col_bytes + 4.0 * (double)draws;
         }
     }
     stab_circuit_info &I = P.info;

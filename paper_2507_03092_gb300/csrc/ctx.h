@@ -37,7 +37,9 @@ struct stab_ctx {
     stab::DevBuf ms_buf, jobs_buf, stage_coins, stage_noise, stage_rec;
     int *d_err = nullptr;
     unsigned int *d_counter = nullptr;
+    unsigned long long *d_stats = nullptr;          // DC_* counters
     std::map<uint32_t, stab_tune> tune;              // bucket ceil(n/32) -> shape
+    stab::KernelProf prof;
     stab::ServeState *serve = nullptr;
 };
 

@@ -99,13 +99,15 @@ __device__ __forceinline__ uint32_t apply_item(const GItem &g, uint32_t &xa, uin
                                                const DevStreams &st, uint32_t shot,
                                                const Thr *thr) {
     uint32_t r = apply_gate(g.gate, xa, za, xb, zb);
-    for (int k = 0; k < g.nn; k++) {
-        uint32_t u = noise_word(st, shot, g.nl[k]);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if (k >= g.nn) break;
+        const uint32_t u = noise_word(st, shot, k ? g.nl[1] : g.nl[0]);
         int pa, pb;
-        noise_paulis(g.nk[k], u, thr[g.np[k]], pa, pb);
+        noise_paulis(k ? g.nk[1] : g.nk[0], u, thr[k ? g.np[1] : g.np[0]], pa, pb);
         if (!(pa | pb)) continue;
         int Pa = 0, Pb = 0;
-        switch (g.nt[k]) {
+        switch (k ? g.nt[1] : g.nt[0]) {
         case NT_A: Pa = pa; break;
         case NT_B: Pb = pa; break;
         case NT_AB: Pa = pa; Pb = pb; break;

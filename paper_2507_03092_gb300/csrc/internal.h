@@ -56,6 +56,14 @@ static_assert(sizeof(MItem) == 24, "MItem layout");
 
 struct Layer {
     uint32_t type, first, count, has_cond;   // has_cond: R or RESET_ERR items present
+    uint32_t ev_off, ev_cap;                 // gate layers: noise-event slots [ev_off, ev_off+ev_cap)
+    uint32_t n_noisy, pad;                   // items carrying noise
+};
+
+// Packed gate item for the layered engine's slice kernel (noise handled by
+// the event pre-pass): ab = a | b << 16, g = gate kind.
+struct SItem {
+    uint32_t ab, g;
 };
 
 struct Thr {              // floor(p_i * 2^32) for the three parameters of a row
@@ -68,13 +76,17 @@ struct DevProg {          // by-value descriptor handed to kernels
     const GItem *gitems;
     const MItem *mitems;
     const Thr *thr;
+    const SItem *sitems;      // packed copy of gitems (layered engine)
+    const uint32_t *item_layer; // layer index of each gate item
     uint32_t record_words, coin_words, noise_words, max_meas;
-    uint32_t max_gitems, n_gitems, n_mitems, pad;
+    uint32_t max_gitems, n_gitems, n_mitems, ev_total;
 };
 
 struct Run {              // layered engine schedule entry
     uint32_t type;        // LT_GATE: layers [l0, l1); LT_MEAS: layer l0
     uint32_t l0, l1;
+    double alg_bytes;     // LT_GATE, per tableau: distinct columns x,z read+written,
+                          // sign column read+written, 4 bytes per noise draw
 };
 
 struct HostProg {
@@ -84,6 +96,8 @@ struct HostProg {
     std::vector<GItem> gitems;
     std::vector<MItem> mitems;
     std::vector<Thr> thr;
+    std::vector<SItem> sitems;
+    std::vector<uint32_t> item_layer;
     std::vector<Run> runs;
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
@@ -132,6 +146,15 @@ struct MeasScratch {
     uint32_t *cols = nullptr;     // [count][max_meas][CW]
     uint8_t *stat = nullptr;      // [count][max_meas]
     uint8_t *out = nullptr;       // [count][max_meas]
+    int *first = nullptr;         // [count][3][64H] wave marking: column rows, pivots, row claims
+    int *qmap = nullptr;          // [count][n] qubit -> item of the current layer
+    uint32_t *detz = nullptr;     // [count][32][2H] deterministic-outcome scratch
+    uint32_t *mpiv = nullptr;     // [count][max_meas] cached pivot (slot - 32H) or ~0
+    uint32_t *mbsz = nullptr;     // [count][max_meas] cached |x-column support|
+    uint8_t *mstale = nullptr;    // [count][max_meas] cache invalid
+    uint16_t *msup = nullptr;     // [count][max_meas][SUPCAP] column support rows (if small)
+    uint32_t *ev = nullptr;       // [count][ev_total] noise events
+    uint32_t *ev_cnt = nullptr;   // [count][n_layers] noise-event counts
     size_t cap_words = 0, cap_items = 0;
 };
 
@@ -140,15 +163,48 @@ struct LaunchCfg {
     size_t smem_optin = 0;
 };
 
+// Capacities of the random-measurement wave kernel's shared-memory lists.
+// Overflowing a list is handled by slower fallback loops; tests shrink the
+// capacities (STAB_WAVE_CAPS="pcap,wcap,paircap,jcap,budget") to exercise them.
+struct WaveCaps {
+    static constexpr uint32_t PCAP_MAX = 8192, WCAP_MAX = 1024, PAIRCAP_MAX = 4096, JCAP_MAX = 4096;
+    uint32_t pcap = PCAP_MAX;          // pending measurements considered per wave
+    uint32_t wcap = WCAP_MAX;          // measurements applied per wave
+    uint32_t paircap = PAIRCAP_MAX;    // (row, pivot) rowsum pairs listed per wave
+    uint32_t jcap = JCAP_MAX;          // measured-column updates listed per wave
+    uint32_t mark_budget = 2048;       // rows marked per wave (bounds the window)
+    uint32_t window = 128;             // pending measurements examined per wave
+};
+constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list
+void set_wave_caps(const WaveCaps &c);
+
+// Launch accounting and optional per-kernel CUDA-event timing.
+struct KernelProf {
+    uint32_t mask = 0;
+    unsigned long long launches = 0;          // every launch, timed or not
+    struct Rec { uint32_t kind; cudaEvent_t e0, e1; double bytes; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    unsigned long long n[STAB_N_KERNEL_KINDS] = {};
+    double ms[STAB_N_KERNEL_KINDS] = {};
+    double bytes[STAB_N_KERNEL_KINDS] = {};
+    std::mutex mu;
+    cudaEvent_t take();
+    void begin(uint32_t kind, cudaStream_t s, Rec &r);
+    void end(Rec &r, cudaStream_t s, double bytes);
+    int collect();                            // synchronizes pending events
+};
+
 size_t batch_bytes(uint32_t n, uint32_t count);
 int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err);
 void batch_free(Batch &b);
 
 // Layered engine (layered.cu)
-cudaError_t layered_init(Batch &b, cudaStream_t s);
+cudaError_t layered_init(Batch &b, cudaStream_t s, KernelProf *kp);
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
-                        const LaunchCfg &lc, cudaStream_t s);
+                        const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
+                        unsigned long long *d_stats);
 cudaError_t layered_sync_qm(Batch &b, cudaStream_t s);
 size_t layered_gate_smem(uint32_t n);
 int layered_supported(uint32_t n, const LaunchCfg &lc);
@@ -164,9 +220,14 @@ struct ResJob {               // one shot
 };
 size_t resident_smem_per_tableau(uint32_t n);
 int resident_supported(uint32_t n, const LaunchCfg &lc);
+int resident_shape_ok(uint32_t max_n, const stab_tune &tune, const LaunchCfg &lc);
 cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
                          const stab_tune &tune, unsigned int *d_counter, int *d_err,
-                         const LaunchCfg &lc, cudaStream_t s);
+                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp);
+
+// device counters (unsigned long long) kept next to the error flag
+enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
+             DC_PIV_RECOMP = 6, DC_N = 8 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

@@ -18,10 +18,21 @@
 //    a scratch row) is computed in one pass with the ordered-product closed
 //    form instead of Alg. 2's per-row grid synchronisation.  Deterministic
 //    outcomes do not depend on the other Z measurements of the layer.
-//  * k_meas_rand: one CTA per tableau runs the layer's random measurements in
-//    circuit order (pivot, rowsum of the pivot into every anticommuting row
-//    with the mod-4 phase, destabilizer copy, +-Z_a install; Sec. 2.4), keeping
-//    the measured columns of later ops of the layer up to date.
+//  * k_meas_rand: one CTA per tableau runs the layer's random measurements
+//    (pivot, rowsum of the pivot into every anticommuting row with the mod-4
+//    phase, destabilizer copy, +-Z_a install; Sec. 2.4) in waves.  Two random
+//    measurements s, t commute as tableau operations when neither pivot row
+//    has an X or Y on the other's qubit: each leaves the other's pivot and
+//    measured column unchanged (up to the overwritten destabilizer partner),
+//    and a row both multiply receives the product of two commuting pivots,
+//    whose sign does not depend on the order.  A pending measurement joins the
+//    current wave when it commutes in this sense with every earlier pending
+//    one, so applying the wave at once gives the tableau circuit order gives,
+//    bit for bit.  The measured columns of the remaining ops are kept current
+//    from the pivot rows.
+//  * k_noise_events: noise draws are evaluated once per shot before the gate
+//    runs; the few Pauli errors that fire are listed per layer and applied by
+//    the slice kernels after the layer's gates.
 //  * k_cond: the X of resets whose outcome was 1 (and the Z of RESET_ERROR)
 //    as sign flips r ^= z_a (x_a); these Paulis commute with the layer's other
 //    measurements, so they are applied after it.
@@ -31,7 +42,7 @@
 
 namespace stab {
 
-enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2 };
+enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2, MS_WAVE = 3 };
 
 struct LArgs {
     DevProg P;
@@ -46,6 +57,14 @@ struct LArgs {
     unsigned long long cols_stride;  // words per tableau
     uint8_t *mstat, *mout;
     unsigned long long m_stride;     // items per tableau
+    int *first, *qmap;               // [B][64H], [B][n]
+    uint32_t *detz;                  // [B][32][2H]
+    uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
+    uint32_t *mpiv, *mbsz;           // [B][max_meas] cached pivot / column size
+    uint8_t *mstale;                 // [B][max_meas]
+    uint16_t *msup;                  // [B][max_meas][SUPCAP]
+    unsigned long long *stats;       // DC_* counters (may be null)
+    WaveCaps caps;                   // k_meas_rand list capacities (<= compile-time maxima)
     DevStreams st;
     unsigned long long *record;
     unsigned long long rec_stride;
@@ -54,6 +73,7 @@ struct LArgs {
 };
 
 static inline uint32_t round4(uint32_t v) { return (v + 3u) & ~3u; }
+extern WaveCaps g_caps;
 
 __device__ __forceinline__ uint32_t rbit(const uint32_t *r, uint32_t s) {
     return (r[s >> 5] >> (s & 31)) & 1u;
@@ -154,7 +174,61 @@ struct GRun {
     int32_t cols_layer;
 };
 
-__global__ void k_gate_run(LArgs a, GRun g) {
+// Combined Pauli (2-bit x|z<<1 form) of an item's noise ops on its two qubits.
+__device__ __forceinline__ void item_noise(const GItem &g, const DevStreams &st, uint32_t shot,
+                                           const Thr *thr, uint32_t &Pa, uint32_t &Pb) {
+    // Pauli code (1 X, 2 Y, 3 Z) -> x | z << 1 is code ^ (code >> 1)
+    Pa = 0; Pb = 0;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if (k >= g.nn) break;
+        const uint32_t u = noise_word(st, shot, k ? g.nl[1] : g.nl[0]);
+        int pa, pb;
+        noise_paulis(k ? g.nk[1] : g.nk[0], u, thr[k ? g.np[1] : g.np[0]], pa, pb);
+        if (!(pa | pb)) continue;
+        const uint32_t xa = (uint32_t)(pa ^ (pa >> 1)), xb = (uint32_t)(pb ^ (pb >> 1));
+        switch (k ? g.nt[1] : g.nt[0]) {
+        case NT_A: Pa ^= xa; break;
+        case NT_B: Pb ^= xa; break;
+        case NT_AB: Pa ^= xa; Pb ^= xb; break;
+        default: Pb ^= xa; Pa ^= xb; break;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t xz_flip(uint32_t P, uint32_t x, uint32_t z) {
+    return ((P & 1u) ? z : 0u) ^ ((P & 2u) ? x : 0u);
+}
+
+// One thread per gate item (x all tableaux): evaluate its noise draws and list
+// the Pauli errors that fire under the item's layer.  A layer whose events
+// overflow its slots keeps counting; the slice kernel then re-evaluates it.
+__global__ void k_noise_events(LArgs a) {
+    const unsigned long long total = (unsigned long long)a.P.n_gitems * a.B;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(e / a.P.n_gitems), i = (uint32_t)(e % a.P.n_gitems);
+        const GItem g = a.P.gitems[i];
+        if (!g.nn) continue;
+        uint32_t Pa, Pb;
+        item_noise(g, a.st, t, a.P.thr, Pa, Pb);
+        if (!(Pa | Pb)) continue;
+        const uint32_t l = a.P.item_layer[i];
+        const Layer L = a.P.layers[l];
+        uint32_t *cnt = a.ev_cnt + (size_t)t * a.P.n_layers + l;
+        uint32_t *ev = a.ev + (size_t)t * a.P.ev_total + L.ev_off;
+        if (Pa) {
+            const uint32_t k = atomicAdd(cnt, 1u);
+            if (k < L.ev_cap) ev[k] = g.a | (Pa << 30);
+        }
+        if (Pb) {
+            const uint32_t k = atomicAdd(cnt, 1u);
+            if (k < L.ev_cap) ev[k] = g.b | (Pb << 30);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(512) k_gate_run(LArgs a, GRun g) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t sred[32];
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
@@ -179,16 +253,44 @@ __global__ void k_gate_run(LArgs a, GRun g) {
     uint32_t racc = 0;
     for (uint32_t l = g.l0; l < g.l1; l++) {
         const Layer L = a.P.layers[l];
-        for (uint32_t i = threadIdx.x; i < L.count; i += blockDim.x) {
-            const GItem it = a.P.gitems[L.first + i];
-            uint32_t xa = sx[it.a], za = sz[it.a], xb = 0, zb = 0;
-            const bool two = it.b != it.a;
-            if (two) { xb = sx[it.b]; zb = sz[it.b]; }
-            racc ^= apply_item(it, xa, za, xb, zb, a.st, t, a.P.thr);
-            sx[it.a] = xa; sz[it.a] = za;
-            if (two) { sx[it.b] = xb; sz[it.b] = zb; }
+        // gates: packed items through the read-only path, next item prefetched
+        const uint2 *__restrict__ it = reinterpret_cast<const uint2 *>(a.P.sitems + L.first);
+        uint32_t i = threadIdx.x;
+        uint2 cur = i < L.count ? __ldg(it + i) : make_uint2(0u, 0u);
+        for (; i < L.count; i += blockDim.x) {
+            const uint2 nxt = (i + blockDim.x < L.count) ? __ldg(it + i + blockDim.x) : make_uint2(0u, 0u);
+            const uint32_t ga = cur.x & 0xffffu, gb = cur.x >> 16, gk = cur.y;
+            if (gk) {
+                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                const bool two = gb != ga;
+                if (two) { xb = sx[gb]; zb = sz[gb]; }
+                racc ^= apply_gate(gk, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za;
+                if (two) { sx[gb] = xb; sz[gb] = zb; }
+            }
+            cur = nxt;
         }
         __syncthreads();
+        if (L.n_noisy) {
+            // the layer's Pauli errors act after its gates
+            const uint32_t cnt = a.ev_cnt[(size_t)t * a.P.n_layers + l];
+            if (cnt <= L.ev_cap) {
+                const uint32_t *ev = a.ev + (size_t)t * a.P.ev_total + L.ev_off;
+                for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+                    const uint32_t v = ev[e], q = v & 0x3fffffffu;
+                    racc ^= xz_flip(v >> 30, sx[q], sz[q]);
+                }
+            } else {
+                for (uint32_t k = threadIdx.x; k < L.count; k += blockDim.x) {
+                    const GItem gi = a.P.gitems[L.first + k];
+                    if (!gi.nn) continue;
+                    uint32_t Pa, Pb;
+                    item_noise(gi, a.st, t, a.P.thr, Pa, Pb);
+                    racc ^= xz_flip(Pa, sx[gi.a], sz[gi.a]) ^ xz_flip(Pb, sx[gi.b], sz[gi.b]);
+                }
+            }
+            __syncthreads();
+        }
     }
     // sign flips: XOR-reduce over the CTA, one plain update per slice
     for (int o = 16; o; o >>= 1) racc ^= __shfl_xor_sync(FULL_MASK, racc, o);
@@ -201,8 +303,8 @@ __global__ void k_gate_run(LArgs a, GRun g) {
     if (g.cols_layer >= 0) {
         const Layer M = a.P.layers[g.cols_layer];
         uint32_t *cols = a.cols + t * a.cols_stride;
-        for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
-            cols[(size_t)i * CW + w] = sx[a.P.mitems[M.first + i].q];
+        for (uint32_t k = threadIdx.x; k < M.count; k += blockDim.x)
+            cols[(size_t)k * CW + w] = sx[a.P.mitems[M.first + k].q];
     }
     __syncthreads();
     if (warp == 0) {
@@ -269,9 +371,9 @@ __global__ void k_gather_cols(LArgs a, uint32_t layer) {
 //   2 sum r_b + sum_b popc(x_b & z_b) + 2 sum_{b<b'} popc(z_b & x_b') - popc(X & Z)
 // with X = xor of x_b, Z = xor of z_b; the product must be +-Z_q, so X = 0.
 // Zp/Xp: per-warp scratch of H words each.
-__device__ int det_outcome_warp(const uint32_t *rm, uint32_t RS, uint32_t Hr, uint32_t H,
-                                const uint32_t *r, const uint32_t *colK, uint32_t q,
-                                uint32_t *Zp, uint32_t *Xp, int *err) {
+__device__ int det_outcome_warp(const uint32_t *__restrict__ rm, uint32_t RS, uint32_t Hr, uint32_t H,
+                                const uint32_t *__restrict__ r, const uint32_t *__restrict__ colK,
+                                uint32_t q, uint32_t *__restrict__ Zp, uint32_t *__restrict__ Xp, int *err) {
     const int lane = threadIdx.x & 31;
     for (uint32_t c = lane; c < H; c += 32) { Zp[c] = 0; Xp[c] = 0; }
     __syncwarp();
@@ -288,9 +390,10 @@ __device__ int det_outcome_warp(const uint32_t *rm, uint32_t RS, uint32_t Hr, ui
                 const int b = __ffs(word) - 1;
                 word &= word - 1;
                 const uint32_t s = 32 * H + 32 * u + b;       // stabilizer partner row
-                const uint32_t *row = rm + (size_t)s * RS;
+                const uint32_t *__restrict__ row = rm + (size_t)s * RS;
+#pragma unroll 4
                 for (uint32_t c = lane; c < H; c += 32) {
-                    uint32_t x = row[c], z = row[Hr + c];
+                    const uint32_t x = row[c], z = row[Hr + c];
                     acc += __popc(x & z) + 2 * __popc(x & Zp[c]);
                     Zp[c] ^= z;
                     Xp[c] ^= x;
@@ -312,9 +415,53 @@ __device__ int det_outcome_warp(const uint32_t *rm, uint32_t RS, uint32_t Hr, ui
     return (e >> 1) & 1;
 }
 
+__device__ __forceinline__ void count(const LArgs &a, int k, unsigned long long v) {
+    if (a.stats && v) atomicAdd(&a.stats[k], v);
+}
+
 __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_t rec, uint32_t out) {
     if (rec != 0xffffffffu && out)
         atomicOr(&a.record[(unsigned long long)t * a.rec_stride + (rec >> 6)], 1ull << (rec & 63));
+}
+
+// One warp scans a measured column (CW words): pivot = first set row of the
+// stabilizer half (as slot - 32H, ~0 if none), size = number of set rows, and
+// when size <= SUPCAP the set rows in ascending order into sup[].
+__device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ col, uint32_t H, uint32_t CW,
+                                                 uint32_t &piv, uint32_t &size, uint16_t *__restrict__ sup) {
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0, pv = 0xffffffffu;
+    uint32_t v = lane < CW ? col[lane] : 0u;
+    for (uint32_t w0 = 0; w0 < CW; w0 += 32) {
+        const uint32_t vn = (w0 + 32 + lane < CW) ? col[w0 + 32 + lane] : 0u;   // prefetch
+        const uint32_t w = w0 + lane;
+        if (pv == 0xffffffffu) {
+            const uint32_t m = __ballot_sync(FULL_MASK, w >= H && v != 0);
+            if (m) {
+                const int L = __ffs(m) - 1;
+                const uint32_t vw = __shfl_sync(FULL_MASK, v, L);
+                pv = 32 * (w0 + L - H) + __ffs(vw) - 1;
+            }
+        }
+        const uint32_t c = __popc(v);
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t tot = __shfl_sync(FULL_MASK, x, 31);
+        uint32_t pos = base + x - c;
+        uint32_t m = v;
+        while (m && pos < SUPCAP) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            sup[pos++] = (uint16_t)(32 * w + b);
+        }
+        base += tot;
+        v = vn;
+    }
+    piv = pv;
+    size = base;
 }
 
 constexpr int DET_WARPS = 8;
@@ -337,11 +484,28 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
         }
     }
     const uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
-    uint32_t nz = 0;
-    for (uint32_t c = lane; c < H; c += 32) nz |= col[H + c];
-    if (__any_sync(FULL_MASK, nz != 0)) {
-        if (lane == 0) stat[i] = MS_RANDOM;
+    // pivot (first stabilizer row of the column), column size and support,
+    // cached for the random-measurement kernel
+    uint32_t pv, csize;
+    const size_t ci = t * a.m_stride + i;
+    warp_column_scan(col, H, CW, pv, csize, a.msup + ci * SUPCAP);
+    if (pv != 0xffffffffu) {
+        if (lane == 0) {
+            stat[i] = MS_RANDOM;
+            a.mpiv[ci] = pv;
+            a.mbsz[ci] = csize;
+            a.mstale[ci] = 0;
+        }
         return;
+    }
+    if (a.stats) {
+        uint32_t k = 0;
+        for (uint32_t w = lane; w < H; w += 32) k += __popc(col[w]);
+        for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL_MASK, k, o);
+        if (lane == 0) {
+            count(a, DC_DET, 1);
+            count(a, DC_SUM_K, k);
+        }
     }
     uint32_t *Zp = smem + (size_t)warp * 2 * H, *Xp = Zp + H;
     const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
@@ -358,9 +522,10 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
 __device__ __forceinline__ void rowsum_warp(uint32_t *rm, uint32_t RS, uint32_t Hr, uint32_t H,
                                             uint32_t *r, uint32_t s, uint32_t p, int *err) {
     const int lane = threadIdx.x & 31;
-    const uint32_t *rp = rm + (size_t)p * RS;
-    uint32_t *rs = rm + (size_t)s * RS;
+    const uint32_t *__restrict__ rp = rm + (size_t)p * RS;
+    uint32_t *__restrict__ rs = rm + (size_t)s * RS;
     int acc = 0;
+#pragma unroll 4
     for (uint32_t c = lane; c < H; c += 32) {
         const uint32_t xp = rp[c], zp = rp[Hr + c], xs = rs[c], zs = rs[Hr + c];
         acc += phase_word(xp, zp, xs, zs);
@@ -378,101 +543,443 @@ __device__ __forceinline__ void rowsum_warp(uint32_t *rm, uint32_t RS, uint32_t 
 }
 
 constexpr int RAND_THREADS = 1024;
+constexpr uint32_t PCAP = WaveCaps::PCAP_MAX;
+constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;
+constexpr uint32_t PAIRCAP = WaveCaps::PAIRCAP_MAX;
+constexpr uint32_t JCAP = WaveCaps::JCAP_MAX;
+constexpr uint16_t NOPIV = 0xffffu;
+
+size_t rand_smem(uint32_t n, uint32_t H) {
+    (void)n;
+    return (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H + 64;
+}
+
+// Block-wide exclusive scan of one value per thread (1024 threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;          // inclusive totals per warp
+        if (lane == nw - 1) *total = w;
+    }
+    __syncthreads();
+    const uint32_t off = warp ? warp_tot[warp - 1] : 0u;
+    const uint32_t res = off + x - v;
+    __syncthreads();
+    return res;
+}
 
 __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t layer) {
-    extern __shared__ uint32_t smem[];      // 2H words for the det fallback
-    __shared__ int s_pw;
-    const uint32_t H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t s_wt[32];
+    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any;
+    const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const Layer M = a.P.layers[layer];
+    const uint32_t pcap = a.caps.pcap, wcap = a.caps.wcap, paircap = a.caps.paircap, jcap = a.caps.jcap;
+    const uint32_t budget = a.caps.mark_budget, wmax = max(1u, a.caps.window);
     uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     uint32_t *cols = a.cols + t * a.cols_stride;
     uint32_t *rm = a.rm + t * a.rm_stride;
     uint32_t *r = a.r + (size_t)t * CW;
     uint8_t *dirty = a.dirty + (size_t)t * CW;
-    for (uint32_t i = 0; i < M.count; i++) {
-        if (stat[i] != MS_RANDOM) continue;          // block-uniform (written by earlier kernels / step)
-        const MItem m = a.P.mitems[M.first + i];
-        const uint32_t *col = cols + (size_t)i * CW;
-        if (threadIdx.x == 0) s_pw = 0x7fffffff;
-        __syncthreads();
-        for (uint32_t c = threadIdx.x; c < H; c += blockDim.x)
-            if (col[H + c]) atomicMin(&s_pw, (int)c);
-        __syncthreads();
-        const int pw = s_pw;
-        if (pw == 0x7fffffff) {
-            // became deterministic after an earlier random measurement of this layer
-            if (warp == 0) {
-                const int o = det_outcome_warp(rm, RS, Hr, H, r, col, m.q, smem, smem + H, a.err);
+    uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
+    uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
+    uint32_t *claim = firstp + 64 * H;                                // rowsum claims
+    int *qmap = a.qmap + (size_t)t * n;
+    uint32_t *detz = a.detz + (size_t)t * 32 * 2 * H + (size_t)warp * 2 * H;
+    uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
+    uint8_t *mstale = a.mstale + t * a.m_stride;
+    uint16_t *msup = a.msup + t * a.m_stride * SUPCAP;
+    uint16_t *pend = (uint16_t *)smem;             // pending item indices, circuit order
+    uint16_t *piv = pend + PCAP;                   // their pivot (slot - 32H), NOPIV
+    uint16_t *bsz = piv + PCAP;                    // |x-column support| (saturated)
+    uint16_t *sel = bsz + PCAP;                    // selected pending positions
+    uint32_t *pairs = (uint32_t *)(sel + WCAP);    // row | sel index << 16
+    uint32_t *ents = pairs + PAIRCAP;              // item | sel index << 16 | bp << 31
+    uint32_t *qmask = ents + JCAP;                 // destabilizer partners of the wave [CW]
+
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
+        if (stat[i] == MS_RANDOM) s_any = 1;
+    __syncthreads();
+    if (!s_any) return;
+    for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = -1;
+    for (uint32_t s = threadIdx.x; s < 3 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (int)i;
+    __syncthreads();
+
+    // first[row] holds stamp(wave) | k for the earliest op k of the wave's window
+    // whose column holds row; stamps decrease, so stale entries never win atomicMin.
+    // Stamps only decrease (marks per wave, claims per claim round), so entries
+    // left from earlier waves never win an atomicMin; when a counter runs out
+    // its arrays are cleared and it restarts.
+    uint32_t wave = 0, cround = 0;
+    // every wave resolves at least one op (the first pending random op always
+    // qualifies), so 2*count+2 waves bound the loop; exceeding it is a bug
+    for (uint32_t guard = 0;; guard++) {
+        if (guard > 2 * M.count + 2) {
+            if (threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+            break;
+        }
+        if (wave >= 0xfff0u) {
+            for (uint32_t s = threadIdx.x; s < 2 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
+            wave = 0;
+            __syncthreads();
+        }
+        const uint32_t stamp = (0xfffeu - wave) << 16;
+        wave++;
+        // ---- (1) ordered list of pending random measurements (first pcap)
+        {
+            uint32_t cnt = 0;
+            const uint32_t per = (M.count + blockDim.x - 1) / blockDim.x;
+            const uint32_t i0 = threadIdx.x * per, i1 = min(M.count, i0 + per);
+            for (uint32_t i = i0; i < i1; i++) cnt += stat[i] == MS_RANDOM;
+            uint32_t off = block_excl_scan(cnt, s_wt, &s_tot);
+            for (uint32_t i = i0; i < i1; i++)
+                if (stat[i] == MS_RANDOM) {
+                    if (off < pcap) pend[off] = (uint16_t)i;
+                    off++;
+                }
+            if (threadIdx.x == 0) {
+                s_np = min(s_tot, pcap);
+                s_nsel = 0; s_npair = 0; s_nent = 0;
+                s_firstrand = 0xffffffffu; s_nrand = 0;
+            }
+            for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
+            __syncthreads();
+        }
+        const uint32_t np = s_np;
+        if (np == 0) break;
+        const uint32_t nlook = min(np, wmax);
+        // ---- (2) pivots and supports of the examined ops (cached; recomputed
+        // for ops whose column an earlier wave changed)
+        for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
+            const uint32_t i = pend[k];
+            uint32_t pv, bs;
+            if (!mstale[i]) {
+                pv = mpiv[i];
+                bs = mbsz[i];
+            } else {
+                warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
                 if (lane == 0) {
-                    out[i] = (uint8_t)o;
-                    stat[i] = MS_DONE;
-                    write_record(a, t, m.rec, (uint32_t)o);
+                    mpiv[i] = pv;
+                    mbsz[i] = bs;
+                    mstale[i] = 0;
+                    count(a, DC_PIV_RECOMP, 1);
                 }
             }
+            if (lane == 0) {
+                piv[k] = pv == 0xffffffffu ? NOPIV : (uint16_t)pv;
+                bsz[k] = (uint16_t)min(bs, 65535u);
+                if (pv != 0xffffffffu) { atomicMin(&s_firstrand, k); atomicAdd(&s_nrand, 1u); }
+            }
+        }
+        __syncthreads();
+        // ---- (3) ops that became deterministic: outcome from the current tableau
+        for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
+            if (piv[k] != NOPIV) continue;
+            const uint32_t i = pend[k];
+            const MItem m = a.P.mitems[M.first + i];
+            const int o = det_outcome_warp(rm, RS, Hr, H, r, cols + (size_t)i * CW, m.q, detz, detz + H, a.err);
+            if (lane == 0) {
+                out[i] = (uint8_t)o;
+                stat[i] = MS_DONE;
+                write_record(a, t, m.rec, (uint32_t)o);
+                count(a, DC_DET_NOW, 1);
+            }
+        }
+        if (s_nrand == 0) {          // block-uniform
             __syncthreads();
             continue;
         }
-        const uint32_t pword = col[H + pw];
-        const uint32_t q = 32u * (uint32_t)pw + (uint32_t)(__ffs(pword) - 1);  // destabilizer slot
-        const uint32_t p = 32u * H + q;                                          // pivot (stabilizer) slot
-        const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.st, t, m.nl + 1) & 1u)
-                                                       : coin_bit(a.st, t, m.coin);
-        // rowsum(s, p) for every row s != p with x_{s,a} = 1.  Row q (= p - n)
-        // is skipped: it is overwritten by row p below, and its product with p
-        // has an odd power of i, which Appendix B leaves the sign bit unchanged for.
-        for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
-            uint32_t mask = col[w];
-            if (lane == 0 && mask) dirty[w] = 1;
-            if (w == (p >> 5)) mask &= ~(1u << (p & 31));
-            if (w == (q >> 5)) mask &= ~(1u << (q & 31));
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1;
-                rowsum_warp(rm, RS, Hr, H, r, 32 * w + b, p, a.err);
+        // ---- (4) window: leading examined ops whose columns total <= budget rows
+        if (warp == 0) {
+            uint32_t base = 0, kend = 0;
+            for (uint32_t k0 = 0; k0 < nlook; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                const uint32_t v = (k < nlook && piv[k] != NOPIV) ? bsz[k] : 0u;
+                uint32_t x = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+                    if (lane >= o) x += y;
+                }
+                const uint32_t ok = __ballot_sync(FULL_MASK, k < nlook && base + x <= budget);
+                kend = ok ? k0 + 32 - __clz(ok) : kend;        // highest lane within budget
+                base += __shfl_sync(FULL_MASK, x, 31);
+                if (base > budget) break;
+            }
+            if (lane == 0) s_kend = max(kend, s_firstrand + 1);
+        }
+        __syncthreads();
+        const uint32_t kend = s_kend;
+        // ---- (5) mark rows with the earliest window op holding them in its
+        // column, and pivot rows with the earliest window op pivoting on them
+        for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
+            if (piv[k] == NOPIV) continue;
+            const uint32_t i = pend[k];
+            if (lane == 0) atomicMin(&firstp[32 * H + piv[k]], stamp | k);
+            if (bsz[k] <= SUPCAP) {
+                const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                for (uint32_t e = lane; e < bsz[k]; e += 32) atomicMin(&first[sp[e]], stamp | k);
+            } else {
+                const uint32_t *col = cols + (size_t)i * CW;
+                for (uint32_t w = lane; w < CW; w += 32) {
+                    uint32_t m = col[w];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        atomicMin(&first[32 * w + b], stamp | k);
+                    }
+                }
             }
         }
         __syncthreads();
-        // row q <- row p; row p <- +-Z_a with sign = coin
-        for (uint32_t c = threadIdx.x; c < H; c += blockDim.x) {
-            const uint32_t xv = rm[(size_t)p * RS + c], zv = rm[(size_t)p * RS + Hr + c];
-            rm[(size_t)q * RS + c] = xv;
-            rm[(size_t)q * RS + Hr + c] = zv;
-            rm[(size_t)p * RS + c] = 0u;
-            rm[(size_t)p * RS + Hr + c] = (c == (m.q >> 5)) ? (1u << (m.q & 31)) : 0u;
-        }
-        if (threadIdx.x == 0) {
-            const uint32_t rp = rbit(r, p);
-            r[q >> 5] = (r[q >> 5] & ~(1u << (q & 31))) | (rp << (q & 31));
-            r[p >> 5] = (r[p >> 5] & ~(1u << (p & 31))) | (coin << (p & 31));
-            dirty[p >> 5] = 1;
-            dirty[q >> 5] = 1;
-        }
-        // keep the measured columns of later random ops current:
-        // rows in A get x ^= x_{p,b}; row q gets x_{p,b}; row p gets 0.
-        for (uint32_t j = i + 1 + (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
-            if (stat[j] != MS_RANDOM) continue;
-            uint32_t *cj = cols + (size_t)j * CW;
-            const uint32_t bp = (cj[p >> 5] >> (p & 31)) & 1u;
-            if (bp) {
-                for (uint32_t c = lane; c < CW; c += 32) {
-                    uint32_t v = col[c];
-                    if (c == (p >> 5)) v &= ~(1u << (p & 31));
-                    cj[c] ^= v;
+        // ---- (6) select op k when no earlier window op pivots on a row of its
+        // column and no earlier window op's column holds its pivot row
+        for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
+            if (piv[k] == NOPIV) continue;
+            const uint32_t i = pend[k], me = stamp | k;
+            bool ok = true;
+            if (bsz[k] <= SUPCAP) {
+                const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                for (uint32_t e = lane; e < bsz[k]; e += 32) ok &= firstp[sp[e]] >= me;
+            } else {
+                const uint32_t *col = cols + (size_t)i * CW;
+                for (uint32_t w = lane; w < CW; w += 32) {
+                    uint32_t m = col[w];
+                    while (m && ok) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        ok = firstp[32 * w + b] >= me;
+                    }
                 }
             }
-            __syncwarp();
-            if (lane == 0) {
-                cj[q >> 5] = (cj[q >> 5] & ~(1u << (q & 31))) | (bp << (q & 31));
-                cj[p >> 5] &= ~(1u << (p & 31));
+            if (lane == 0) ok &= first[32 * H + piv[k]] == me;
+            if (__all_sync(FULL_MASK, ok) && lane == 0) {
+                const uint32_t idx = atomicAdd(&s_nsel, 1u);
+                if (idx < wcap) {
+                    sel[idx] = (uint16_t)k;
+                    stat[i] = MS_WAVE;
+                }
             }
-            __syncwarp();
         }
+        __syncthreads();
+        // ---- (7) list rowsum pairs and measured-column updates
+        const uint32_t nsel = min(s_nsel, wcap);
+        for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+            const uint32_t k = sel[x], i = pend[k];
+            const uint32_t q = piv[k], p = 32 * H + q;
+            if (bsz[k] <= SUPCAP) {
+                const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                for (uint32_t e = lane; e < bsz[k]; e += 32) {
+                    const uint32_t row = sp[e];
+                    dirty[row >> 5] = 1;
+                    if (row == p || row == q) continue;
+                    const uint32_t f = atomicAdd(&s_npair, 1u);
+                    if (f < paircap) pairs[f] = row | (x << 16);
+                }
+            } else {
+                const uint32_t *col = cols + (size_t)i * CW;
+                for (uint32_t w = lane; w < CW; w += 32) {
+                    uint32_t m = col[w];
+                    if (m) dirty[w] = 1;
+                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
+                    if (w == (q >> 5)) m &= ~(1u << (q & 31));
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const uint32_t f = atomicAdd(&s_npair, 1u);
+                        if (f < paircap) pairs[f] = (32 * w + b) | (x << 16);
+                    }
+                }
+            }
+            // remaining pending ops whose qubit has X or Y in row p or row q
+            const uint32_t *rp_ = rm + (size_t)p * RS, *rq_ = rm + (size_t)q * RS;
+            for (uint32_t c = lane; c < H; c += 32) {
+                const uint32_t xp = rp_[c];
+                uint32_t mm = xp | rq_[c];
+                while (mm) {
+                    const int b = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int j = qmap[32 * c + b];
+                    if (j >= 0 && stat[j] == MS_RANDOM) {
+                        const uint32_t f = atomicAdd(&s_nent, 1u);
+                        if (f < jcap) ents[f] = (uint32_t)j | (x << 16) | (((xp >> b) & 1u) << 31);
+                    }
+                }
+            }
+            if (lane == 0) {
+                dirty[p >> 5] = 1;
+                dirty[q >> 5] = 1;
+                atomicOr(&qmask[q >> 5], 1u << (q & 31));
+            }
+        }
+        __syncthreads();
+        const uint32_t npair = s_npair, nent = s_nent;
         if (threadIdx.x == 0) {
-            out[i] = (uint8_t)coin;
-            stat[i] = MS_DONE;
-            write_record(a, t, m.rec, coin);
+            count(a, DC_WAVES, 1);
+            count(a, DC_WAVE_OPS, nsel);
+            count(a, DC_SUM_A, npair);
+        }
+        // ---- (8) rowsums of the wave.  A row in the columns of several wave
+        // ops is multiplied by their (commuting) pivots one at a time: each
+        // round every pending pair claims its row and the winners go.
+        if (npair <= paircap) {
+            // a row is held by at most nsel wave ops, so nsel rounds suffice
+            bool done = false;
+            for (uint32_t round = 0; round <= nsel; round++) {
+                if (cround >= 0xfff0u) {
+                    for (uint32_t s = threadIdx.x; s < 64 * H; s += blockDim.x) claim[s] = 0xffffffffu;
+                    cround = 0;
+                    __syncthreads();
+                }
+                const uint32_t cst = (0xfffeu - cround) << 16;
+                cround++;
+                if (threadIdx.x == 0) s_tot = 0;
+                __syncthreads();
+                for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x)
+                    if (!(pairs[e] >> 31)) atomicMin(&claim[pairs[e] & 0xffffu], cst | e);
+                __syncthreads();
+                for (uint32_t e = (uint32_t)warp; e < npair; e += (uint32_t)nw) {
+                    const uint32_t pe = pairs[e];
+                    if (pe >> 31) continue;
+                    const uint32_t row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
+                    if (claim[row] != (cst | e)) {
+                        if (lane == 0) s_tot = 1;
+                        continue;
+                    }
+                    rowsum_warp(rm, RS, Hr, H, r, row, 32 * H + piv[sel[x]], a.err);
+                    if (lane == 0) pairs[e] = pe | 0x80000000u;
+                }
+                __syncthreads();
+                if (!s_tot) { done = true; break; }
+            }
+            if (!done && threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+        } else {
+            // list overflow: one warp applies the pivots row by row, in wave order
+            for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
+                for (uint32_t x = 0; x < nsel; x++) {
+                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                    uint32_t m = cols[(size_t)pend[k] * CW + w];
+                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
+                    if (w == (q >> 5)) m &= ~(1u << (q & 31));
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        rowsum_warp(rm, RS, Hr, H, r, 32 * w + b, p, a.err);
+                    }
+                }
+            }
+        }
+        // ---- (9) measured columns of remaining ops: x ^= x_{p,b} on A rows.
+        // Rows that are destabilizer partners of this wave's pivots are left
+        // out: each ends as a copy of its pivot row, so its bit is set in (10).
+        if (nent <= jcap) {
+            for (uint32_t e = (uint32_t)warp; e < nent; e += (uint32_t)nw) {
+                if (!(ents[e] >> 31)) continue;
+                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu;
+                const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                uint32_t *cj = cols + (size_t)j * CW;
+                if (bsz[k] <= SUPCAP) {
+                    const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
+                    for (uint32_t f = lane; f < bsz[k]; f += 32) {
+                        const uint32_t row = sp[f];
+                        if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
+                        atomicXor(&cj[row >> 5], 1u << (row & 31));
+                    }
+                } else {
+                    const uint32_t *col = cols + (size_t)pend[k] * CW;
+                    for (uint32_t w = lane; w < CW; w += 32) {
+                        uint32_t v = col[w] & ~qmask[w];
+                        if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                        if (v) atomicXor(&cj[w], v);
+                    }
+                }
+            }
+        } else {
+            for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
+                if (stat[j] != MS_RANDOM) continue;
+                uint32_t *cj = cols + (size_t)j * CW;
+                for (uint32_t x = 0; x < nsel; x++) {
+                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                    if (!((cj[p >> 5] >> (p & 31)) & 1u)) continue;
+                    const uint32_t *col = cols + (size_t)pend[k] * CW;
+                    for (uint32_t w = lane; w < CW; w += 32) {
+                        uint32_t v = col[w] & ~qmask[w];
+                        if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                        cj[w] ^= v;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+        // ---- (10) bit fixes (row q gets x_{p,b}, row p gets 0), row copies
+        if (nent <= jcap) {
+            for (uint32_t e = threadIdx.x; e < nent; e += blockDim.x) {
+                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
+                const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                uint32_t *cj = cols + (size_t)j * CW;
+                if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
+                else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                mstale[j] = 1;
+            }
+        } else {
+            // fallback: recompute bits from the untouched pivot rows
+            for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
+                if (stat[j] != MS_RANDOM) continue;
+                uint32_t *cj = cols + (size_t)j * CW;
+                const uint32_t qb = a.P.mitems[M.first + j].q;
+                if (lane == 0) mstale[j] = 1;
+                for (uint32_t x = lane; x < nsel; x += 32) {
+                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                    const uint32_t bp = (rm[(size_t)p * RS + (qb >> 5)] >> (qb & 31)) & 1u;
+                    if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
+                    else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                    atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                }
+            }
+            __syncthreads();          // the pivot rows read above are overwritten next
+        }
+        for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+            const uint32_t k = sel[x], i = pend[k], q = piv[k], p = 32 * H + q;
+            const MItem m = a.P.mitems[M.first + i];
+            const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.st, t, m.nl + 1) & 1u)
+                                                           : coin_bit(a.st, t, m.coin);
+            uint32_t *rowp = rm + (size_t)p * RS, *rowq = rm + (size_t)q * RS;
+            for (uint32_t c = lane; c < H; c += 32) {
+                const uint32_t xv = rowp[c], zv = rowp[Hr + c];
+                rowq[c] = xv;
+                rowq[Hr + c] = zv;
+                rowp[c] = 0u;
+                rowp[Hr + c] = (c == (m.q >> 5)) ? (1u << (m.q & 31)) : 0u;
+            }
+            if (lane == 0) {
+                const uint32_t rp = rbit(r, p);
+                if (rp) atomicOr(&r[q >> 5], 1u << (q & 31));
+                else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
+                if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
+                else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
+                out[i] = (uint8_t)coin;
+                stat[i] = MS_DONE;
+                write_record(a, t, m.rec, coin);
+            }
         }
         __syncthreads();
     }
@@ -516,8 +1023,11 @@ __global__ void k_cond(LArgs a, uint32_t layer) {
 // ---------------------------------------------------------------- host side
 size_t layered_gate_smem(uint32_t n) { return (size_t)8 * n; }
 
+size_t rand_smem(uint32_t n, uint32_t H);
+
 int layered_supported(uint32_t n, const LaunchCfg &lc) {
-    return layered_gate_smem(n) + 1024 <= lc.smem_optin;
+    const uint32_t H = (n + 31) / 32;
+    return layered_gate_smem(n) + 1024 <= lc.smem_optin && rand_smem(n, H) + 1024 <= lc.smem_optin;
 }
 
 size_t batch_bytes(uint32_t n, uint32_t count) {
@@ -562,6 +1072,7 @@ void batch_free(Batch &b) {
 static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevStreams *st,
                        unsigned long long *record, size_t rec_stride, int *d_err) {
     LArgs a{};
+    a.caps = g_caps;
     if (p) a.P = p->dev;
     a.P.n = b.n; a.P.H = b.H; a.P.CW = b.CW;
     a.qm = b.qm; a.qm_stride = b.qm_stride;
@@ -573,6 +1084,15 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
         a.cols_stride = (unsigned long long)std::max<uint32_t>(1, p->dev.max_meas) * b.CW;
         a.mstat = ms->stat; a.mout = ms->out;
         a.m_stride = std::max<uint32_t>(1, p->dev.max_meas);
+        a.first = ms->first;
+        a.qmap = ms->qmap;
+        a.detz = ms->detz;
+        a.ev = ms->ev;
+        a.ev_cnt = ms->ev_cnt;
+        a.mpiv = ms->mpiv;
+        a.mbsz = ms->mbsz;
+        a.mstale = ms->mstale;
+        a.msup = ms->msup;
     }
     if (st) a.st = *st;
     a.record = record;
@@ -582,9 +1102,25 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
     return a;
 }
 
-cudaError_t layered_init(Batch &b, cudaStream_t s) {
+// Launch wrapper: counts the launch and, when the kind is selected, brackets
+// it with CUDA events on its stream.
+template <typename F>
+static void launch(KernelProf *kp, uint32_t kind, cudaStream_t s, double bytes, F &&f) {
+    if (!kp) { f(); return; }
+    kp->launches++;
+    if (kp->mask & (1u << kind)) {
+        KernelProf::Rec r;
+        kp->begin(kind, s, r);
+        f();
+        kp->end(r, s, bytes);
+    } else {
+        f();
+    }
+}
+
+cudaError_t layered_init(Batch &b, cudaStream_t s, KernelProf *kp) {
     LArgs a = make_args(nullptr, b, nullptr, nullptr, nullptr, 0, nullptr);
-    k_init<<<1024, 256, 0, s>>>(a);
+    launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] { k_init<<<1024, 256, 0, s>>>(a); });
     b.rm_valid = true;
     return cudaGetLastError();
 }
@@ -596,10 +1132,21 @@ cudaError_t layered_sync_qm(Batch &b, cudaStream_t s) {
 }
 
 static bool g_attr_set = false;
+WaveCaps g_caps;
+
+void set_wave_caps(const WaveCaps &c) {
+    g_caps.pcap = std::max(1u, std::min(c.pcap, WaveCaps::PCAP_MAX));
+    g_caps.wcap = std::max(1u, std::min(c.wcap, WaveCaps::WCAP_MAX));
+    g_caps.paircap = std::min(c.paircap, WaveCaps::PAIRCAP_MAX);
+    g_caps.jcap = std::min(c.jcap, WaveCaps::JCAP_MAX);
+    g_caps.mark_budget = c.mark_budget;
+    g_caps.window = std::max(1u, c.window);
+}
 
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
-                        const LaunchCfg &lc, cudaStream_t s) {
+                        const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
+                        unsigned long long *d_stats) {
     if (!g_attr_set) {
         cudaFuncSetAttribute(k_gate_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(lc.smem_optin - 1024));
@@ -610,6 +1157,13 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
         g_attr_set = true;
     }
     LArgs a = make_args(&p, b, &ms, &st, record, rec_stride, d_err);
+    a.stats = d_stats;
+    if (p.dev.ev_total) {
+        cudaMemsetAsync(ms.ev_cnt, 0, sizeof(uint32_t) * p.layers.size() * b.count, s);
+        const unsigned long long work = (unsigned long long)p.dev.n_gitems * b.count;
+        const uint32_t blocks = (uint32_t)std::min<unsigned long long>((work + 255) / 256, 8ull * lc.sm_count * 8);
+        launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] { k_noise_events<<<blocks, 256, 0, s>>>(a); });
+    }
     const uint32_t gthreads = std::min<uint32_t>(512, std::max<uint32_t>(64, (p.dev.max_gitems + 31) / 32 * 32));
     const size_t gsm = layered_gate_smem(b.n);
     bool cols_ready = false;
@@ -621,23 +1175,30 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
             const bool next_meas = k + 1 < p.runs.size() && p.runs[k + 1].type == LT_MEAS;
             g.want_rm = next_meas ? 1u : 0u;
             g.cols_layer = next_meas ? (int32_t)p.runs[k + 1].l0 : -1;
-            k_gate_run<<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g);
+            launch(kp, STAB_KERNEL_GATE_RUN, s, R.alg_bytes * b.count,
+                   [&] { k_gate_run<<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g); });
             b.rm_valid = next_meas;
             cols_ready = next_meas;
         } else {
             const uint32_t l = R.l0;
             const Layer &L = p.layers[l];
             if (!b.rm_valid) {
-                k_qm_to_rm<<<dim3(b.CW, b.count), 256, 0, s>>>(a);
+                launch(kp, STAB_KERNEL_OTHER, s, 0.0,
+                       [&] { k_qm_to_rm<<<dim3(b.CW, b.count), 256, 0, s>>>(a); });
                 b.rm_valid = true;
             }
             if (!cols_ready)
-                k_gather_cols<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l);
+                launch(kp, STAB_KERNEL_OTHER, s, 0.0,
+                       [&] { k_gather_cols<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
             const uint32_t nb = (L.count + DET_WARPS - 1) / DET_WARPS;
-            k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
-            k_meas_rand<<<b.count, RAND_THREADS, (size_t)2 * b.H * 4, s>>>(a, l);
+            launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
+                k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
+            });
+            launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
+                   [&] { k_meas_rand<<<b.count, RAND_THREADS, rand_smem(b.n, b.H), s>>>(a, l); });
             if (L.has_cond)
-                k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l);
+                launch(kp, STAB_KERNEL_OTHER, s, 0.0,
+                       [&] { k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
             cols_ready = false;
         }
         cudaError_t e = cudaGetLastError();

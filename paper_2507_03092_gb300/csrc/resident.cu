@@ -253,12 +253,29 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
     }
 }
 
+// Can the shape be launched at all (shared memory and registers)?
+int resident_shape_ok(uint32_t max_n, const stab_tune &tune, const LaunchCfg &lc) {
+    const uint32_t G = tune.group_threads, tpc = tune.tableaux_per_cta;
+    if (!G || !tpc || G * tpc > 1024 || (G != 32 && tpc > 15)) return 0;
+    if (4 * res_words(max_n) * tpc > lc.smem_optin) return 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = tune.words_per_thread == 1 ? cudaFuncGetAttributes(&fa, k_resident<1>)
+                  : tune.words_per_thread == 2 ? cudaFuncGetAttributes(&fa, k_resident<2>)
+                                               : cudaFuncGetAttributes(&fa, k_resident<4>);
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    const uint32_t regs = (uint32_t)fa.numRegs, thr = G * tpc;
+    // registers are allocated per warp in units of 256
+    const uint32_t per_warp = ((regs * 32 + 255) / 256) * 256;
+    return per_warp * (thr / 32) <= 65536u && thr <= (uint32_t)fa.maxThreadsPerBlock;
+}
+
 cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, const stab_tune &tune,
-                         unsigned int *d_counter, int *d_err, const LaunchCfg &lc, cudaStream_t s) {
+                         unsigned int *d_counter, int *d_err, const LaunchCfg &lc, cudaStream_t s,
+                         KernelProf *kp) {
     const uint32_t G = tune.group_threads, tpc = tune.tableaux_per_cta;
     const size_t gw = res_words(max_n);
     const size_t smem = 4 * gw * tpc;
-    if (smem > lc.smem_optin || G * tpc > 1024 || (G != 32 && tpc > 15)) return cudaErrorInvalidConfiguration;
+    if (!resident_shape_ok(max_n, tune, lc)) return cudaErrorInvalidConfiguration;
     static bool attr[5] = {false, false, false, false, false};
     cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s);
     int occ = 0;
@@ -272,7 +289,12 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, 
         if (occ < 1) occ = 1;
         uint32_t groups_needed = (n_jobs + tpc - 1) / tpc;
         uint32_t grid = std::min<uint32_t>((uint32_t)(occ * lc.sm_count), std::max<uint32_t>(1, groups_needed));
+        KernelProf::Rec rec;
+        const bool timed = kp && (kp->mask & (1u << STAB_KERNEL_RESIDENT));
+        if (kp) kp->launches++;
+        if (timed) kp->begin(STAB_KERNEL_RESIDENT, s, rec);
         kern<<<grid, G * tpc, smem, s>>>(d_jobs, n_jobs, d_counter, d_err, G, (uint32_t)gw);
+        if (timed) kp->end(rec, s, 0.0);
         e = cudaGetLastError();
     };
     switch (tune.words_per_thread) {

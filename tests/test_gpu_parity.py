@@ -208,3 +208,54 @@ def test_host_validation_errors(sim):
     with pytest.raises(B.StabError) as e:
         B.stab_sample(sim.ctx, cid, 2, st, rec)
     assert e.value.code == B.ERR_STREAM_SHORT
+
+
+def _measure_all_after(n, layers, seed):
+    """Random Clifford layers without measurement, then one layer measuring
+    every qubit: a single measurement layer with many random outcomes."""
+    base = C.random_clifford_layers(n, layers, seed=seed, meas_frac=0.0)
+    b = C.Builder(n)
+    for q in range(n):
+        b.measure(q)
+    return C.concat([base, b.build()])
+
+
+def _wave_cases():
+    yield "independent", (lambda: (lambda b: ([b.gate1(C.H, q) for q in range(300)],
+                                              [b.measure(q) for q in range(300)], b.build())[-1])(C.Builder(300)))()
+    yield "shallow", _measure_all_after(300, 2, 1)
+    yield "deep", _measure_all_after(160, 12, 2)
+    yield "surface", C.surface_code_memory(9, p=5e-3)
+
+
+def _check_wave_cases(sim):
+    for name, circ in _wave_cases():
+        coins, noise = S.streams_for(circ, 3, [0])
+        rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+        orec, otab = _oracle(circ, coins[0], noise[0])
+        assert np.array_equal(rec[0], orec), name
+        _assert_tableau_equal(tabs[0], otab, name)
+
+
+def test_wave_measurement_layers_match_oracle(sim):
+    _check_wave_cases(sim)
+
+
+def test_wave_list_overflow_fallbacks_match_oracle():
+    """Shrunken wave-list capacities force every fallback path of the random
+    measurement kernel (pending window, wave size, rowsum-pair list, column
+    update list, marking budget)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import tests.test_gpu_parity as t\n"
+            "from paper_2507_03092_gb300 import binding as B\n"
+            "s = B.Simulator(0)\n"
+            "t._check_wave_cases(s)\n"
+            "s.close()\nprint('ok')\n")
+    for caps in ("8,2,4,4,16", "64,1,2,2,1", "3,1000,1,1,100000", "100,50,100,100,200,3"):
+        env = dict(os.environ, STAB_WAVE_CAPS=caps)
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and "ok" in r.stdout, (caps, r.stdout[-2000:], r.stderr[-4000:])
