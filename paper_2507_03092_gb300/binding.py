@@ -332,12 +332,14 @@ def stab_launch_count(ctx, reset=True) -> int:
 
 
 COUNTER_NAMES = ("waves", "wave_ops", "det_in_wave_kernel", "det", "sum_K", "sum_A",
-                 "pivot_recomputes", "reserved")
+                 "pivot_recomputes", "reserved",
+                 "cyc_pending", "cyc_pivots", "cyc_det_now", "cyc_window", "cyc_mark", "cyc_select",
+                 "cyc_lists", "cyc_rowsums", "cyc_colupd", "cyc_copies", "cyc_other")
 
 
 def stab_engine_counters(ctx, reset=True) -> dict:
-    arr = (ctypes.c_uint64 * 8)()
-    _check(lib().stab_engine_counters(ctx, arr, 8, 1 if reset else 0))
+    arr = (ctypes.c_uint64 * 24)()
+    _check(lib().stab_engine_counters(ctx, arr, 24, 1 if reset else 0))
     return {k: int(v) for k, v in zip(COUNTER_NAMES, arr)}
 
 

@@ -131,11 +131,12 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     const size_t qmap_b = 4 * (size_t)p.n * count;
     const size_t piv_b = 4 * items, bsz_b = 4 * items, stale_b = items;
     const size_t sup_b = 2 * (size_t)SUPCAP * items;
+    const size_t pwl_b = 2 * (size_t)WaveCaps::WCAP_MAX * PWCAP * count;
     const size_t detz_b = 4 * (size_t)32 * 2 * p.H * count;
     const size_t ev_b = 4 * (size_t)std::max<uint32_t>(1, p.dev.ev_total) * count;
     const size_t cnt_b = 4 * (size_t)std::max<size_t>(1, p.layers.size()) * count;
     const size_t bytes = up(4 * words) + up(2 * items) + up(first_b) + up(ev_b) + up(cnt_b) +
-                         up(qmap_b) + up(detz_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b);
+                         up(qmap_b) + up(detz_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b) + up(pwl_b);
     int rc = buf.ensure(bytes);
     if (rc) return rc;
     char *b = (char *)buf.p;
@@ -150,7 +151,8 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     ms.mpiv = (uint32_t *)b; b += up(piv_b);
     ms.mbsz = (uint32_t *)b; b += up(bsz_b);
     ms.mstale = (uint8_t *)b; b += up(stale_b);
-    ms.msup = (uint16_t *)b;
+    ms.msup = (uint16_t *)b; b += up(sup_b);
+    ms.pwl = (uint16_t *)b;
     ms.cap_words = words;
     ms.cap_items = items;
     return STAB_OK;
@@ -356,14 +358,14 @@ int stab_create(stab_ctx **out, int device, void *cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->lc.sm_count = prop.multiProcessorCount;
     ctx->lc.smem_optin = prop.sharedMemPerBlockOptin;
-    if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_err, 512) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return fail(STAB_ERR_OOM, "cudaMalloc for the error flag failed");
     }
     ctx->d_counter = (unsigned int *)((char *)ctx->d_err + 128);
-    ctx->d_stats = (unsigned long long *)((char *)ctx->d_err + 192);
-    cudaMemset(ctx->d_err, 0, 256);
+    ctx->d_stats = (unsigned long long *)((char *)ctx->d_err + 256);
+    cudaMemset(ctx->d_err, 0, 512);
     if (const char *env = getenv("STAB_WAVE_CAPS")) {
         WaveCaps c;
         unsigned v[5];

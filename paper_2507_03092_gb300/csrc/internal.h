@@ -153,6 +153,7 @@ struct MeasScratch {
     uint32_t *mbsz = nullptr;     // [count][max_meas] cached |x-column support|
     uint8_t *mstale = nullptr;    // [count][max_meas] cache invalid
     uint16_t *msup = nullptr;     // [count][max_meas][SUPCAP] column support rows (if small)
+    uint16_t *pwl = nullptr;      // [count][WCAP_MAX][PWCAP] nonzero words of the wave's pivot rows
     uint32_t *ev = nullptr;       // [count][ev_total] noise events
     uint32_t *ev_cnt = nullptr;   // [count][n_layers] noise-event counts
     size_t cap_words = 0, cap_items = 0;
@@ -176,6 +177,7 @@ struct WaveCaps {
     uint32_t window = 128;             // pending measurements examined per wave
 };
 constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list
+constexpr uint32_t PWCAP = 64;         // nonzero words kept per pivot row
 void set_wave_caps(const WaveCaps &c);
 
 // Launch accounting and optional per-kernel CUDA-event timing.
@@ -227,7 +229,7 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
 
 // device counters (unsigned long long) kept next to the error flag
 enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
-             DC_PIV_RECOMP = 6, DC_N = 8 };
+             DC_PIV_RECOMP = 6, DC_PHASE0 = 8, DC_N_PHASES = 11, DC_N = 24 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

@@ -63,6 +63,7 @@ struct LArgs {
     uint32_t *mpiv, *mbsz;           // [B][max_meas] cached pivot / column size
     uint8_t *mstale;                 // [B][max_meas]
     uint16_t *msup;                  // [B][max_meas][SUPCAP]
+    uint16_t *pwl;                   // [B][WCAP_MAX][PWCAP]
     unsigned long long *stats;       // DC_* counters (may be null)
     WaveCaps caps;                   // k_meas_rand list capacities (<= compile-time maxima)
     DevStreams st;
@@ -366,48 +367,111 @@ __global__ void k_gather_cols(LArgs a, uint32_t layer) {
 }
 
 // Sign of the product of the stabilizers selected by the destabilizer column
-// `colK` (H words), computed by one warp.  For commuting rows P_1..P_k (ascending
-// row order) the power of i of the product is
+// `colK` (H words), computed by one warp.  For commuting rows P_1..P_k the
+// power of i of the product taken in any fixed order is
 //   2 sum r_b + sum_b popc(x_b & z_b) + 2 sum_{b<b'} popc(z_b & x_b') - popc(X & Z)
-// with X = xor of x_b, Z = xor of z_b; the product must be +-Z_q, so X = 0.
-// Zp/Xp: per-warp scratch of H words each.
+// with X = xor of x_b, Z = xor of z_b (the rows commute, so the order does not
+// change the product); the product must be +-Z_q, so X = 0.  The selected rows
+// are first listed in `scratch` (2H words); each lane then walks them for its
+// own words, keeping the running xor of z in registers.  If more than 2H rows
+// are selected, the running xors live in scratch instead.
 __device__ int det_outcome_warp(const uint32_t *__restrict__ rm, uint32_t RS, uint32_t Hr, uint32_t H,
                                 const uint32_t *__restrict__ r, const uint32_t *__restrict__ colK,
-                                uint32_t q, uint32_t *__restrict__ Zp, uint32_t *__restrict__ Xp, int *err) {
+                                uint32_t q, uint32_t *__restrict__ scratch, int *err) {
     const int lane = threadIdx.x & 31;
-    for (uint32_t c = lane; c < H; c += 32) { Zp[c] = 0; Xp[c] = 0; }
+    // list the stabilizer rows (partners of the set destabilizer bits)
+    uint32_t nk = 0;
+    for (uint32_t base = 0; base < H; base += 32) {
+        const uint32_t w = base + lane;
+        const uint32_t kw = w < H ? colK[w] : 0u;
+        const uint32_t c = __popc(kw);
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t pos = nk + x - c, m = kw;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < 2 * H) scratch[pos] = 32 * H + 32 * w + b;
+            pos++;
+        }
+        nk += __shfl_sync(FULL_MASK, x, 31);
+    }
     __syncwarp();
     int acc = 0, rsum = 0;
-    for (uint32_t base = 0; base < H; base += 32) {
-        uint32_t kw = (base + lane < H) ? colK[base + lane] : 0u;
-        uint32_t m = __ballot_sync(FULL_MASK, kw != 0);
-        while (m) {
-            const int L = __ffs(m) - 1;
-            m &= m - 1;
-            uint32_t word = __shfl_sync(FULL_MASK, kw, L);
-            const uint32_t u = base + L;
-            while (word) {
-                const int b = __ffs(word) - 1;
-                word &= word - 1;
-                const uint32_t s = 32 * H + 32 * u + b;       // stabilizer partner row
-                const uint32_t *__restrict__ row = rm + (size_t)s * RS;
-#pragma unroll 4
-                for (uint32_t c = lane; c < H; c += 32) {
-                    const uint32_t x = row[c], z = row[Hr + c];
-                    acc += __popc(x & z) + 2 * __popc(x & Zp[c]);
-                    Zp[c] ^= z;
-                    Xp[c] ^= x;
+    bool ok = true;
+    if (nk <= 2 * H) {
+        for (uint32_t e = lane; e < nk; e += 32) rsum += (int)rbit(r, scratch[e]);
+        // each lane owns DW words per chunk and walks the listed rows, issuing
+        // the loads of one row's DW words at once
+        constexpr int DW = 6;
+        for (uint32_t c0 = 0; c0 < H; c0 += 32 * DW) {
+            uint32_t zp[DW], xp[DW];
+#pragma unroll
+            for (int k = 0; k < DW; k++) { zp[k] = 0u; xp[k] = 0u; }
+            for (uint32_t e = 0; e < nk; e++) {
+                const uint32_t *__restrict__ row = rm + (size_t)scratch[e] * RS;
+                uint32_t xv[DW], zv[DW];
+#pragma unroll
+                for (int k = 0; k < DW; k++) {
+                    const uint32_t c = c0 + 32 * k + lane;
+                    xv[k] = c < H ? row[c] : 0u;
+                    zv[k] = c < H ? row[Hr + c] : 0u;
                 }
-                rsum += (int)rbit(r, s);
+#pragma unroll
+                for (int k = 0; k < DW; k++) {
+                    acc += __popc(xv[k] & zv[k]) + 2 * __popc(xv[k] & zp[k]);
+                    zp[k] ^= zv[k];
+                    xp[k] ^= xv[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < DW; k++) {
+                const uint32_t c = c0 + 32 * k + lane;
+                if (c < H) {
+                    const uint32_t wantz = (c == (q >> 5)) ? (1u << (q & 31)) : 0u;
+                    ok &= (xp[k] == 0u) && (zp[k] == wantz);
+                }
             }
         }
+    } else {
+        uint32_t *Zp = scratch, *Xp = scratch + H;
+        for (uint32_t c = lane; c < H; c += 32) { Zp[c] = 0; Xp[c] = 0; }
+        __syncwarp();
+        for (uint32_t base = 0; base < H; base += 32) {
+            uint32_t kw = (base + lane < H) ? colK[base + lane] : 0u;
+            uint32_t m = __ballot_sync(FULL_MASK, kw != 0);
+            while (m) {
+                const int L = __ffs(m) - 1;
+                m &= m - 1;
+                uint32_t word = __shfl_sync(FULL_MASK, kw, L);
+                const uint32_t u = base + L;
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    const uint32_t s = 32 * H + 32 * u + b;
+                    const uint32_t *__restrict__ row = rm + (size_t)s * RS;
+                    for (uint32_t c = lane; c < H; c += 32) {
+                        const uint32_t x = row[c], z = row[Hr + c];
+                        acc += __popc(x & z) + 2 * __popc(x & Zp[c]);
+                        Zp[c] ^= z;
+                        Xp[c] ^= x;
+                    }
+                    if (lane == 0) rsum += (int)rbit(r, s);
+                }
+            }
+        }
+        for (uint32_t c = lane; c < H; c += 32) {
+            const uint32_t wantz = (c == (q >> 5)) ? (1u << (q & 31)) : 0u;
+            ok &= (Xp[c] == 0u) && (Zp[c] == wantz);
+        }
     }
-    bool ok = true;
-    for (uint32_t c = lane; c < H; c += 32) {
-        uint32_t wantz = (c == (q >> 5)) ? (1u << (q & 31)) : 0u;
-        ok &= (Xp[c] == 0u) && (Zp[c] == wantz);
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        rsum += __shfl_xor_sync(FULL_MASK, rsum, o);
     }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
     const int e = (acc + 2 * rsum) & 3;
     if (!__all_sync(FULL_MASK, ok)) set_err(err, DERR_BAD_PRODUCT);
     if (e & 1) set_err(err, DERR_ODD_PHASE);
@@ -426,39 +490,45 @@ __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_
 
 // One warp scans a measured column (CW words): pivot = first set row of the
 // stabilizer half (as slot - 32H, ~0 if none), size = number of set rows, and
-// when size <= SUPCAP the set rows in ascending order into sup[].
+// when size <= SUPCAP the set rows (in no particular order) into sup[].
+// Each lane keeps 8 loads in flight.
 __device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ col, uint32_t H, uint32_t CW,
                                                  uint32_t &piv, uint32_t &size, uint16_t *__restrict__ sup) {
     const int lane = threadIdx.x & 31;
     uint32_t base = 0, pv = 0xffffffffu;
-    uint32_t v = lane < CW ? col[lane] : 0u;
-    for (uint32_t w0 = 0; w0 < CW; w0 += 32) {
-        const uint32_t vn = (w0 + 32 + lane < CW) ? col[w0 + 32 + lane] : 0u;   // prefetch
-        const uint32_t w = w0 + lane;
-        if (pv == 0xffffffffu) {
-            const uint32_t m = __ballot_sync(FULL_MASK, w >= H && v != 0);
-            if (m) {
-                const int L = __ffs(m) - 1;
-                const uint32_t vw = __shfl_sync(FULL_MASK, v, L);
-                pv = 32 * (w0 + L - H) + __ffs(vw) - 1;
-            }
+    for (uint32_t w0 = 0; w0 < CW; w0 += 256) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t w = w0 + 32 * k + lane;
+            v[k] = w < CW ? col[w] : 0u;
         }
-        const uint32_t c = __popc(v);
+        uint32_t c = 0, mine = 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            c += __popc(v[k]);
+            const uint32_t w = w0 + 32 * k + lane;
+            if (mine == 0xffffffffu && w >= H && v[k]) mine = 32 * (w - H) + __ffs(v[k]) - 1;
+        }
+        for (int o = 16; o; o >>= 1) mine = min(mine, __shfl_xor_sync(FULL_MASK, mine, o));
+        if (pv == 0xffffffffu) pv = mine;
         uint32_t x = c;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
             if (lane >= o) x += y;
         }
-        const uint32_t tot = __shfl_sync(FULL_MASK, x, 31);
         uint32_t pos = base + x - c;
-        uint32_t m = v;
-        while (m && pos < SUPCAP) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            sup[pos++] = (uint16_t)(32 * w + b);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            uint32_t m = v[k];
+            const uint32_t w = w0 + 32 * k + lane;
+            while (m && pos < SUPCAP) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                sup[pos++] = (uint16_t)(32 * w + b);
+            }
         }
-        base += tot;
-        v = vn;
+        base += __shfl_sync(FULL_MASK, x, 31);
     }
     piv = pv;
     size = base;
@@ -507,9 +577,8 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
             count(a, DC_SUM_K, k);
         }
     }
-    uint32_t *Zp = smem + (size_t)warp * 2 * H, *Xp = Zp + H;
     const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
-                                   col, m.q, Zp, Xp, a.err);
+                                   col, m.q, smem + (size_t)warp * 2 * H, a.err);
     if (lane == 0) {
         stat[i] = MS_DONE;
         out[i] = (uint8_t)o;
@@ -518,23 +587,69 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
 }
 
 // rowsum(s, p) on the row-packed copy by one warp: row s <- row p * row s
-// with r_s from 2 r_s + 2 r_p + (power of i) mod 4 (Appendix B).
+// with r_s from 2 r_s + 2 r_p + (power of i) mod 4 (Appendix B).  Each lane
+// issues the loads of RSW words of both rows before using any of them.
+constexpr int RSW = 5;
 __device__ __forceinline__ void rowsum_warp(uint32_t *rm, uint32_t RS, uint32_t Hr, uint32_t H,
                                             uint32_t *r, uint32_t s, uint32_t p, int *err) {
     const int lane = threadIdx.x & 31;
     const uint32_t *__restrict__ rp = rm + (size_t)p * RS;
     uint32_t *__restrict__ rs = rm + (size_t)s * RS;
+    const uint32_t rwords = lane == 0 ? ((r[s >> 5] >> (s & 31)) & 1u) | (((r[p >> 5] >> (p & 31)) & 1u) << 1) : 0u;
     int acc = 0;
-#pragma unroll 4
-    for (uint32_t c = lane; c < H; c += 32) {
-        const uint32_t xp = rp[c], zp = rp[Hr + c], xs = rs[c], zs = rs[Hr + c];
-        acc += phase_word(xp, zp, xs, zs);
-        rs[c] = xs ^ xp;
-        rs[Hr + c] = zs ^ zp;
+    for (uint32_t c0 = 0; c0 < H; c0 += 32 * RSW) {
+        uint32_t xp[RSW], zp[RSW], xs[RSW], zs[RSW];
+#pragma unroll
+        for (int k = 0; k < RSW; k++) {
+            const uint32_t c = c0 + 32 * k + lane;
+            const bool in = c < H;
+            xp[k] = in ? rp[c] : 0u;
+            zp[k] = in ? rp[Hr + c] : 0u;
+            xs[k] = in ? rs[c] : 0u;
+            zs[k] = in ? rs[Hr + c] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < RSW; k++) {
+            const uint32_t c = c0 + 32 * k + lane;
+            acc += phase_word(xp[k], zp[k], xs[k], zs[k]);
+            if (c < H) {
+                rs[c] = xs[k] ^ xp[k];
+                rs[Hr + c] = zs[k] ^ zp[k];
+            }
+        }
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
     if (lane == 0) {
-        const uint32_t r_s = rbit(r, s), r_p = rbit(r, p);
+        const uint32_t r_s = rwords & 1u, r_p = rwords >> 1;
+        const int e = (int)(2 * r_s + 2 * r_p) + acc;
+        if (e & 1) set_err(err, DERR_ODD_PHASE);
+        const uint32_t nr = (uint32_t)((e & 3) >> 1);
+        if (nr != r_s) atomicXor(&r[s >> 5], 1u << (s & 31));
+    }
+}
+
+// rowsum(s, p) restricted to the words where row p is nonzero (listed in
+// `wl`, `nwl` entries): elsewhere row p contributes neither an XOR nor a power
+// of i (phase_word(0, 0, x, z) = 0), so the result is the full rowsum's.
+__device__ __forceinline__ void rowsum_warp_sparse(uint32_t *rm, uint32_t RS, uint32_t Hr, uint32_t *r,
+                                                   uint32_t s, uint32_t p, const uint16_t *wl,
+                                                   uint32_t nwl, int *err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t *__restrict__ rp = rm + (size_t)p * RS;
+    uint32_t *__restrict__ rs = rm + (size_t)s * RS;
+    const uint32_t rwords = lane == 0 ? ((r[s >> 5] >> (s & 31)) & 1u) | (((r[p >> 5] >> (p & 31)) & 1u) << 1) : 0u;
+    const uint32_t c0 = lane < nwl ? wl[lane] : 0u, c1 = lane + 32 < nwl ? wl[lane + 32] : 0u;
+    const bool in0 = lane < nwl, in1 = lane + 32 < nwl;
+    const uint32_t xp0 = in0 ? rp[c0] : 0u, zp0 = in0 ? rp[Hr + c0] : 0u;
+    const uint32_t xs0 = in0 ? rs[c0] : 0u, zs0 = in0 ? rs[Hr + c0] : 0u;
+    const uint32_t xp1 = in1 ? rp[c1] : 0u, zp1 = in1 ? rp[Hr + c1] : 0u;
+    const uint32_t xs1 = in1 ? rs[c1] : 0u, zs1 = in1 ? rs[Hr + c1] : 0u;
+    int acc = phase_word(xp0, zp0, xs0, zs0) + phase_word(xp1, zp1, xs1, zs1);
+    if (in0) { rs[c0] = xs0 ^ xp0; rs[Hr + c0] = zs0 ^ zp0; }
+    if (in1) { rs[c1] = xs1 ^ xp1; rs[Hr + c1] = zs1 ^ zp1; }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if (lane == 0) {
+        const uint32_t r_s = rwords & 1u, r_p = rwords >> 1;
         const int e = (int)(2 * r_s + 2 * r_p) + acc;
         if (e & 1) set_err(err, DERR_ODD_PHASE);
         const uint32_t nr = (uint32_t)((e & 3) >> 1);
@@ -548,10 +663,12 @@ constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;
 constexpr uint32_t PAIRCAP = WaveCaps::PAIRCAP_MAX;
 constexpr uint32_t JCAP = WaveCaps::JCAP_MAX;
 constexpr uint16_t NOPIV = 0xffffu;
+constexpr uint32_t QMAP_SMEM_MAX = 16384;   // qubits whose item map fits shared memory
+static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
 
 size_t rand_smem(uint32_t n, uint32_t H) {
-    (void)n;
-    return (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H + 64;
+    return (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H +
+           (n <= QMAP_SMEM_MAX ? 4 * (size_t)n : 0) + 2 * WCAP + 10 * (size_t)PAIRCAP + 64;
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
@@ -580,10 +697,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
     return res;
 }
 
-__global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t layer) {
+__global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_wt[32];
     __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any;
+    __shared__ uint32_t s_tw, s_tt, s_more;
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -598,7 +716,9 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
     uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
     uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
     uint32_t *claim = firstp + 64 * H;                                // rowsum claims
-    int *qmap = a.qmap + (size_t)t * n;
+    // qubit -> item map: shared memory when n is small enough, else global
+    int *qmap = n <= QMAP_SMEM_MAX ? (int *)(smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW)
+                                   : a.qmap + (size_t)t * n;
     uint32_t *detz = a.detz + (size_t)t * 32 * 2 * H + (size_t)warp * 2 * H;
     uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
     uint8_t *mstale = a.mstale + t * a.m_stride;
@@ -610,6 +730,11 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
     uint32_t *pairs = (uint32_t *)(sel + WCAP);    // row | sel index << 16
     uint32_t *ents = pairs + PAIRCAP;              // item | sel index << 16 | bp << 31
     uint32_t *qmask = ents + JCAP;                 // destabilizer partners of the wave [CW]
+    uint16_t *pwn = (uint16_t *)(qmask + CW + (n <= QMAP_SMEM_MAX ? n : 0));   // nonzero words per pivot
+    uint32_t *wl_off = (uint32_t *)(pwn + WCAP);   // task offsets of the round's winning pairs [PAIRCAP]
+    int *pacc = (int *)(wl_off + PAIRCAP);         // their accumulated powers of i [PAIRCAP]
+    uint16_t *wl_e = (uint16_t *)(pacc + PAIRCAP); // their pair indices [PAIRCAP]
+    uint16_t *pwl = a.pwl + (size_t)t * WCAP * PWCAP;
 
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -625,6 +750,16 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
 
     // first[row] holds stamp(wave) | k for the earliest op k of the wave's window
     // whose column holds row; stamps decrease, so stale entries never win atomicMin.
+    unsigned long long tlast = clock64();
+#define PHASE(k)                                                              \
+    do {                                                                      \
+        if (threadIdx.x == 0 && a.stats) {                                    \
+            const unsigned long long now_ = clock64();                         \
+            atomicAdd(&a.stats[DC_PHASE0 + (k)], now_ - tlast);               \
+            tlast = now_;                                                     \
+        }                                                                     \
+    } while (0)
+    bool full_scan = true;          // pending list rebuilt from all items (first wave, or overflow)
     // Stamps only decrease (marks per wave, claims per claim round), so entries
     // left from earlier waves never win an atomicMin; when a counter runs out
     // its arrays are cleared and it restarts.
@@ -643,18 +778,43 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
         }
         const uint32_t stamp = (0xfffeu - wave) << 16;
         wave++;
-        // ---- (1) ordered list of pending random measurements (first pcap)
+        // ---- (1) ordered list of pending random measurements (first pcap):
+        // from all items on the first wave or after an overflow, else by
+        // compacting the previous list (ops only ever leave it)
         {
-            uint32_t cnt = 0;
-            const uint32_t per = (M.count + blockDim.x - 1) / blockDim.x;
-            const uint32_t i0 = threadIdx.x * per, i1 = min(M.count, i0 + per);
-            for (uint32_t i = i0; i < i1; i++) cnt += stat[i] == MS_RANDOM;
-            uint32_t off = block_excl_scan(cnt, s_wt, &s_tot);
-            for (uint32_t i = i0; i < i1; i++)
-                if (stat[i] == MS_RANDOM) {
-                    if (off < pcap) pend[off] = (uint16_t)i;
-                    off++;
+            if (full_scan) {
+                uint32_t cnt = 0;
+                const uint32_t per = (M.count + blockDim.x - 1) / blockDim.x;
+                const uint32_t i0 = threadIdx.x * per, i1 = min(M.count, i0 + per);
+                for (uint32_t i = i0; i < i1; i++) cnt += stat[i] == MS_RANDOM;
+                uint32_t off = block_excl_scan(cnt, s_wt, &s_tot);
+                for (uint32_t i = i0; i < i1; i++)
+                    if (stat[i] == MS_RANDOM) {
+                        if (off < pcap) pend[off] = (uint16_t)i;
+                        off++;
+                    }
+                full_scan = s_tot > pcap;
+            } else {
+                // each thread owns at most PCAP / RAND_THREADS = 8 entries
+                const uint32_t np0 = s_np;
+                const uint32_t per = (np0 + blockDim.x - 1) / blockDim.x;
+                const uint32_t k0 = threadIdx.x * per, k1 = min(np0, k0 + per);
+                uint16_t keep[8];
+                uint32_t cnt = 0;
+#pragma unroll
+                for (uint32_t d = 0; d < 8; d++) {
+                    const uint32_t k = k0 + d;
+                    if (k < k1) {
+                        const uint16_t i = pend[k];
+                        if (stat[i] == MS_RANDOM) keep[cnt++] = i;
+                    }
                 }
+                const uint32_t off = block_excl_scan(cnt, s_wt, &s_tot);   // syncs: all reads done
+#pragma unroll
+                for (uint32_t d = 0; d < 8; d++)
+                    if (d < cnt) pend[off + d] = keep[d];
+            }
+            __syncthreads();
             if (threadIdx.x == 0) {
                 s_np = min(s_tot, pcap);
                 s_nsel = 0; s_npair = 0; s_nent = 0;
@@ -663,6 +823,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
             __syncthreads();
         }
+        PHASE(0);
         const uint32_t np = s_np;
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
@@ -690,12 +851,13 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(1);
         // ---- (3) ops that became deterministic: outcome from the current tableau
         for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
             if (piv[k] != NOPIV) continue;
             const uint32_t i = pend[k];
             const MItem m = a.P.mitems[M.first + i];
-            const int o = det_outcome_warp(rm, RS, Hr, H, r, cols + (size_t)i * CW, m.q, detz, detz + H, a.err);
+            const int o = det_outcome_warp(rm, RS, Hr, H, r, cols + (size_t)i * CW, m.q, detz, a.err);
             if (lane == 0) {
                 out[i] = (uint8_t)o;
                 stat[i] = MS_DONE;
@@ -705,6 +867,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
         }
         if (s_nrand == 0) {          // block-uniform
             __syncthreads();
+            PHASE(2);
             continue;
         }
         // ---- (4) window: leading examined ops whose columns total <= budget rows
@@ -726,6 +889,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             if (lane == 0) s_kend = max(kend, s_firstrand + 1);
         }
         __syncthreads();
+        PHASE(3);
         const uint32_t kend = s_kend;
         // ---- (5) mark rows with the earliest window op holding them in its
         // column, and pivot rows with the earliest window op pivoting on them
@@ -749,6 +913,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(4);
         // ---- (6) select op k when no earlier window op pivots on a row of its
         // column and no earlier window op's column holds its pivot row
         for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
@@ -779,6 +944,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(5);
         // ---- (7) list rowsum pairs and measured-column updates
         const uint32_t nsel = min(s_nsel, wcap);
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
@@ -823,6 +989,19 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
                     }
                 }
             }
+            // nonzero words of row p (x or z), for the sparse rowsums
+            {
+                uint32_t cnt = 0;
+                for (uint32_t c0 = 0; c0 < H; c0 += 32) {
+                    const uint32_t c = c0 + lane;
+                    const bool nzw = c < H && (rp_[c] | rp_[Hr + c]) != 0u;
+                    const uint32_t m = __ballot_sync(FULL_MASK, nzw);
+                    const uint32_t pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (nzw && pos < PWCAP) pwl[x * PWCAP + pos] = (uint16_t)c;
+                    cnt += __popc(m);
+                }
+                if (lane == 0) pwn[x] = (uint16_t)min(cnt, 0xffffu);
+            }
             if (lane == 0) {
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
@@ -830,6 +1009,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(6);
         const uint32_t npair = s_npair, nent = s_nent;
         if (threadIdx.x == 0) {
             count(a, DC_WAVES, 1);
@@ -840,7 +1020,10 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
         // ops is multiplied by their (commuting) pivots one at a time: each
         // round every pending pair claims its row and the winners go.
         if (npair <= paircap) {
-            // a row is held by at most nsel wave ops, so nsel rounds suffice
+            // a row is held by at most nsel wave ops, so nsel rounds suffice.
+            // Within a round the winning pairs have distinct rows; each (pair,
+            // nonzero pivot word) is one thread task, the per-pair power of i
+            // is summed in shared memory and the sign set afterwards.
             bool done = false;
             for (uint32_t round = 0; round <= nsel; round++) {
                 if (cround >= 0xfff0u) {
@@ -850,26 +1033,84 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
                 }
                 const uint32_t cst = (0xfffeu - cround) << 16;
                 cround++;
-                if (threadIdx.x == 0) s_tot = 0;
-                __syncthreads();
                 for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x)
                     if (!(pairs[e] >> 31)) atomicMin(&claim[pairs[e] & 0xffffu], cst | e);
+                if (threadIdx.x == 0) s_more = 0;
                 __syncthreads();
-                for (uint32_t e = (uint32_t)warp; e < npair; e += (uint32_t)nw) {
+                // winners of this round and their task counts (contiguous pairs per thread)
+                const uint32_t per = (npair + blockDim.x - 1) / blockDim.x;
+                const uint32_t e0 = threadIdx.x * per, e1 = min(npair, e0 + per);
+                uint32_t nwin = 0, ntask = 0;
+                bool losers = false;
+                for (uint32_t e = e0; e < e1; e++) {
                     const uint32_t pe = pairs[e];
                     if (pe >> 31) continue;
-                    const uint32_t row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
-                    if (claim[row] != (cst | e)) {
-                        if (lane == 0) s_tot = 1;
-                        continue;
+                    if (claim[pe & 0xffffu] != (cst | e)) { losers = true; continue; }
+                    const uint32_t x = (pe >> 16) & 0x7fffu;
+                    nwin++;
+                    ntask += pwn[x] <= PWCAP ? pwn[x] : 0u;
+                }
+                if (losers) s_more = 1;
+                uint32_t kw = block_excl_scan(nwin, s_wt, &s_tw);
+                uint32_t kt = block_excl_scan(ntask, s_wt, &s_tt);
+                for (uint32_t e = e0; e < e1; e++) {
+                    const uint32_t pe = pairs[e];
+                    if ((pe >> 31) || claim[pe & 0xffffu] != (cst | e)) continue;
+                    const uint32_t x = (pe >> 16) & 0x7fffu;
+                    wl_e[kw] = (uint16_t)e;
+                    wl_off[kw] = kt;
+                    pacc[kw] = 0;
+                    kw++;
+                    kt += pwn[x] <= PWCAP ? pwn[x] : 0u;
+                }
+                __syncthreads();
+                const uint32_t totw = s_tw, tott = s_tt;
+                // tasks: thread per (winning pair, nonzero pivot word)
+                for (uint32_t tk = threadIdx.x; tk < tott; tk += blockDim.x) {
+                    uint32_t lo = 0, hi = totw;                 // upper bound of tk in wl_off
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (wl_off[mid] <= tk) lo = mid + 1; else hi = mid;
                     }
-                    rowsum_warp(rm, RS, Hr, H, r, row, 32 * H + piv[sel[x]], a.err);
+                    const uint32_t k = lo - 1;                  // wl_off[0] = 0 <= tk, so lo >= 1
+                    const uint32_t pe = pairs[wl_e[k]], row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
+                    const uint32_t c = pwl[x * PWCAP + (tk - wl_off[k])];
+                    const uint32_t p = 32 * H + piv[sel[x]];
+                    const uint32_t xp = rm[(size_t)p * RS + c], zp = rm[(size_t)p * RS + Hr + c];
+                    uint32_t *rs = rm + (size_t)row * RS;
+                    const uint32_t xs = rs[c], zs = rs[Hr + c];
+                    atomicAdd(&pacc[k], phase_word(xp, zp, xs, zs));
+                    rs[c] = xs ^ xp;
+                    rs[Hr + c] = zs ^ zp;
+                }
+                __syncthreads();
+                // signs of the winning sparse pairs; dense-pivot winners by warps
+                for (uint32_t k = threadIdx.x; k < totw; k += blockDim.x) {
+                    const uint32_t e = wl_e[k], pe = pairs[e];
+                    const uint32_t x = (pe >> 16) & 0x7fffu;
+                    if (pwn[x] > PWCAP) continue;
+                    const uint32_t row = pe & 0xffffu, p = 32 * H + piv[sel[x]];
+                    const uint32_t r_s = rbit(r, row), r_p = rbit(r, p);
+                    const int ev = (int)(2 * r_s + 2 * r_p) + pacc[k];
+                    if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
+                    if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
+                    pairs[e] = pe | 0x80000000u;
+                }
+                for (uint32_t k = (uint32_t)warp; k < totw; k += (uint32_t)nw) {
+                    const uint32_t e = wl_e[k], pe = pairs[e];
+                    const uint32_t x = (pe >> 16) & 0x7fffu;
+                    if (pwn[x] <= PWCAP) continue;
+                    rowsum_warp(rm, RS, Hr, H, r, pe & 0xffffu, 32 * H + piv[sel[x]], a.err);
+                    __syncwarp();
                     if (lane == 0) pairs[e] = pe | 0x80000000u;
                 }
                 __syncthreads();
-                if (!s_tot) { done = true; break; }
+                const bool more = s_more != 0;
+                __syncthreads();          // everyone has read the flag before it is reset
+                if (!more) { done = true; break; }
             }
             if (!done && threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+            PHASE(7);
         } else {
             // list overflow: one warp applies the pivots row by row, in wave order
             for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
@@ -929,6 +1170,7 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(8);
         // ---- (10) bit fixes (row q gets x_{p,b}, row p gets 0), row copies
         if (nent <= jcap) {
             for (uint32_t e = threadIdx.x; e < nent; e += blockDim.x) {
@@ -982,7 +1224,9 @@ __global__ void __launch_bounds__(RAND_THREADS) k_meas_rand(LArgs a, uint32_t la
             }
         }
         __syncthreads();
+        PHASE(9);
     }
+#undef PHASE
 }
 
 // X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a).
@@ -1093,6 +1337,7 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
         a.mbsz = ms->mbsz;
         a.mstale = ms->mstale;
         a.msup = ms->msup;
+        a.pwl = ms->pwl;
     }
     if (st) a.st = *st;
     a.record = record;
