@@ -177,6 +177,26 @@ typedef struct stab_job_group {
 
 int stab_sample_batch(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
 
+/* Same launch as stab_sample_batch, for callers that cannot allocate device
+ * memory at call time: code running where every device allocation is owned by
+ * a host framework's pool, or latency-critical loops that cannot afford
+ * cudaMalloc's implicit synchronisation.  (The paper has no counterpart; this
+ * is a property of this library.)  The resident engine's only global scratch,
+ * its job table and work counter, live in a fixed array compiled into the
+ * library instead of memory from cudaMalloc: at most 8192 shots in total and 64
+ * groups per call (about 0.7 MiB, held on every GPU that loads the library
+ * until the process exits); larger batches are rejected with
+ * STAB_ERR_UNSUPPORTED before anything is launched.  The call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library call); the caller
+ * still passes the streams and record buffers, and the circuits must have been
+ * compiled before.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that first
+ * call before any stream capture.  Every call shares the array and a host
+ * staging buffer: calls whose launches overlap on the GPU, or that run
+ * concurrently from several host threads, race; the work counter is cleared by
+ * each call before its launch. */
+int stab_sample_batch_noalloc(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
+
 /* Resident-engine launch shape, chosen per qubit-count bucket by the autotuner. */
 typedef struct stab_tune {
     uint32_t group_threads;    /* threads per tableau: 32, 64, 128 or 256 */

@@ -118,6 +118,7 @@ _SIGS = {
     "stab_sample": (I32, [P, U64, U32, ctypes.POINTER(Streams), P, U64, U32]),
     "stab_sample_host": (I32, [P, U64, U32, P, U64, P, U64, P, U64, U32]),
     "stab_sample_batch": (I32, [P, ctypes.POINTER(JobGroup), SZ]),
+    "stab_sample_batch_noalloc": (I32, [P, ctypes.POINTER(JobGroup), SZ]),
     "stab_autotune": (I32, [P, PU64, SZ, U32]),
     "stab_get_tune": (I32, [P, U32, ctypes.POINTER(Tune)]),
     "stab_set_tune": (I32, [P, U32, ctypes.POINTER(Tune)]),
@@ -267,6 +268,12 @@ def stab_sample_host(ctx, cid, shots, coins, noise, record_words, engine=ENGINE_
 def stab_sample_batch(ctx, groups):
     arr = (JobGroup * len(groups))(*groups)
     _check(lib().stab_sample_batch(ctx, arr, len(groups)))
+
+
+def stab_sample_batch_noalloc(ctx, groups):
+    """stab_sample_batch without device allocation (fixed in-library scratch)."""
+    arr = (JobGroup * len(groups))(*groups)
+    _check(lib().stab_sample_batch_noalloc(ctx, arr, len(groups)))
 
 
 def stab_autotune(ctx, cids, shots):

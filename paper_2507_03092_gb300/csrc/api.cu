@@ -223,7 +223,7 @@ static int upload_prog(HostProg &P) {
     return STAB_OK;
 }
 
-static const DevProg *dev_desc(const HostProg &P) {
+const DevProg *prog_desc(const HostProg &P) {
     size_t off[7];
     prog_layout(P, off);
     return (const DevProg *)((char *)P.dmem + off[6]);
@@ -285,7 +285,7 @@ int run_resident_groups(stab_ctx *ctx, const stab_job_group *groups, size_t n_gr
         if (G.record_words < p->info.record_words)
             return fail(STAB_ERR_STREAM_SHORT, "record has fewer words per shot than the circuit needs");
         max_n = std::max(max_n, p->n);
-        const DevProg *dp = dev_desc(*p);
+        const DevProg *dp = prog_desc(*p);
         for (uint32_t k = 0; k < G.shots; k++) {
             ResJob j{};
             j.prog = dp;

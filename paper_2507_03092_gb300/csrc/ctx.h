@@ -47,6 +47,7 @@ namespace stab {
 stab_tune default_tune(const stab_ctx *ctx, uint32_t n);
 stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n);
 const HostProg *find_prog(stab_ctx *ctx, uint64_t id);
+const DevProg *prog_desc(const HostProg &p);     // device copy of p's descriptor
 DevStreams to_dev(const stab_streams &s);
 int check_streams(const HostProg &p, const stab_streams *s, uint32_t shots);
 // launch the resident engine over job groups (ctx->mu held)

@@ -10,6 +10,7 @@
 // a column-packed tableau in shared memory: x[j][w], z[j][w] hold rows
 // 32w..32w+31 of column j, so a gate touches CW contiguous words per column.
 #include "device_common.cuh"
+#include "ctx.h"
 
 #include <algorithm>
 
@@ -306,3 +307,114 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, 
 }
 
 }  // namespace stab
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch launch
+// ---------------------------------------------------------------------------
+// The resident engine's global scratch is its job table and its work counter.
+// stab_sample_batch_noalloc keeps both in this file-scope device array instead
+// of memory obtained from cudaMalloc.  Every GPU that loads the library holds
+// the array until the process exits; all calls share it.
+namespace stab {
+
+constexpr uint32_t NOALLOC_MAX_SHOTS = 8192;
+constexpr uint32_t NOALLOC_MAX_GROUPS = 64;
+constexpr size_t NOALLOC_JOBS_OFF = 256;        // counter in the first 256 bytes
+constexpr size_t NOALLOC_BYTES = NOALLOC_JOBS_OFF + (size_t)NOALLOC_MAX_SHOTS * sizeof(ResJob);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// host staging for the job table (shared by all calls, like the device array)
+static ResJob g_noalloc_jobs[NOALLOC_MAX_SHOTS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void *g_noalloc_dev[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+static std::mutex g_noalloc_mu;
+
+}  // namespace stab
+
+extern "C" int stab_sample_batch_noalloc(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups) {
+    using namespace stab;
+    if (!ctx) return fail(STAB_ERR_ARG, "context is NULL");
+    if (n_groups && !groups) return fail(STAB_ERR_ARG, "groups is NULL");
+    if (n_groups > NOALLOC_MAX_GROUPS)
+        return fail(STAB_ERR_UNSUPPORTED, "stab_sample_batch_noalloc takes at most " +
+                                              std::to_string(NOALLOC_MAX_GROUPS) + " groups");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    std::lock_guard<std::mutex> lk2(g_noalloc_mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e) return cuda_fail(e, "cudaSetDevice");
+    if (ctx->device < 0 || ctx->device >= NOALLOC_MAX_DEVICES)
+        return fail(STAB_ERR_UNSUPPORTED, "device index too large for the allocation-free path");
+    // set-up, once per device with that device current: the array's device address
+    if (!g_noalloc_dev[ctx->device]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+        g_noalloc_dev[ctx->device] = ptr;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_dev[ctx->device];
+    // validate and size the batch before touching the device
+    uint64_t total = 0;
+    uint32_t max_n = 0;
+    for (size_t gi = 0; gi < n_groups; gi++) {
+        const stab_job_group &G = groups[gi];
+        const HostProg *p = find_prog(ctx, G.circuit_id);
+        if (!p) return fail(STAB_ERR_NOT_FOUND, "unknown circuit id " + std::to_string(G.circuit_id));
+        if (!resident_supported(p->n, ctx->lc))
+            return fail(STAB_ERR_UNSUPPORTED, "n = " + std::to_string(p->n) + " does not fit the resident engine");
+        int rc = check_streams(*p, &G.streams, G.shots);
+        if (rc) return rc;
+        if (G.shots && !G.d_record) return fail(STAB_ERR_ARG, "record buffer is NULL");
+        if (G.record_words < p->info.record_words)
+            return fail(STAB_ERR_STREAM_SHORT, "record has fewer words per shot than the circuit needs");
+        total += G.shots;
+        max_n = std::max(max_n, p->n);
+    }
+    if (total > NOALLOC_MAX_SHOTS)
+        return fail(STAB_ERR_UNSUPPORTED, "stab_sample_batch_noalloc runs at most " +
+                                              std::to_string(NOALLOC_MAX_SHOTS) + " shots per call (got " +
+                                              std::to_string(total) + ")");
+    if (!total) return STAB_OK;
+    // job table: groups in decreasing cost order (longest shots first)
+    uint32_t order[NOALLOC_MAX_GROUPS];
+    uint64_t cost[NOALLOC_MAX_GROUPS];
+    for (size_t gi = 0; gi < n_groups; gi++) {          // insertion sort: no temporary buffers
+        const uint64_t c = find_prog(ctx, groups[gi].circuit_id)->cost;
+        size_t j = gi;
+        while (j > 0 && cost[j - 1] < c) {
+            order[j] = order[j - 1];
+            cost[j] = cost[j - 1];
+            j--;
+        }
+        order[j] = (uint32_t)gi;
+        cost[j] = c;
+    }
+    uint32_t k = 0;
+    for (size_t oi = 0; oi < n_groups; oi++) {
+        const stab_job_group &G = groups[order[oi]];
+        const HostProg *p = find_prog(ctx, G.circuit_id);
+        for (uint32_t sh = 0; sh < G.shots; sh++) {
+            ResJob &j = g_noalloc_jobs[k++];
+            j.prog = prog_desc(*p);
+            j.st = to_dev(G.streams);
+            j.record = (unsigned long long *)G.d_record;
+            j.rec_stride = G.record_words;
+            j.shot = sh;
+            j.pad = 0;
+        }
+        if (G.shots) {
+            e = cudaMemsetAsync(G.d_record, 0, (size_t)G.shots * G.record_words * 8, ctx->stream);
+            if (e) return cuda_fail(e, "clearing records");
+        }
+    }
+    e = cudaMemcpyAsync(base + NOALLOC_JOBS_OFF, g_noalloc_jobs, (size_t)total * sizeof(ResJob),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e) return cuda_fail(e, "copying the job table");
+    const stab_tune t = lookup_tune(ctx, max_n);
+    // resident_run zeroes the counter (first word of the array) before the launch
+    e = resident_run((const ResJob *)(base + NOALLOC_JOBS_OFF), (uint32_t)total, max_n, t,
+                     (unsigned int *)base, ctx->d_err, ctx->lc, ctx->stream, nullptr);
+    if (e) return cuda_fail(e, "resident launch");
+    return STAB_OK;
+}
