@@ -379,3 +379,17 @@ def test_random_measurement_moves_pivot_row_to_destabilizer():
         x, z, r = t.get()
         assert (int(x[0, 0]), int(z[0, 0]), int(r[0])) == (1, 0, 1)
         assert (int(x[1, 0]), int(z[1, 0]), int(r[1])) == (0, 1, coin)
+
+
+def test_serving_trace_is_seeded_poisson():
+    from paper_2507_03092_gb300 import serve_trace as T
+    a = T.make_trace(200.0, 60.0, seed=0)
+    b = T.make_trace(200.0, 60.0, seed=0)
+    assert [(r.t_arrival, r.d, r.shots) for r in a] == [(r.t_arrival, r.d, r.shots) for r in b]
+    assert 11000 < len(a) < 13000                       # ~ rate * duration
+    gaps = np.diff([r.t_arrival for r in a])
+    assert abs(gaps.mean() - 1 / 200.0) < 2e-4
+    assert {r.d for r in a} == set(range(3, 32, 2))
+    shots = np.array([r.shots for r in a])
+    assert shots.min() >= 1 and shots.max() <= 256 and abs(shots.mean() - 128.5) < 5
+    assert len({r.seed for r in a}) == len(a)            # streams keyed per request
