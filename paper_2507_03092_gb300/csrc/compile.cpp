@@ -96,6 +96,8 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         first = type == LT_GATE ? (uint32_t)P.gitems.size() : (uint32_t)P.mitems.size();
     };
     auto touch = [&](uint32_t q, int64_t item) { owner[q] = item; touched.push_back(q); };
+    // last_m[q]: the measurement item of the last op on q if that op was an M or R
+    std::vector<int64_t> last_m(n, -1);
 
     for (size_t k = 0; k < n_ops; k++) {
         const stab_op &o = ops[k];
@@ -103,6 +105,17 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         if (kind == STAB_NOP || kind == STAB_TICK) continue;
         n_real++;
         uint32_t a = o.q0, b = is_two(kind) ? o.q1 : o.q0;
+        if (kind == STAB_R && last_m[a] >= 0) {
+            // R right after M/R on the same qubit: deterministic, outcome = that
+            // measurement's; fold it in as "X if the outcome was 1" (or drop it
+            // after a reset, whose outcome is 0).  Its coin slot is still used up.
+            MItem &prev = P.mitems[(size_t)last_m[a]];
+            if (!(prev.flags & (MF_RESET | MF_RESET_AFTER))) prev.flags |= MF_RESET_AFTER;
+            c_ord++;
+            continue;
+        }
+        last_m[a] = -1;
+        if (is_two(kind)) last_m[b] = -1;
         if (is_meas_class(kind)) {
             if (cur != LT_MEAS || owner[a] >= 0) open_layer(LT_MEAS);
             MItem m{};
@@ -119,6 +132,7 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
                 else m.flags = MF_RESET;
             }
             touch(a, (int64_t)P.mitems.size());
+            if (kind != STAB_RESET_ERR) last_m[a] = (int64_t)P.mitems.size();
             P.mitems.push_back(m);
             continue;
         }
@@ -164,6 +178,13 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         }
     }
     close_layer();
+    // folded resets may have flagged items of layers closed earlier
+    for (auto &L : P.layers)
+        if (L.type == LT_MEAS) {
+            L.has_cond = 0;
+            for (uint32_t i = L.first; i < L.first + L.count; i++)
+                if (P.mitems[i].flags) L.has_cond = 1;
+        }
     if (m_ord > 0xfffffff0ull || c_ord > 0xfffffff0ull || l_ord > 0xfffffff0ull) {
         *err = "circuit too long (more than 2^32 measurements or noise draws)";
         return STAB_ERR_UNSUPPORTED;

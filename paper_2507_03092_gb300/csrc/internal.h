@@ -30,7 +30,10 @@ enum LayerType : uint32_t { LT_GATE = 0, LT_MEAS = 1 };
 // noise target of an item's noise op
 enum : uint8_t { NT_A = 0, NT_B = 1, NT_AB = 2, NT_BA = 3 };
 // measurement item flags
-enum : uint32_t { MF_RESET = 1u, MF_RESET_ERR = 2u };
+enum : uint32_t { MF_RESET = 1u, MF_RESET_ERR = 2u, MF_RESET_AFTER = 4u };
+// MF_RESET_AFTER: an R that followed this M on the same qubit with no op on the
+// qubit in between was folded in: that R is deterministic with this M's outcome,
+// so it reduces to X after the measurement when the outcome is 1.
 
 struct GItem {            // 32 bytes
     uint32_t a, b;        // qubits (b == a for one-qubit items)

@@ -1244,7 +1244,7 @@ __global__ void k_cond(LArgs a, uint32_t layer) {
         const MItem m = a.P.mitems[M.first + i];
         if (!m.flags) continue;
         bool fx = false, fz = false;
-        if (m.flags & MF_RESET) fx = out[i] != 0;
+        if (m.flags & (MF_RESET | MF_RESET_AFTER)) fx = out[i] != 0;
         if (m.flags & MF_RESET_ERR) {
             fx = stat[i] == MS_DONE && out[i] != 0;
             const uint32_t u2 = noise_word(a.st, t, m.nl + 2);

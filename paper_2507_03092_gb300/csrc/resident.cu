@@ -27,10 +27,48 @@ __device__ __forceinline__ void gsync(const GroupCtx &g) {
 
 // smem layout per group (32-bit words): x[n*CW], z[n*CW], r[CW], cnt[64H] (int),
 // acol[CW] (snapshot of the measured column), prow[n] (pivot row Pauli per
-// column), misc[8]
+// column), mflag[n] bytes (per-op class within a measurement layer), misc[8]
 __host__ __device__ __forceinline__ size_t res_words(uint32_t n) {
     const size_t H = (n + 31) / 32, CW = 2 * H;
-    return 2 * (size_t)n * CW + CW + 64 * H + CW + n + 8;
+    return 2 * (size_t)n * CW + CW + 64 * H + CW + n + (n + 3) / 4 + 8;
+}
+
+// Deterministic outcome of measuring Z_a by one warp of the group: sign of the
+// product of the stabilizers selected by the destabilizer half of column a
+// (ordered-product closed form, evaluated column by column).
+__device__ uint32_t res_det_warp(uint32_t n, uint32_t H, uint32_t CW, const uint32_t *X, const uint32_t *Z,
+                                 const uint32_t *r, uint32_t a, int *err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t *K = X + (size_t)a * CW;
+    int acc = 0;
+    uint32_t bad = 0;
+    for (uint32_t j = lane; j < n; j += 32) {
+        const uint32_t *xj = X + (size_t)j * CW + H, *zj = Z + (size_t)j * CW + H;
+        uint32_t carry = 0, px = 0, pz = 0;
+        for (uint32_t w = 0; w < H; w++) {
+            const uint32_t k = K[w];
+            if (!k) continue;
+            const uint32_t kx = xj[w] & k, kz = zj[w] & k;
+            uint32_t pre = kz;
+            pre ^= pre << 1; pre ^= pre << 2; pre ^= pre << 4; pre ^= pre << 8; pre ^= pre << 16;
+            pre <<= 1;
+            acc += __popc(kx & kz) + 2 * ((__popc(kx & pre) + (int)(carry & __popc(kx))) & 1);
+            carry ^= __popc(kz) & 1u;
+            px ^= __popc(kx) & 1u;
+            pz ^= __popc(kz) & 1u;
+        }
+        bad |= px | (pz ^ (j == a ? 1u : 0u));
+    }
+    for (uint32_t w = lane; w < H; w += 32) acc += 2 * __popc(r[H + w] & K[w]);
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        bad |= __shfl_xor_sync(FULL_MASK, bad, o);
+    }
+    if (lane == 0) {
+        if (acc & 1) set_err(err, DERR_ODD_PHASE);
+        if (bad) set_err(err, DERR_BAD_PRODUCT);
+    }
+    return (uint32_t)(acc >> 1) & 1u;
 }
 
 size_t resident_smem_per_tableau(uint32_t n) { return 4 * res_words(n); }
@@ -186,7 +224,7 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
         const uint32_t n = P.n, H = P.H, CW = P.CW;
         uint32_t *X = base, *Z = X + (size_t)n * CW, *r = Z + (size_t)n * CW;
         int *cnt = (int *)(r + CW);
-        uint32_t *acol = (uint32_t *)(cnt + 64 * H), *prow = acol + CW, *misc = prow + n;
+        uint32_t *acol = (uint32_t *)(cnt + 64 * H), *prow = acol + CW, *misc = prow + n + (n + 3) / 4;
         // |0...0>: destabilizer i = X_i (slot i), stabilizer i = Z_i (slot 32H+i)
         for (uint32_t e = g.gtid; e < n * CW; e += G) {
             const uint32_t j = e / CW, w = e - j * CW;
@@ -219,7 +257,43 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
                 }
                 gsync(g);
             } else {
+                // measurement layer: deterministic outcomes do not depend on the
+                // layer's other Z measurements, so they are resolved first, in
+                // parallel from the layer's starting state (one warp per op);
+                // the random ones then run in circuit order.
+                uint8_t *mflag = (uint8_t *)(prow + n);
+                const uint32_t gw = g.gtid >> 5, ngw = G >> 5;
+                for (uint32_t i = gw; i < L.count; i += ngw) {
+                    const MItem m = P.mitems[L.first + i];
+                    uint32_t any = 0;
+                    if (!(m.flags & MF_RESET_ERR))
+                        for (uint32_t w = g.gtid & 31; w < H; w += 32) any |= X[(size_t)m.q * CW + H + w];
+                    any = __any_sync(FULL_MASK, any != 0);
+                    if ((g.gtid & 31) == 0) mflag[i] = (m.flags & MF_RESET_ERR) ? 2 : (any ? 1 : 0);
+                }
+                gsync(g);
+                for (uint32_t i = gw; i < L.count; i += ngw) {
+                    if (mflag[i] != 0) continue;
+                    const MItem m = P.mitems[L.first + i];
+                    const uint32_t o = res_det_warp(n, H, CW, X, Z, r, m.q, err);
+                    if ((g.gtid & 31) == 0) {
+                        if (m.rec != 0xffffffffu && o)
+                            atomicOr(&job.record[(unsigned long long)job.shot * job.rec_stride + (m.rec >> 6)],
+                                     1ull << (m.rec & 63));
+                        if (o && (m.flags & (MF_RESET | MF_RESET_AFTER))) mflag[i] = 3;
+                    }
+                }
+                gsync(g);
+                // X after deterministic resets whose outcome was 1 (commutes with
+                // the layer's other measurements)
                 for (uint32_t i = 0; i < L.count; i++) {
+                    if (mflag[i] != 3) continue;          // group-uniform
+                    const uint32_t q = P.mitems[L.first + i].q;
+                    for (uint32_t w = g.gtid; w < CW; w += G) r[w] ^= Z[(size_t)q * CW + w];
+                }
+                gsync(g);
+                for (uint32_t i = 0; i < L.count; i++) {
+                    if (mflag[i] != 1 && mflag[i] != 2) continue;
                     const MItem m = P.mitems[L.first + i];
                     uint32_t coin;
                     if (m.flags & MF_RESET_ERR) {
@@ -239,11 +313,10 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
                     }
                     coin = coin_bit(job.st, job.shot, m.coin);
                     const uint32_t o = res_measure(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, m.q, coin, err);
-                    if (m.rec != 0xffffffffu) {
-                        if (o && g.gtid == 0)
-                            atomicOr(&job.record[(unsigned long long)job.shot * job.rec_stride + (m.rec >> 6)],
-                                     1ull << (m.rec & 63));
-                    } else if (o) {                     // reset: X_a flips rows with z_a = 1
+                    if (m.rec != 0xffffffffu && o && g.gtid == 0)
+                        atomicOr(&job.record[(unsigned long long)job.shot * job.rec_stride + (m.rec >> 6)],
+                                 1ull << (m.rec & 63));
+                    if (o && (m.flags & (MF_RESET | MF_RESET_AFTER))) {   // X_a flips rows with z_a = 1
                         for (uint32_t w = g.gtid; w < CW; w += G) r[w] ^= Z[(size_t)m.q * CW + w];
                         gsync(g);
                     }
