@@ -393,3 +393,32 @@ def test_serving_trace_is_seeded_poisson():
     shots = np.array([r.shots for r in a])
     assert shots.min() >= 1 and shots.max() <= 256 and abs(shots.mean() - 128.5) < 5
     assert len({r.seed for r in a}) == len(a)            # streams keyed per request
+
+
+def test_composite_t1t2_mixture_equals_kraus_composition():
+    """Sec. 4.2: reset w.p. gamma then Z w.p. q (the RESET_ERROR channel with
+    composite_t1t2_probs) equals dephasing after amplitude damping, for random
+    states and T1 >= T2."""
+    rng = np.random.default_rng(3)
+    Zm = np.diag([1.0, -1.0]).astype(complex)
+    P0 = np.diag([1.0, 0.0]).astype(complex)
+    for _ in range(200):
+        T1 = float(rng.uniform(20, 200))
+        T2 = float(rng.uniform(5, T1))
+        t = float(rng.uniform(0, 3 * T1))
+        a = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+        rho = a @ a.conj().T
+        rho /= np.trace(rho)
+        g = 1 - np.exp(-t / T1)                         # amplitude damping
+        K0 = np.array([[1, 0], [0, np.sqrt(1 - g)]], complex)
+        K1 = np.array([[0, np.sqrt(g)], [0, 0]], complex)
+        ad = K0 @ rho @ K0.conj().T + K1 @ rho @ K1.conj().T
+        pd = (1 - np.exp(-t * (1 / T2 - 1 / (2 * T1)))) / 2   # extra dephasing to reach T2
+        want = (1 - pd) * ad + pd * Zm @ ad @ Zm
+        gamma, q = C.composite_t1t2_probs(T1, T2, t)
+        reset = np.trace(rho) * P0
+        mix = (1 - gamma) * rho + gamma * reset
+        got = (1 - q) * mix + q * Zm @ mix @ Zm
+        assert np.allclose(got, want, atol=1e-12)
+    with pytest.raises(ValueError):
+        C.composite_t1t2_probs(50.0, 60.0, 1.0)
