@@ -1,0 +1,131 @@
+"""Parity at the workloads' full sizes, in the launch configurations the
+benchmark times: bit-exact records (and tableaux where the oracle can follow)
+against the CPU oracle, or properties that hold at any size."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_03092_gb300 import binding as B
+from paper_2507_03092_gb300 import circuit as C
+from paper_2507_03092_gb300 import streams as S
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s = B.Simulator(0)
+    yield s
+    s.close()
+
+
+def test_config1_d3_1024_shots_both_engines(sim):
+    circ = C.surface_code_memory(3, p=1e-3)
+    coins, noise = S.streams_for(circ, 0, range(1024))
+    want, _ = oracle.sample(circ, coins, noise, threads=THREADS)
+    cid = sim.compile(circ)
+    for eng in (B.ENGINE_RESIDENT, B.ENGINE_LAYERED):
+        got = B.records_to_numpy(sim.sample(cid, circ, 1024, coins, noise, engine=eng))
+        sim.sync()
+        assert np.array_equal(got, want), eng
+
+
+def test_config2_random_clifford_n1000_200_layers(sim):
+    circ = C.random_clifford_layers(1000, 200, seed=0)
+    coins, noise = S.streams_for(circ, 0, [0])
+    want, wtab, st = oracle.run(circ, coins[0], noise[0], return_tableau=True)
+    cid = sim.compile(circ)
+    B.stab_tableau_init(sim.ctx, circ.n, 1)
+    rec = sim.record_buffer(1, circ.record_words)
+    B.stab_apply_circuit(sim.ctx, cid, B.make_streams(B.STREAM_BUFFER, coins=sim.to_dev(coins),
+                                                      noise=sim.to_dev(noise)), rec)
+    sim.sync()
+    assert np.array_equal(B.records_to_numpy(rec)[0], want)
+    for g, w in zip(B.stab_get_tableau(sim.ctx, 0, circ.n), wtab):
+        assert np.array_equal(g, w)
+    assert st["n_meas_random"] > 10000          # the workload is dominated by random outcomes
+
+
+def test_config3_d71_noiseless_detectors_all_zero(sim):
+    circ = C.surface_code_memory(71)
+    cid = sim.compile(circ)
+    for seed in (0, 1):
+        rec = B.records_to_numpy(sim.sample(cid, circ, 1, seed=seed, engine=B.ENGINE_LAYERED))
+        sim.sync()
+        bits = oracle.record_bits(rec, circ.n_meas)[0]
+        det = np.array([np.bitwise_xor.reduce(bits[d]) for d in circ.meta["detectors"]])
+        assert not det.any()
+        assert int(np.bitwise_xor.reduce(bits[circ.meta["observable"]])) == 0
+        # round-1 X-ancilla outcomes follow the coins (random), so records differ by seed
+        assert bits.any()
+
+
+def test_config3_d71_noisy_prefix_bit_exact(sim):
+    """The d=71 noisy circuit's first rounds on the layered engine the
+    benchmark times, against the oracle: records and the full tableau."""
+    full = C.surface_code_memory(71, p=1e-3)
+    pre = C.prefix(full, full.meta["round_end"][1])        # reset + 2 syndrome rounds
+    coins, noise = S.streams_for(full, 0, [0])
+    want, wtab, _ = oracle.run(pre, coins[0], noise[0], return_tableau=True)
+    cid = sim.compile(pre)
+    B.stab_tableau_init(sim.ctx, pre.n, 1)
+    rec = sim.record_buffer(1, pre.record_words)
+    B.stab_apply_circuit(sim.ctx, cid, B.make_streams(B.STREAM_BUFFER, coins=sim.to_dev(coins),
+                                                      noise=sim.to_dev(noise)), rec)
+    sim.sync()
+    assert np.array_equal(B.records_to_numpy(rec)[0], want)
+    for g, w in zip(B.stab_get_tableau(sim.ctx, 0, pre.n), wtab):
+        assert np.array_equal(g, w)
+    # and the full noisy circuit: detector flips are sparse (p = 1e-3)
+    cidf = sim.compile(full)
+    recf = B.records_to_numpy(sim.sample(cidf, full, 1, coins, noise, engine=B.ENGINE_LAYERED))
+    sim.sync()
+    bits = oracle.record_bits(recf, full.n_meas)[0]
+    det = np.array([np.bitwise_xor.reduce(bits[d]) for d in full.meta["detectors"]])
+    assert 0 < det.mean() < 0.05
+
+
+def test_config4_4096_mixed_distance_shots_one_launch(sim):
+    T = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
+    dists = S.shot_distances(0, 4096)
+    groups, checks, keep = [], [], []
+    for d in (3, 5, 7, 9, 11):
+        shots = np.flatnonzero(dists == d)
+        circ = C.surface_code_memory(d, t1t2=T)
+        coins, noise = S.streams_for(circ, 100 + d, shots)
+        want, _ = oracle.sample(circ, coins, noise, threads=THREADS)
+        cid = sim.compile(circ)
+        rec = sim.record_buffer(len(shots), circ.record_words)
+        dc, dn = sim.to_dev(coins), sim.to_dev(noise)
+        keep += [dc, dn]
+        g = B.JobGroup()
+        g.circuit_id, g.shots = cid, len(shots)
+        g.streams = B.make_streams(B.STREAM_BUFFER, coins=dc, noise=dn)
+        g.d_record, g.record_words = rec.data_ptr(), circ.record_words
+        groups.append(g)
+        checks.append((rec, want))
+    B.stab_sample_batch(sim.ctx, groups)
+    sim.sync()
+    for rec, want in checks:
+        assert np.array_equal(B.records_to_numpy(rec), want)
+
+
+def test_random_wide_benchmark_matches_oracle(sim):
+    circ = C.random_wide_benchmark(96, 96, seed=1)
+    coins, noise = S.streams_for(circ, 2, [0])
+    want, wtab, _ = oracle.run(circ, coins[0], noise[0], return_tableau=True)
+    cid = sim.compile(circ)
+    B.stab_tableau_init(sim.ctx, circ.n, 1)
+    rec = sim.record_buffer(1, circ.record_words)
+    B.stab_apply_circuit(sim.ctx, cid, B.make_streams(B.STREAM_BUFFER, coins=sim.to_dev(coins),
+                                                      noise=sim.to_dev(noise)), rec)
+    sim.sync()
+    assert np.array_equal(B.records_to_numpy(rec)[0], want)
+    for g, w in zip(B.stab_get_tableau(sim.ctx, 0, circ.n), wtab):
+        assert np.array_equal(g, w)
