@@ -140,6 +140,8 @@ struct Batch {
     uint32_t *rm = nullptr;  size_t rm_stride = 0;
     uint32_t *r = nullptr;
     uint8_t *dirty = nullptr;
+    uint32_t *tflags = nullptr;   // per tableau: bit 0 destabilizer half of RM current,
+                                  // bit 1 the current measurement layer has random ops
     bool rm_valid = false;
     void *mem = nullptr;
     size_t bytes = 0;

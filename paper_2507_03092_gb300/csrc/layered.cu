@@ -42,7 +42,16 @@
 
 namespace stab {
 
-enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2, MS_WAVE = 3 };
+enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2, MS_WAVE = 3, MS_DETLATE = 4 };
+// MS_DETLATE: an op that was random when the layer started but became
+// deterministic after earlier random ops of the layer.  Its outcome does not
+// change under the layer's remaining Z measurements, so k_meas_late resolves
+// all of them after k_meas_rand, one warp each across the whole GPU; until then
+// their measured columns are kept current like those of pending random ops.
+// tflags: the row-packed copy's destabilizer half (rows of slices w < H) is
+// only needed by random measurements; gate runs write the stabilizer half and
+// k_destab_to_rm fills the other half when a layer turns out to have random ops.
+enum : uint32_t { TF_DESTAB_FRESH = 1u, TF_RAND_LAYER = 2u };
 
 struct LArgs {
     DevProg P;
@@ -53,6 +62,7 @@ struct LArgs {
     uint32_t RS, Hr;                 // row stride (words) and z offset in a row
     uint32_t *r;
     uint8_t *dirty;
+    uint32_t *tflags;                // TF_* per tableau
     uint32_t *cols;
     unsigned long long cols_stride;  // words per tableau
     uint8_t *mstat, *mout;
@@ -111,6 +121,7 @@ __global__ void k_init(LArgs a) {
             a.r[(unsigned long long)t * CW + e] = 0u;
             a.dirty[(unsigned long long)t * CW + e] = 0;
         }
+        if (start == 0) a.tflags[t] = TF_DESTAB_FRESH;
     }
 }
 
@@ -229,7 +240,7 @@ __global__ void k_noise_events(LArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(512) k_gate_run(LArgs a, GRun g) {
+__global__ void __launch_bounds__(1024) k_gate_run(LArgs a, GRun g) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t sred[32];
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
@@ -256,20 +267,26 @@ __global__ void __launch_bounds__(512) k_gate_run(LArgs a, GRun g) {
         const Layer L = a.P.layers[l];
         // gates: packed items through the read-only path, next item prefetched
         const uint2 *__restrict__ it = reinterpret_cast<const uint2 *>(a.P.sitems + L.first);
-        uint32_t i = threadIdx.x;
-        uint2 cur = i < L.count ? __ldg(it + i) : make_uint2(0u, 0u);
-        for (; i < L.count; i += blockDim.x) {
-            const uint2 nxt = (i + blockDim.x < L.count) ? __ldg(it + i + blockDim.x) : make_uint2(0u, 0u);
-            const uint32_t ga = cur.x & 0xffffu, gb = cur.x >> 16, gk = cur.y;
-            if (gk) {
-                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
-                const bool two = gb != ga;
-                if (two) { xb = sx[gb]; zb = sz[gb]; }
-                racc ^= apply_gate(gk, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za;
-                if (two) { sx[gb] = xb; sz[gb] = zb; }
+        // items in groups of 4 per thread, all four loaded before any is used
+        for (uint32_t i0 = threadIdx.x; i0 < L.count; i0 += 4 * blockDim.x) {
+            uint2 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t i = i0 + k * blockDim.x;
+                v[k] = i < L.count ? __ldg(it + i) : make_uint2(0u, 0u);
             }
-            cur = nxt;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t ga = v[k].x & 0xffffu, gb = v[k].x >> 16, gk = v[k].y;
+                if (gk) {
+                    uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                    const bool two = gb != ga;
+                    if (two) { xb = sx[gb]; zb = sz[gb]; }
+                    racc ^= apply_gate(gk, xa, za, xb, zb);
+                    sx[ga] = xa; sz[ga] = za;
+                    if (two) { sx[gb] = xb; sz[gb] = zb; }
+                }
+            }
         }
         __syncthreads();
         if (L.n_noisy) {
@@ -316,11 +333,27 @@ __global__ void __launch_bounds__(512) k_gate_run(LArgs a, GRun g) {
             dirty[w] = 0;
         }
     }
-    if (g.want_rm) {
+    if (w == 0 && threadIdx.x == 0) a.tflags[t] &= ~TF_DESTAB_FRESH;
+    if (g.want_rm && w >= H) {        // stabilizer half only (see TF_DESTAB_FRESH)
         slice_store_rm(rm, a.RS, a.Hr, H, w,
                        [&](uint32_t j) { return j < n ? sx[j] : 0u; },
                        [&](uint32_t j) { return j < n ? sz[j] : 0u; });
     }
+}
+
+// Destabilizer half of the row-packed copy, for tableaux whose current
+// measurement layer has random ops and whose copy is stale.  The column-packed
+// copy is current then: it is only left behind by random measurements, which
+// first make the destabilizer half current.
+__global__ void k_destab_to_rm(LArgs a) {
+    const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
+    const uint32_t w = blockIdx.x, t = blockIdx.y;
+    const uint32_t f = a.tflags[t];
+    if (!(f & TF_RAND_LAYER) || (f & TF_DESTAB_FRESH)) return;
+    const uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
+    slice_store_rm(a.rm + t * a.rm_stride, a.RS, a.Hr, H, w,
+                   [&](uint32_t j) { return j < n ? qx[(size_t)w * n + j] : 0u; },
+                   [&](uint32_t j) { return j < n ? qz[(size_t)w * n + j] : 0u; });
 }
 
 // Full column-packed -> row-packed copy (used when a measurement layer comes
@@ -328,6 +361,7 @@ __global__ void __launch_bounds__(512) k_gate_run(LArgs a, GRun g) {
 __global__ void k_qm_to_rm(LArgs a) {
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
     const uint32_t w = blockIdx.x, t = blockIdx.y;
+    if (w == 0 && threadIdx.x == 0) a.tflags[t] |= TF_DESTAB_FRESH;
     const uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
     slice_store_rm(a.rm + t * a.rm_stride, a.RS, a.Hr, H, w,
                    [&](uint32_t j) { return j < n ? qx[(size_t)w * n + j] : 0u; },
@@ -562,6 +596,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
     if (pv != 0xffffffffu) {
         if (lane == 0) {
             stat[i] = MS_RANDOM;
+            atomicOr(&a.tflags[t], TF_RAND_LAYER);
             a.mpiv[ci] = pv;
             a.mbsz[ci] = csize;
             a.mstale[ci] = 0;
@@ -577,6 +612,29 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
             count(a, DC_SUM_K, k);
         }
     }
+    const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
+                                   col, m.q, smem + (size_t)warp * 2 * H, a.err);
+    if (lane == 0) {
+        stat[i] = MS_DONE;
+        out[i] = (uint8_t)o;
+        write_record(a, t, m.rec, (uint32_t)o);
+    }
+}
+
+// Outcomes of the ops that became deterministic during k_meas_rand (one warp
+// each), from the layer's final tableau.
+__global__ void __launch_bounds__(DET_WARPS * 32) k_meas_late(LArgs a, uint32_t layer) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t H = a.P.H, CW = a.P.CW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = blockIdx.y;
+    const Layer M = a.P.layers[layer];
+    const uint32_t i = blockIdx.x * DET_WARPS + warp;
+    if (i >= M.count) return;
+    uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
+    if (stat[i] != MS_DETLATE) return;
+    const MItem m = a.P.mitems[M.first + i];
+    const uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
     const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
                                    col, m.q, smem + (size_t)warp * 2 * H, a.err);
     if (lane == 0) {
@@ -741,6 +799,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
         if (stat[i] == MS_RANDOM) s_any = 1;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        // k_destab_to_rm has made the destabilizer half current if it was not
+        if (a.tflags[t] & TF_RAND_LAYER) a.tflags[t] = TF_DESTAB_FRESH;
+    }
     if (!s_any) return;
     for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = -1;
     for (uint32_t s = threadIdx.x; s < 3 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
@@ -852,18 +914,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }
         __syncthreads();
         PHASE(1);
-        // ---- (3) ops that became deterministic: outcome from the current tableau
-        for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
+        // ---- (3) ops that became deterministic: resolved by k_meas_late
+        for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
             if (piv[k] != NOPIV) continue;
-            const uint32_t i = pend[k];
-            const MItem m = a.P.mitems[M.first + i];
-            const int o = det_outcome_warp(rm, RS, Hr, H, r, cols + (size_t)i * CW, m.q, detz, a.err);
-            if (lane == 0) {
-                out[i] = (uint8_t)o;
-                stat[i] = MS_DONE;
-                write_record(a, t, m.rec, (uint32_t)o);
-                count(a, DC_DET_NOW, 1);
-            }
+            stat[pend[k]] = MS_DETLATE;
+            count(a, DC_DET_NOW, 1);
         }
         if (s_nrand == 0) {          // block-uniform
             __syncthreads();
@@ -983,7 +1038,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     const int b = __ffs(mm) - 1;
                     mm &= mm - 1;
                     const int j = qmap[32 * c + b];
-                    if (j >= 0 && stat[j] == MS_RANDOM) {
+                    if (j >= 0 && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
                         const uint32_t f = atomicAdd(&s_nent, 1u);
                         if (f < jcap) ents[f] = (uint32_t)j | (x << 16) | (((xp >> b) & 1u) << 31);
                     }
@@ -1154,7 +1209,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         } else {
             for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
-                if (stat[j] != MS_RANDOM) continue;
+                if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
                 uint32_t *cj = cols + (size_t)j * CW;
                 for (uint32_t x = 0; x < nsel; x++) {
                     const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
@@ -1185,7 +1240,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         } else {
             // fallback: recompute bits from the untouched pivot rows
             for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
-                if (stat[j] != MS_RANDOM) continue;
+                if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
                 uint32_t *cj = cols + (size_t)j * CW;
                 const uint32_t qb = a.P.mitems[M.first + j].q;
                 if (lane == 0) mstale[j] = 1;
@@ -1276,7 +1331,7 @@ int layered_supported(uint32_t n, const LaunchCfg &lc) {
 
 size_t batch_bytes(uint32_t n, uint32_t count) {
     const size_t H = (n + 31) / 32, CW = 2 * H, Hr = round4((uint32_t)H), RS = 2 * Hr;
-    size_t per = 4 * (2 * CW * (size_t)n + 64 * H * RS + CW) + CW;
+    size_t per = 4 * (2 * CW * (size_t)n + 64 * H * RS + CW) + CW + 4;
     return per * count + 1024;
 }
 
@@ -1290,9 +1345,9 @@ int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err) {
     b.qm_stride = 2 * (size_t)b.CW * n;
     b.rm_stride = 64 * (size_t)b.H * RS;
     const size_t qm_b = 4 * b.qm_stride * count, rm_b = 4 * b.rm_stride * count;
-    const size_t r_b = 4 * (size_t)b.CW * count, d_b = (size_t)b.CW * count;
+    const size_t r_b = 4 * (size_t)b.CW * count, d_b = (size_t)b.CW * count, f_b = 4 * (size_t)count;
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    b.bytes = up(qm_b) + up(rm_b) + up(r_b) + up(d_b);
+    b.bytes = up(qm_b) + up(rm_b) + up(r_b) + up(d_b) + up(f_b);
     if (cudaMalloc(&b.mem, b.bytes) != cudaSuccess) {
         cudaGetLastError();
         b.mem = nullptr;
@@ -1303,7 +1358,8 @@ int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err) {
     b.qm = (uint32_t *)p; p += up(qm_b);
     b.rm = (uint32_t *)p; p += up(rm_b);
     b.r = (uint32_t *)p; p += up(r_b);
-    b.dirty = (uint8_t *)p;
+    b.dirty = (uint8_t *)p; p += up(d_b);
+    b.tflags = (uint32_t *)p;
     b.rm_valid = false;
     return STAB_OK;
 }
@@ -1322,7 +1378,7 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
     a.qm = b.qm; a.qm_stride = b.qm_stride;
     a.rm = b.rm; a.rm_stride = b.rm_stride;
     a.Hr = round4(b.H); a.RS = 2 * a.Hr;
-    a.r = b.r; a.dirty = b.dirty;
+    a.r = b.r; a.dirty = b.dirty; a.tflags = b.tflags;
     if (ms && p) {
         a.cols = ms->cols;
         a.cols_stride = (unsigned long long)std::max<uint32_t>(1, p->dev.max_meas) * b.CW;
@@ -1397,6 +1453,8 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                              (int)(lc.smem_optin - 1024));
         cudaFuncSetAttribute(k_meas_det, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(lc.smem_optin - 1024));
+        cudaFuncSetAttribute(k_meas_late, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(lc.smem_optin - 1024));
         cudaFuncSetAttribute(k_meas_rand, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(lc.smem_optin - 1024));
         g_attr_set = true;
@@ -1409,7 +1467,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
         const uint32_t blocks = (uint32_t)std::min<unsigned long long>((work + 255) / 256, 8ull * lc.sm_count * 8);
         launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] { k_noise_events<<<blocks, 256, 0, s>>>(a); });
     }
-    const uint32_t gthreads = std::min<uint32_t>(512, std::max<uint32_t>(64, (p.dev.max_gitems + 31) / 32 * 32));
+    const uint32_t gthreads = std::min<uint32_t>(1024, std::max<uint32_t>(64, (p.dev.max_gitems / 2 + 31) / 32 * 32));
     const size_t gsm = layered_gate_smem(b.n);
     bool cols_ready = false;
     for (size_t k = 0; k < p.runs.size(); k++) {
@@ -1439,8 +1497,13 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
             });
+            launch(kp, STAB_KERNEL_OTHER, s, 0.0,
+                   [&] { k_destab_to_rm<<<dim3(b.H, b.count), 256, 0, s>>>(a); });
             launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
                    [&] { k_meas_rand<<<b.count, RAND_THREADS, rand_smem(b.n, b.H), s>>>(a, l); });
+            launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
+                k_meas_late<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
+            });
             if (L.has_cond)
                 launch(kp, STAB_KERNEL_OTHER, s, 0.0,
                        [&] { k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
