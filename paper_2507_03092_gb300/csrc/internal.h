@@ -159,6 +159,8 @@ struct MeasScratch {
     uint8_t *mstale = nullptr;    // [count][max_meas] cache invalid
     uint16_t *msup = nullptr;     // [count][max_meas][SUPCAP] column support rows (if small)
     uint16_t *pwl = nullptr;      // [count][WCAP_MAX][PWCAP] nonzero words of the wave's pivot rows
+    uint32_t *flips = nullptr;    // [count][2*max_meas] qubit | Pauli<<30 to apply after the layer
+    uint32_t *flip_cnt = nullptr; // [count][n_layers]
     uint32_t *ev = nullptr;       // [count][ev_total] noise events
     uint32_t *ev_cnt = nullptr;   // [count][n_layers] noise-event counts
     size_t cap_words = 0, cap_items = 0;

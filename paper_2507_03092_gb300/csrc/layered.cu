@@ -74,6 +74,7 @@ struct LArgs {
     uint8_t *mstale;                 // [B][max_meas]
     uint16_t *msup;                  // [B][max_meas][SUPCAP]
     uint16_t *pwl;                   // [B][WCAP_MAX][PWCAP]
+    uint32_t *flips, *flip_cnt;      // [B][2*max_meas], [B][n_layers]
     unsigned long long *stats;       // DC_* counters (may be null)
     WaveCaps caps;                   // k_meas_rand list capacities (<= compile-time maxima)
     DevStreams st;
@@ -517,6 +518,19 @@ __device__ __forceinline__ void count(const LArgs &a, int k, unsigned long long 
     if (a.stats && v) atomicAdd(&a.stats[k], v);
 }
 
+// Sign flips to apply once the layer's measurements are done: X after a reset
+// whose outcome is 1 (Pauli 1), Z of a RESET_ERROR (Pauli 3).
+__device__ __forceinline__ void push_flip(const LArgs &a, uint32_t t, uint32_t layer, uint32_t q, uint32_t P) {
+    const uint32_t k = atomicAdd(&a.flip_cnt[(size_t)t * a.P.n_layers + layer], 1u);
+    a.flips[t * 2 * a.m_stride + k] = q | (P << 30);
+}
+
+// Flips implied by an op's outcome (resets with outcome 1).
+__device__ __forceinline__ void outcome_flips(const LArgs &a, uint32_t t, uint32_t layer, const MItem &m,
+                                              uint32_t o) {
+    if (o && (m.flags & (MF_RESET | MF_RESET_AFTER | MF_RESET_ERR))) push_flip(a, t, layer, m.q, 1u);
+}
+
 __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_t rec, uint32_t out) {
     if (rec != 0xffffffffu && out)
         atomicOr(&a.record[(unsigned long long)t * a.rec_stride + (rec >> 6)], 1ull << (rec & 63));
@@ -581,6 +595,10 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
     const MItem m = a.P.mitems[M.first + i];
     uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     if (m.flags & MF_RESET_ERR) {
+        if (lane == 0) {
+            const uint32_t u2 = noise_word(a.st, t, m.nl + 2);
+            if ((unsigned long long)u2 < a.P.thr[m.np].t[1]) push_flip(a, t, layer, m.q, 3u);
+        }
         const uint32_t u0 = noise_word(a.st, t, m.nl);
         if ((unsigned long long)u0 >= a.P.thr[m.np].t[0]) {
             if (lane == 0) { stat[i] = MS_SKIP; out[i] = 0; }
@@ -618,6 +636,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
         stat[i] = MS_DONE;
         out[i] = (uint8_t)o;
         write_record(a, t, m.rec, (uint32_t)o);
+        outcome_flips(a, t, layer, m, (uint32_t)o);
     }
 }
 
@@ -641,6 +660,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_late(LArgs a, uint32_t 
         stat[i] = MS_DONE;
         out[i] = (uint8_t)o;
         write_record(a, t, m.rec, (uint32_t)o);
+        outcome_flips(a, t, layer, m, (uint32_t)o);
     }
 }
 
@@ -1276,6 +1296,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 out[i] = (uint8_t)coin;
                 stat[i] = MS_DONE;
                 write_record(a, t, m.rec, coin);
+                outcome_flips(a, t, layer, m, coin);
             }
         }
         __syncthreads();
@@ -1284,29 +1305,23 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
 #undef PHASE
 }
 
-// X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a).
+// X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a),
+// from the layer's flip list.
 __global__ void k_cond(LArgs a, uint32_t layer) {
     __shared__ uint32_t sred[32];
     const uint32_t n = a.P.n, CW = a.P.CW;
     const uint32_t w = blockIdx.x, t = blockIdx.y;
-    const Layer M = a.P.layers[layer];
+    const uint32_t cnt = a.flip_cnt[(size_t)t * a.P.n_layers + layer];
+    if (cnt == 0) return;
+    const uint32_t *fl = a.flips + t * 2 * a.m_stride;
     const bool dty = a.dirty[(size_t)t * CW + w] != 0;
     const uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
     const uint32_t *rm = a.rm + t * a.rm_stride;
-    const uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     uint32_t v = 0;
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
-        const MItem m = a.P.mitems[M.first + i];
-        if (!m.flags) continue;
-        bool fx = false, fz = false;
-        if (m.flags & (MF_RESET | MF_RESET_AFTER)) fx = out[i] != 0;
-        if (m.flags & MF_RESET_ERR) {
-            fx = stat[i] == MS_DONE && out[i] != 0;
-            const uint32_t u2 = noise_word(a.st, t, m.nl + 2);
-            fz = (unsigned long long)u2 < a.P.thr[m.np].t[1];
-        }
-        if (fx) v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, m.q, true) : qz[(size_t)w * n + m.q];
-        if (fz) v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, m.q, false) : qx[(size_t)w * n + m.q];
+    for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const uint32_t f = fl[e], q = f & 0x3fffffffu, P = f >> 30;
+        if (P == 1u) v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, q, true) : qz[(size_t)w * n + q];
+        else v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, q, false) : qx[(size_t)w * n + q];
     }
     for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(FULL_MASK, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1394,6 +1409,8 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
         a.mstale = ms->mstale;
         a.msup = ms->msup;
         a.pwl = ms->pwl;
+        a.flips = ms->flips;
+        a.flip_cnt = ms->flip_cnt;
     }
     if (st) a.st = *st;
     a.record = record;
@@ -1461,6 +1478,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     }
     LArgs a = make_args(&p, b, &ms, &st, record, rec_stride, d_err);
     a.stats = d_stats;
+    cudaMemsetAsync(ms.flip_cnt, 0, sizeof(uint32_t) * std::max<size_t>(1, p.layers.size()) * b.count, s);
     if (p.dev.ev_total) {
         cudaMemsetAsync(ms.ev_cnt, 0, sizeof(uint32_t) * p.layers.size() * b.count, s);
         const unsigned long long work = (unsigned long long)p.dev.n_gitems * b.count;

@@ -129,3 +129,25 @@ def test_random_wide_benchmark_matches_oracle(sim):
     assert np.array_equal(B.records_to_numpy(rec)[0], want)
     for g, w in zip(B.stab_get_tableau(sim.ctx, 0, circ.n), wtab):
         assert np.array_equal(g, w)
+
+
+def test_config3_d71_noisy_full_record_matches_golden(sim):
+    """All 362 881 outcomes of the full d=71 noisy circuit (shot 0, seed 0)
+    against the oracle's record, stored as a digest by
+    tests/golden/make_golden.py (oracle only)."""
+    import hashlib
+    import json
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "d71_noisy_seed0.json")) as fh:
+        gold = json.load(fh)
+    circ = C.surface_code_memory(71, p=1e-3)
+    coins, noise = S.streams_for(circ, 0, [0])
+    cid = sim.compile(circ)
+    rec = B.records_to_numpy(sim.sample(cid, circ, 1, coins, noise, engine=B.ENGINE_LAYERED))
+    sim.sync()
+    assert rec.shape[1] == gold["record_words"]
+    bits = oracle.record_bits(rec, circ.n_meas)[0]
+    assert int(bits.sum()) == gold["ones"]
+    det = [int(np.bitwise_xor.reduce(bits[d])) for d in circ.meta["detectors"]]
+    assert sum(det) == gold["detectors_fired"]
+    assert hashlib.sha256(np.ascontiguousarray(rec[0], "<u8").tobytes()).hexdigest() == gold["record_sha256"]
