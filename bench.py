@@ -214,6 +214,24 @@ def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
             "tune": {str(k): v for k, v in tunes.items()}}
 
 
+# ------------------------------------------------------------------ ranks
+def shot_indices(rank: int, steps: int, warmup: int) -> list:
+    """Stream shot indices of one rank: every rank simulates its own shots
+    (replicas), so the ranges are disjoint."""
+    return [rank * (steps + warmup) + s for s in range(steps + warmup)]
+
+
+def aggregate(t_local_s: float, ops_per_step: int, steps: int, world: int, dist=None, device=None):
+    """Whole-job throughput: all ranks' ops over the slowest rank's time."""
+    t = t_local_s
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return ops_per_step * steps * world / t, t
+
+
 # ------------------------------------------------------------------ main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -250,7 +268,7 @@ def main():
     circ = C.surface_code_memory(d, p=p)
     ops_per_step = C.gate_measure_ops(circ)
     K, W = args.steps, args.warmup
-    shots_idx = [rank * (K + W) + s for s in range(K + W)]
+    shots_idx = shot_indices(rank, K, W)
     coins, noise = S.streams_for(circ, 0, shots_idx)
 
     sim = B.Simulator(local)
@@ -297,12 +315,7 @@ def main():
     counters = B.stab_engine_counters(sim.ctx, reset=True)
     kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in range(5)}
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_dev], device=sim.device, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = ops_per_step * K * world / t_dev
+    value, t_dev = aggregate(sum(step_ms) / 1e3, ops_per_step, K, world, dist, sim.device)
 
     # parity spot check of the timed shots (first rounds, oracle) is done by the
     # tests; here only the noiseless-free sanity: the record is non-trivial.
