@@ -1049,34 +1049,42 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     }
                 }
             }
-            // remaining pending ops whose qubit has X or Y in row p or row q
-            const uint32_t *rp_ = rm + (size_t)p * RS, *rq_ = rm + (size_t)q * RS;
-            for (uint32_t c = lane; c < H; c += 32) {
-                const uint32_t xp = rp_[c];
-                uint32_t mm = xp | rq_[c];
-                while (mm) {
-                    const int b = __ffs(mm) - 1;
-                    mm &= mm - 1;
-                    const int j = qmap[32 * c + b];
-                    if (j >= 0 && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
-                        const uint32_t f = atomicAdd(&s_nent, 1u);
-                        if (f < jcap) ents[f] = (uint32_t)j | (x << 16) | (((xp >> b) & 1u) << 31);
+            // remaining pending ops whose qubit has X or Y in row p or row q, and
+            // the nonzero words of row p (for the sparse rowsums); each lane
+            // loads 6 words of both rows before using them
+            const uint32_t *__restrict__ rp_ = rm + (size_t)p * RS;
+            const uint32_t *__restrict__ rq_ = rm + (size_t)q * RS;
+            uint32_t nzcnt = 0;
+            for (uint32_t c0 = 0; c0 < H; c0 += 32 * 6) {
+                uint32_t xp[6], zp[6], xq[6];
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const uint32_t c = c0 + 32 * k + lane;
+                    xp[k] = c < H ? rp_[c] : 0u;
+                    zp[k] = c < H ? rp_[Hr + c] : 0u;
+                    xq[k] = c < H ? rq_[c] : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const uint32_t c = c0 + 32 * k + lane;
+                    uint32_t mm = xp[k] | xq[k];
+                    while (mm) {
+                        const int b = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int j = qmap[32 * c + b];
+                        if (j >= 0 && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
+                            const uint32_t f = atomicAdd(&s_nent, 1u);
+                            if (f < jcap) ents[f] = (uint32_t)j | (x << 16) | (((xp[k] >> b) & 1u) << 31);
+                        }
                     }
-                }
-            }
-            // nonzero words of row p (x or z), for the sparse rowsums
-            {
-                uint32_t cnt = 0;
-                for (uint32_t c0 = 0; c0 < H; c0 += 32) {
-                    const uint32_t c = c0 + lane;
-                    const bool nzw = c < H && (rp_[c] | rp_[Hr + c]) != 0u;
+                    const bool nzw = (xp[k] | zp[k]) != 0u;
                     const uint32_t m = __ballot_sync(FULL_MASK, nzw);
-                    const uint32_t pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    const uint32_t pos = nzcnt + __popc(m & ((1u << lane) - 1u));
                     if (nzw && pos < PWCAP) pwl[x * PWCAP + pos] = (uint16_t)c;
-                    cnt += __popc(m);
+                    nzcnt += __popc(m);
                 }
-                if (lane == 0) pwn[x] = (uint16_t)min(cnt, 0xffffu);
             }
+            if (lane == 0) pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
             if (lane == 0) {
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
@@ -1279,13 +1287,26 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             const MItem m = a.P.mitems[M.first + i];
             const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.st, t, m.nl + 1) & 1u)
                                                            : coin_bit(a.st, t, m.coin);
-            uint32_t *rowp = rm + (size_t)p * RS, *rowq = rm + (size_t)q * RS;
-            for (uint32_t c = lane; c < H; c += 32) {
-                const uint32_t xv = rowp[c], zv = rowp[Hr + c];
-                rowq[c] = xv;
-                rowq[Hr + c] = zv;
-                rowp[c] = 0u;
-                rowp[Hr + c] = (c == (m.q >> 5)) ? (1u << (m.q & 31)) : 0u;
+            uint32_t *__restrict__ rowp = rm + (size_t)p * RS;
+            uint32_t *__restrict__ rowq = rm + (size_t)q * RS;
+            for (uint32_t c0 = 0; c0 < H; c0 += 32 * 6) {
+                uint32_t xv[6], zv[6];
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const uint32_t c = c0 + 32 * k + lane;
+                    xv[k] = c < H ? rowp[c] : 0u;
+                    zv[k] = c < H ? rowp[Hr + c] : 0u;
+                }
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    const uint32_t c = c0 + 32 * k + lane;
+                    if (c < H) {
+                        rowq[c] = xv[k];
+                        rowq[Hr + c] = zv[k];
+                        rowp[c] = 0u;
+                        rowp[Hr + c] = (c == (m.q >> 5)) ? (1u << (m.q & 31)) : 0u;
+                    }
+                }
             }
             if (lane == 0) {
                 const uint32_t rp = rbit(r, p);
