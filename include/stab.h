@@ -18,10 +18,14 @@
  *  - Tableau (Sec. 2.3, "The CHP Formalism"): 2n rows, rows 0..n-1
  *    destabilizers, n..2n-1 stabilizers, each x[0..n), z[0..n) and sign r.
  *    Initial state |0...0>: destabilizer i = X_i, stabilizer i = Z_i.
- *  - Coins: the m-th M/R op (circuit order) reads bit m%64 of coin word m/64
+ *  - Coins: the m-th M/R/MPP op (circuit order) reads bit m%64 of coin word m/64
  *    of its shot, and only if its outcome is random (Sec. 2.4: "a random phase
  *    bit ... is chosen").  Outcome 1 means eigenvalue -1.
- *  - Records: bit k of a shot's record is the outcome of the k-th M op.
+ *  - Records: bit k of a shot's record is the outcome of the k-th M or MPP op.
+ *  - MPP (Pauli-product measurement): measures the product P of its factors'
+ *    Pauli matrices; outcome 1 = eigenvalue -1; one coin slot, like M.  A
+ *    random outcome makes (-1)^coin P the new stabilizer (Sec. 2.4's update
+ *    with Z_a replaced by P; commutation of a row with P as in Sec. 3.2).
  *  - Noise: the l-th noise op reads uint32 word l of its shot's noise stream
  *    (RESET_ERROR reads words l, l+1, l+2).  T(p) = floor(p * 2^32).
  *    DEPOLARIZE1(p): error iff u < T, Pauli (u*3)/T = X, Y, Z.
@@ -69,7 +73,10 @@ enum stab_kind {
     STAB_DEP2 = 12,   /* DEPOLARIZE2(p) on (q0, q1): params[arg] = (p, -, -) */
     STAB_PC1 = 13,    /* PAULI_CHANNEL_1: params[arg] = (px, py, pz) */
     STAB_TICK = 14,   /* layer hint, no effect */
-    STAB_RESET_ERR = 15 /* RESET_ERROR: params[arg] = (gamma, q, -) */
+    STAB_RESET_ERR = 15, /* RESET_ERROR: params[arg] = (gamma, q, -) */
+    STAB_MPP = 16,    /* Pauli-product measurement, recorded: q0 = number of factors k (1..64),
+                         followed by k STAB_PAULI ops on distinct qubits */
+    STAB_PAULI = 17   /* factor of the preceding MPP: q0 = qubit, q1 = 1 X, 2 Y, 3 Z */
 };
 
 /* One op: 16 bytes, little-endian, identical to the Python OP_DTYPE. */

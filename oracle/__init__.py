@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 ERRORS = {0: "ok", -1: "bad argument", -2: "out of memory", -4: "stream too short",
-          -10: "odd phase in rowsum", -11: "deterministic product is not +-Z_a"}
+          -10: "odd phase in rowsum", -11: "deterministic product is not +-Z_a (or +-P)"}
 
 
 class OracleError(RuntimeError):
@@ -71,6 +71,8 @@ def lib():
             L.chp_g.argtypes = [ctypes.c_int] * 4
             L.chp_run.restype = ctypes.c_int
             L.chp_run.argtypes = [P, P, sz, P, sz, P, sz, P, sz, P, sz, ctypes.POINTER(Stats)]
+            L.chp_commute.restype = ctypes.c_int
+            L.chp_commute.argtypes = [P, P, P, sz, P]
             L.chp_sample.restype = ctypes.c_int
             L.chp_sample.argtypes = [u32, P, sz, P, sz, u64, P, sz, P, sz, P, sz,
                                      ctypes.c_int, ctypes.POINTER(Stats)]
@@ -131,6 +133,17 @@ class Tableau:
         r = np.zeros(2 * self.n, np.uint8)
         lib().chp_get(self._h, _ptr(x), _ptr(z), _ptr(r))
         return x, z, r
+
+    def commute(self, px, pz) -> np.ndarray:
+        """Anticommutation of m Paulis (px, pz: uint64 [m, W]) with every row:
+        uint64 [m, ceil(2n/64)], bit i = row i anticommutes."""
+        px = np.ascontiguousarray(px, np.uint64).reshape(-1, self.W)
+        pz = np.ascontiguousarray(pz, np.uint64).reshape(-1, self.W)
+        m = px.shape[0]
+        out = np.zeros((m, (2 * self.n + 63) // 64), np.uint64)
+        if m:
+            lib().chp_commute(self._h, _ptr(px), _ptr(pz), m, _ptr(out))
+        return out
 
     def set(self, x, z, r):
         x = np.ascontiguousarray(x, np.uint64)

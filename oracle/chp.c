@@ -33,6 +33,18 @@
  *    scratch <- 0, rowsum(scratch, i+n) for each destabilizer i with
  *    x_{i,a} = 1 in ascending order; the outcome is r_scratch.
  *  - Reset: measure (consuming its coin slot), then X_a if the outcome is 1.
+ *  - Commutation of a Pauli P = (x_P, z_P) with a row S (Sec. 3.2, the
+ *    tableau-wide commutation equation): S anticommutes with P iff
+ *    sum_j (x_P,j z_S,j + z_P,j x_S,j) is odd.  chp_commute evaluates it for
+ *    every row of the tableau, one bit at a time.
+ *  - Pauli-product measurement MPP of P (the measurement rules of Sec. 2.4
+ *    with Z_a replaced by P, the commutation test above deciding which rows
+ *    take part): p = first stabilizer row anticommuting with P.  If it exists
+ *    the outcome is random: rowsum(i, p) for every other row i anticommuting
+ *    with P; row p-n <- row p; row p <- P with sign r_p = the coin.  Otherwise
+ *    scratch <- 0, rowsum(scratch, i+n) for each destabilizer i anticommuting
+ *    with P (ascending i); the product must be +-P and the outcome is
+ *    r_scratch.  Factors are X (x=1), Y (x=z=1), Z (z=1) on distinct qubits.
  *  - Pauli noise (Sec. 2.6, stochastic Pauli channels): a Pauli P on qubit a
  *    flips r on the rows it anticommutes with: X -> z_a, Z -> x_a, Y -> x_a^z_a.
  *    Draw semantics (one uint32 u per noise op): T = floor(p * 2^32);
@@ -51,7 +63,7 @@
 enum {
     K_NOP = 0, K_H = 1, K_S = 2, K_X = 3, K_Y = 4, K_Z = 5, K_CX = 6, K_CZ = 7,
     K_SWAP = 8, K_M = 9, K_R = 10, K_DEP1 = 11, K_DEP2 = 12, K_PC1 = 13,
-    K_TICK = 14, K_RESET_ERR = 15
+    K_TICK = 14, K_RESET_ERR = 15, K_MPP = 16, K_PAULI = 17
 };
 
 enum {
@@ -74,8 +86,8 @@ typedef struct {
 
 typedef struct {
     uint32_t n, W;          /* qubits, 64-bit words per row */
-    uint64_t *x, *z;        /* (2n+1) * W */
-    uint8_t *r;             /* 2n+1 */
+    uint64_t *x, *z;        /* (2n+2) * W: 2n rows, scratch row 2n, Pauli row 2n+1 */
+    uint8_t *r;             /* 2n+2 */
 } chp_t;
 
 static inline int bit(const uint64_t *row, uint32_t j) {
@@ -89,7 +101,7 @@ static inline uint64_t *XR(chp_t *s, uint32_t i) { return s->x + (size_t)i * s->
 static inline uint64_t *ZR(chp_t *s, uint32_t i) { return s->z + (size_t)i * s->W; }
 
 void chp_reset(chp_t *s) {
-    size_t rows = 2 * (size_t)s->n + 1;
+    size_t rows = 2 * (size_t)s->n + 2;
     memset(s->x, 0, rows * s->W * sizeof(uint64_t));
     memset(s->z, 0, rows * s->W * sizeof(uint64_t));
     memset(s->r, 0, rows);
@@ -105,7 +117,7 @@ chp_t *chp_new(uint32_t n) {
     s->n = n;
     s->W = (n + 63) / 64;
     if (s->W == 0) s->W = 1;
-    size_t rows = 2 * (size_t)n + 1;
+    size_t rows = 2 * (size_t)n + 2;
     s->x = (uint64_t *)calloc(rows * s->W, sizeof(uint64_t));
     s->z = (uint64_t *)calloc(rows * s->W, sizeof(uint64_t));
     s->r = (uint8_t *)calloc(rows, 1);
@@ -258,6 +270,74 @@ static int measure(chp_t *s, uint32_t a, int coin, chp_stats *st) {
     return s->r[sc];
 }
 
+/* Sec. 3.2: does row i anticommute with the Pauli held in row pr? */
+static int anticommutes(chp_t *s, uint32_t i, uint32_t pr) {
+    uint64_t *xs = XR(s, i), *zs = ZR(s, i), *xp = XR(s, pr), *zp = ZR(s, pr);
+    int acc = 0;
+    for (uint32_t j = 0; j < s->n; j++)
+        acc += bit(xp, j) * bit(zs, j) + bit(zp, j) * bit(xs, j);
+    return acc & 1;
+}
+
+/* Commutation of m Paulis (px, pz: m x W words, row-major) with every row of
+ * the tableau: bit i of out[k * ((2n+63)/64) + i/64] = 1 iff row i
+ * anticommutes with Pauli k. */
+int chp_commute(chp_t *s, const uint64_t *px, const uint64_t *pz, size_t m, uint64_t *out) {
+    uint32_t n = s->n, pr = 2 * n + 1;
+    size_t ow = (2 * (size_t)n + 63) / 64;
+    memset(out, 0, m * ow * sizeof(uint64_t));
+    for (size_t k = 0; k < m; k++) {
+        memcpy(XR(s, pr), px + k * s->W, s->W * sizeof(uint64_t));
+        memcpy(ZR(s, pr), pz + k * s->W, s->W * sizeof(uint64_t));
+        for (uint32_t i = 0; i < 2 * n; i++)
+            if (anticommutes(s, i, pr)) out[k * ow + i / 64] |= (uint64_t)1 << (i % 64);
+    }
+    return OR_OK;
+}
+
+/* Measurement of the Pauli product held in row 2n+1 (sign +).  Returns the
+ * outcome (0/1) or a negative error. */
+static int measure_pauli(chp_t *s, int coin, chp_stats *st) {
+    uint32_t n = s->n, pr = 2 * n + 1;
+    uint32_t p = 0;
+    int found = 0;
+    for (uint32_t i = n; i < 2 * n; i++)
+        if (anticommutes(s, i, pr)) { p = i; found = 1; break; }
+    if (found) {
+        uint64_t cntA = 0;
+        for (uint32_t i = 0; i < 2 * n; i++) {
+            if (i == p || !anticommutes(s, i, pr)) continue;
+            int m = rowsum(s, i, p);
+            cntA++;
+            if ((m & 1) && i != p - n) return OR_ODD_PHASE;
+        }
+        memcpy(XR(s, p - n), XR(s, p), s->W * sizeof(uint64_t));
+        memcpy(ZR(s, p - n), ZR(s, p), s->W * sizeof(uint64_t));
+        s->r[p - n] = s->r[p];
+        memcpy(XR(s, p), XR(s, pr), s->W * sizeof(uint64_t));
+        memcpy(ZR(s, p), ZR(s, pr), s->W * sizeof(uint64_t));
+        s->r[p] = (uint8_t)(coin & 1);
+        if (st) { st->n_meas_random++; st->sum_A += cntA; }
+        return coin & 1;
+    }
+    uint32_t sc = 2 * n;
+    memset(XR(s, sc), 0, s->W * sizeof(uint64_t));
+    memset(ZR(s, sc), 0, s->W * sizeof(uint64_t));
+    s->r[sc] = 0;
+    uint64_t cntK = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        if (!anticommutes(s, i, pr)) continue;
+        int m = rowsum(s, sc, i + n);
+        cntK++;
+        if (m & 1) return OR_ODD_PHASE;
+    }
+    for (uint32_t j = 0; j < n; j++)
+        if (bit(XR(s, sc), j) != bit(XR(s, pr), j) || bit(ZR(s, sc), j) != bit(ZR(s, pr), j))
+            return OR_BAD_DET;
+    if (st) { st->n_meas_det++; st->sum_K += cntK; }
+    return s->r[sc];
+}
+
 static inline uint64_t thr(double p) {
     if (!(p > 0.0)) return 0;
     if (p >= 1.0) return (uint64_t)1 << 32;
@@ -279,6 +359,31 @@ int chp_run(chp_t *s, const chp_op *ops, size_t n_ops,
         int kind = o->kind;
         int two = (kind == K_CX || kind == K_CZ || kind == K_SWAP || kind == K_DEP2);
         if (kind == K_NOP || kind == K_TICK) continue;
+        if (kind == K_MPP) {
+            /* a = number of factors; the next a ops are its PAULI factors */
+            uint32_t pr = 2 * s->n + 1;
+            if (a == 0 || a > s->n || k + (size_t)a >= n_ops)
+                return OR_BAD_ARG;
+            memset(XR(s, pr), 0, s->W * sizeof(uint64_t));
+            memset(ZR(s, pr), 0, s->W * sizeof(uint64_t));
+            for (uint32_t f = 1; f <= a; f++) {
+                const chp_op *fo = &ops[k + f];
+                uint32_t q = fo->q0, c = fo->q1;
+                if (fo->kind != K_PAULI || q >= s->n || c < 1 || c > 3) return OR_BAD_ARG;
+                if (bit(XR(s, pr), q) || bit(ZR(s, pr), q)) return OR_BAD_ARG;   /* repeated qubit */
+                if (c == 1 || c == 2) setb(XR(s, pr), q, 1);
+                if (c == 2 || c == 3) setb(ZR(s, pr), q, 1);
+            }
+            if ((c_ord >> 6) >= coin_words || (m_ord >> 6) >= record_words) return OR_STREAM_SHORT;
+            int coin = (int)((coins[c_ord >> 6] >> (c_ord & 63)) & 1u);
+            c_ord++;
+            int out = measure_pauli(s, coin, st);
+            if (out < 0) return out;
+            if (out) record[m_ord >> 6] |= (uint64_t)1 << (m_ord & 63);
+            m_ord++;
+            k += a;
+            continue;
+        }
         if (kind > K_RESET_ERR) return OR_BAD_ARG;
         if (a >= s->n || (two && (b >= s->n || b == a))) return OR_BAD_ARG;
         switch (kind) {

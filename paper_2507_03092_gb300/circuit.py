@@ -42,11 +42,13 @@ DEP2 = 12        # two-qubit depolarizing, params (p, 0, 0)
 PC1 = 13         # single-qubit Pauli channel, params (px, py, pz)
 TICK = 14        # layer hint; no effect on the state
 RESET_ERR = 15   # composite relaxation/dephasing error, params (gamma, q, 0)
+MPP = 16         # Pauli-product measurement: q0 = number of factors k, then k PAULI ops
+PAULI = 17       # one factor of the preceding MPP: q0 = qubit, q1 = 1 X, 2 Y, 3 Z
 
 KIND_NAMES = {
     NOP: "NOP", H: "H", S: "S", X: "X", Y: "Y", Z: "Z", CX: "CX", CZ: "CZ",
     SWAP: "SWAP", M: "M", R: "R", DEP1: "DEPOLARIZE1", DEP2: "DEPOLARIZE2",
-    PC1: "PAULI_CHANNEL_1", TICK: "TICK", RESET_ERR: "RESET_ERROR",
+    PC1: "PAULI_CHANNEL_1", TICK: "TICK", RESET_ERR: "RESET_ERROR", MPP: "MPP", PAULI: "PAULI",
 }
 ONE_QUBIT_GATES = (H, S, X, Y, Z)
 TWO_QUBIT_GATES = (CX, CZ, SWAP)
@@ -68,13 +70,14 @@ class Circuit:
     meta: dict = field(default_factory=dict)
 
     @property
-    def n_meas(self) -> int:            # record bits
-        return int(np.count_nonzero(self.ops["kind"] == M))
+    def n_meas(self) -> int:            # record bits (M and MPP)
+        k = self.ops["kind"]
+        return int(np.count_nonzero((k == M) | (k == MPP)))
 
     @property
-    def n_coin(self) -> int:            # coin slots (one per M or R)
+    def n_coin(self) -> int:            # coin slots (one per M, R or MPP)
         k = self.ops["kind"]
-        return int(np.count_nonzero((k == M) | (k == R)))
+        return int(np.count_nonzero((k == M) | (k == R) | (k == MPP)))
 
     @property
     def n_noise(self) -> int:           # noise draws: one uint32 per noise op, three for RESET_ERROR
@@ -146,6 +149,15 @@ class Builder:
 
     def reset_error(self, q, gamma, qz):
         return self.op(RESET_ERR, q, 0, self._param((gamma, qz)))
+
+    def mpp(self, factors):
+        """Measure the Pauli product of ``factors`` [(qubit, 'X'|'Y'|'Z' or 1|2|3), ...]
+        on distinct qubits; recorded like M."""
+        code = {"X": 1, "Y": 2, "Z": 3}
+        self.op(MPP, len(factors))
+        for q, pch in factors:
+            self.op(PAULI, int(q), code.get(pch, pch))
+        return self
 
     def build(self, **meta) -> Circuit:
         ops = np.array(self._ops, dtype=OP_DTYPE) if self._ops else np.zeros(0, OP_DTYPE)
@@ -420,15 +432,22 @@ def random_wide_benchmark(n: int, rounds: int | None = None, seed: int = 0) -> C
 
 
 def random_small_circuit(n: int, n_ops: int, seed: int, noise: bool = True,
-                         allow=(H, S, X, Y, Z, CX, CZ, SWAP, M, R)) -> Circuit:
+                         allow=(H, S, X, Y, Z, CX, CZ, SWAP, M, R), mpp: bool = False) -> Circuit:
     """Uniformly random op soup for differential tests (any op at any time)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     b = Builder(n)
     kinds = list(allow)
     if noise:
         kinds += [DEP1, DEP2, PC1]
+    if mpp:
+        kinds += [MPP] * 4
     for _ in range(n_ops):
         kind = kinds[int(rng.integers(len(kinds)))]
+        if kind == MPP:
+            k = int(rng.integers(1, min(n, 5) + 1))
+            qs = rng.choice(n, size=k, replace=False)
+            b.mpp([(int(q), int(rng.integers(1, 4))) for q in qs])
+            continue
         a = int(rng.integers(n))
         c = a
         if n > 1:
@@ -471,9 +490,10 @@ def prefix(c: Circuit, n_ops: int) -> Circuit:
 
 
 def gate_measure_ops(c: Circuit) -> int:
-    """Clifford gates plus M and R ops (noise channels and TICKs excluded)."""
+    """Clifford gates plus M, R and MPP ops (noise channels, TICKs and MPP
+    factors excluded)."""
     k = c.ops["kind"]
-    return int(np.count_nonzero(np.isin(k, ONE_QUBIT_GATES + TWO_QUBIT_GATES + (M, R))))
+    return int(np.count_nonzero(np.isin(k, ONE_QUBIT_GATES + TWO_QUBIT_GATES + (M, R, MPP))))
 
 
 def concat(circuits: list[Circuit]) -> Circuit:

@@ -82,6 +82,32 @@ class StateVector:
         if code:
             self.apply1(MAT[PAULI_OF_CODE[code]], q)
 
+    def apply_product(self, factors, psi):
+        out = StateVector(self.n)
+        out.psi = psi.copy()
+        for q, code in factors:
+            out.pauli(q, code)
+        return out.psi
+
+    def measure_product(self, factors, coin) -> tuple[int, bool]:
+        """Projective measurement of the Hermitian Pauli product P: outcome 1
+        (eigenvalue -1) has probability (1 - <psi|P|psi>)/2; the post-state
+        is (psi +- P psi) normalised."""
+        Ppsi = self.apply_product(factors, self.psi)
+        ev = float(np.real(np.vdot(self.psi, Ppsi)))
+        p1 = (1 - ev) / 2
+        if abs(p1 - 0.5) < 1e-9:
+            out, rnd = int(coin) & 1, True
+        elif p1 < 1e-9:
+            out, rnd = 0, False
+        elif p1 > 1 - 1e-9:
+            out, rnd = 1, False
+        else:
+            raise AssertionError(f"non-stabilizer probability {p1}")
+        self.psi = self.psi + (1 - 2 * out) * Ppsi
+        self.psi /= np.linalg.norm(self.psi)
+        return out, rnd
+
 
 def threshold(p: float) -> int:
     if not p > 0:
@@ -98,7 +124,11 @@ def run(circ: C.Circuit, coins, noise):
     noise = np.asarray(noise, np.uint32).ravel()
     rec, rnd = [], []
     ci = li = 0
+    skip = 0
     for k, o in enumerate(circ.ops):
+        if skip:
+            skip -= 1
+            continue
         kind, a, b = int(o["kind"]), int(o["q0"]), int(o["q1"])
         pp = circ.params[int(o["arg"])] if kind in C.NOISE_KINDS else None
         if kind in (C.H, C.S, C.X, C.Y, C.Z):
@@ -118,6 +148,14 @@ def run(circ: C.Circuit, coins, noise):
                 rec.append(out)
             elif out:
                 sv.apply1(MAT["X"], a)
+        elif kind == C.MPP:
+            factors = [(int(f["q0"]), int(f["q1"])) for f in circ.ops[k + 1:k + 1 + a]]
+            skip = a
+            coin = (int(coins[ci >> 6]) >> (ci & 63)) & 1
+            ci += 1
+            out, r = sv.measure_product(factors, coin)
+            rnd.append((k, r))
+            rec.append(out)
         elif kind == C.DEP1:
             u, T = int(noise[li]), threshold(pp[0])
             li += 1

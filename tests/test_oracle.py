@@ -422,3 +422,142 @@ def test_composite_t1t2_mixture_equals_kraus_composition():
         assert np.allclose(got, want, atol=1e-12)
     with pytest.raises(ValueError):
         C.composite_t1t2_probs(50.0, 60.0, 1.0)
+
+
+# ---------------------------------------------------------------- Pauli products
+
+def _pauli_kron(xbits, zbits):
+    m = np.eye(1, dtype=complex)
+    for xb, zb in zip(xbits, zbits):
+        m = np.kron(pauli_matrix((int(xb), int(zb))), m)     # qubit 0 least significant
+    return m
+
+
+def _bits(words, n):
+    w = np.ascontiguousarray(words, np.uint64)
+    return np.unpackbits(w.view(np.uint8), bitorder="little")[:n]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_commute_matches_matrix_commutation(n):
+    """Sec. 3.2's commutation equation, checked against P S = -S P for the
+    dense 2^n x 2^n matrices of every tableau row and random Paulis."""
+    rng = np.random.default_rng(n)
+    for seed in range(6):
+        circ = C.random_small_circuit(n, 30, seed=seed + 10 * n, noise=False)
+        coins, noise = _streams(circ, seed)
+        t = oracle.Tableau(n)
+        t.run(circ, coins, noise)
+        x, z, _ = t.get()
+        px = rng.integers(0, 2 ** n, size=(8, 1), dtype=np.uint64)
+        pz = rng.integers(0, 2 ** n, size=(8, 1), dtype=np.uint64)
+        got = t.commute(px, pz)
+        for k in range(8):
+            P = _pauli_kron(_bits(px[k], n), _bits(pz[k], n))
+            for i in range(2 * n):
+                Srow = _pauli_kron(_bits(x[i], n), _bits(z[i], n))
+                anti = not np.allclose(P @ Srow, Srow @ P)
+                assert anti == bool((int(got[k, i // 64]) >> (i % 64)) & 1), (seed, k, i)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_mpp_matches_statevector(n):
+    """Pauli-product measurements interleaved with gates, M, R and noise:
+    records equal the statevector's projective measurement of P."""
+    for seed in range(25 if n <= 3 else 10):
+        circ = C.random_small_circuit(n, 40, seed=seed + 500 * n, mpp=True)
+        assert int(np.count_nonzero(circ.ops["kind"] == C.MPP)) > 0
+        for cs in (seed, seed + 1000):
+            coins, noise = _streams(circ, cs)
+            bits = oracle.record_bits(oracle.run(circ, coins, noise), circ.n_meas).tolist()
+            sv_bits, _ = SV.run(circ, coins, noise)
+            assert bits == sv_bits, (n, seed, cs)
+
+
+def test_mpp_of_single_z_is_m():
+    """MPP of one Z factor is the Z measurement: same records and the same
+    tableau, row for row."""
+    for seed in range(5):
+        circ = C.random_small_circuit(6, 60, seed=seed)
+        b = C.Builder(6)
+        for o in circ.ops:
+            if int(o["kind"]) == C.M:
+                b.mpp([(int(o["q0"]), "Z")])
+            else:
+                b.op(int(o["kind"]), int(o["q0"]), int(o["q1"]), int(o["arg"]))
+        alt = b.build()
+        alt.params = circ.params
+        coins, noise = _streams(circ, seed)
+        r1, t1, _ = oracle.run(circ, coins, noise, return_tableau=True)
+        r2, t2, _ = oracle.run(alt, coins, noise, return_tableau=True)
+        assert np.array_equal(r1, r2)
+        for a, b_ in zip(t1, t2):
+            assert np.array_equal(a, b_)
+
+
+def test_mpp_ghz_closed_forms():
+    """GHZ_3 = (|000> + |111>)/sqrt2: XXX = +1, XYY = YXY = YYX = -1,
+    Z0 Z1 = Z1 Z2 = +1 -- deterministic whatever the coins."""
+    for coin in (0, 1):
+        b = C.Builder(3)
+        b.gate1(C.H, 0)
+        b.gate2(C.CX, 0, 1)
+        b.gate2(C.CX, 1, 2)
+        for f in ("XXX", "XYY", "YXY", "YYX"):
+            b.mpp([(q, ch) for q, ch in enumerate(f)])
+        b.mpp([(0, "Z"), (1, "Z")])
+        b.mpp([(2, "Z"), (1, "Z")])
+        c = b.build()
+        t = oracle.Tableau(3)
+        bits = oracle.record_bits(t.run(c, np.array([2 ** 64 - 1 if coin else 0], np.uint64)), 6)
+        assert bits.tolist() == [0, 1, 1, 1, 0, 0]
+        assert t.stats.n_meas_random == 0 and t.stats.n_meas_det == 6
+
+
+def test_mpp_random_outcome_installs_signed_product():
+    """A random MPP outcome c leaves (-1)^c P in the stabilizer group:
+    measuring P again is deterministic with the same outcome, and Z-basis
+    products that commute with P keep their values."""
+    b = C.Builder(4)
+    b.mpp([(0, "X"), (1, "Y"), (3, "Z")])
+    b.mpp([(0, "X"), (1, "Y"), (3, "Z")])
+    b.mpp([(2, "Z")])
+    c = b.build()
+    for coin in (0, 1):
+        t = oracle.Tableau(4)
+        bits = oracle.record_bits(t.run(c, np.array([coin], np.uint64)), 3)
+        assert bits.tolist() == [coin, coin, 0]
+        assert t.stats.n_meas_random == 1
+
+
+def test_mpp_rejects_bad_factor_lists():
+    for ops in ([(C.MPP, 2, 0), (C.PAULI, 0, 3)],                     # too few factors
+                [(C.MPP, 2, 0), (C.PAULI, 0, 3), (C.PAULI, 0, 1)],   # repeated qubit
+                [(C.MPP, 1, 0), (C.PAULI, 0, 4)],                    # bad Pauli code
+                [(C.MPP, 1, 0), (C.H, 0, 0)],                        # factor is not PAULI
+                [(C.MPP, 0, 0)]):                                    # no factors
+        b = C.Builder(2)
+        for k, q0, q1 in ops:
+            b.op(k, q0, q1)
+        with pytest.raises(oracle.OracleError):
+            oracle.run(b.build(), np.zeros(1, np.uint64))
+
+
+def test_invariants_after_every_mpp():
+    """The symplectic invariants hold after every Pauli-product measurement
+    (each MPP with its factors run as one unit)."""
+    for seed in range(6):
+        n = 8
+        circ = C.random_small_circuit(n, 60, seed=seed + 77, noise=False, mpp=True)
+        coins, _ = _streams(circ, seed)
+        t = oracle.Tableau(n)
+        ci, k, ops = 0, 0, circ.ops
+        while k < len(ops):
+            kind = int(ops[k]["kind"])
+            w = 1 + (int(ops[k]["q0"]) if kind == C.MPP else 0)
+            c1 = np.array([(int(coins[ci >> 6]) >> (ci & 63)) & 1], np.uint64)
+            t.run(C.Circuit(n, ops[k:k + w], circ.params), c1, np.zeros(1, np.uint32))
+            ci += kind in (C.M, C.R, C.MPP)
+            k += w
+            x, z, _ = t.get()
+            assert _symplectic_ok(x, z, n), (seed, k)
