@@ -160,6 +160,19 @@ int stab_get_tableau(stab_ctx *ctx, uint32_t index, uint64_t *host_x, uint64_t *
 int stab_set_tableau(stab_ctx *ctx, uint32_t index, const uint64_t *host_x,
                      const uint64_t *host_z, const uint8_t *host_r);
 
+/* Commutation of m Pauli strings with every row of resident tableau `index`
+ * (Sec. 3.2: row S anticommutes with P iff x_P . z_S + z_P . x_S is odd).
+ *   d_px, d_pz: device uint64 [m][ceil(n/64)], bit j = the X / Z part of the
+ *               Pauli on qubit j (X: x, Y: x and z, Z: z); bits >= n ignored.
+ *   d_out:      device uint64 [m][2 ceil(n/64)], overwritten: words
+ *               [0, ceil(n/64)) hold bit i = destabilizer i anticommutes, words
+ *               [ceil(n/64), 2 ceil(n/64)) bit i = stabilizer i anticommutes.
+ * Caller owns all buffers.  Asynchronous on the context's stream; m = 0 does
+ * nothing.  Errors: STAB_ERR_ARG (no tableaux, index out of range, NULL
+ * buffers with m > 0). */
+int stab_commute(stab_ctx *ctx, uint32_t index, const uint64_t *d_px, const uint64_t *d_pz,
+                 size_t m, uint64_t *d_out);
+
 /* ---- sample(shots, streams) -> records: every shot from |0...0> ---- */
 
 /* d_record: device [shots][record_words] uint64, overwritten. */
@@ -255,7 +268,8 @@ int stab_serve_stop(stab_ctx *ctx);
 #define STAB_KERNEL_MEAS_RAND 2u /* layered engine: random measurements of a layer */
 #define STAB_KERNEL_OTHER 3u     /* layered engine: init, transposes, column gather, conditional Paulis */
 #define STAB_KERNEL_RESIDENT 4u  /* resident engine persistent launch */
-#define STAB_N_KERNEL_KINDS 5u
+#define STAB_KERNEL_COMMUTE 5u   /* Pauli-vs-tableau commutation (stab_commute) */
+#define STAB_N_KERNEL_KINDS 6u
 
 typedef struct stab_kernel_stats {
     uint64_t launches;    /* launches timed since the last reset */

@@ -77,10 +77,10 @@ class KernelStats(ctypes.Structure):
                 "alg_bytes": float(self.alg_bytes)}
 
 
-KERNEL_GATE_RUN, KERNEL_MEAS_DET, KERNEL_MEAS_RAND, KERNEL_OTHER, KERNEL_RESIDENT = range(5)
+KERNEL_GATE_RUN, KERNEL_MEAS_DET, KERNEL_MEAS_RAND, KERNEL_OTHER, KERNEL_RESIDENT, KERNEL_COMMUTE = range(6)
 KERNEL_NAMES = {KERNEL_GATE_RUN: "k_gate_run", KERNEL_MEAS_DET: "k_meas_det",
                 KERNEL_MEAS_RAND: "k_meas_rand", KERNEL_OTHER: "other",
-                KERNEL_RESIDENT: "k_resident"}
+                KERNEL_RESIDENT: "k_resident", KERNEL_COMMUTE: "k_commute"}
 
 
 class ServeConfig(ctypes.Structure):
@@ -115,6 +115,7 @@ _SIGS = {
     "stab_apply_circuit": (I32, [P, U64, ctypes.POINTER(Streams), P, U64]),
     "stab_get_tableau": (I32, [P, U32, P, P, P]),
     "stab_set_tableau": (I32, [P, U32, P, P, P]),
+    "stab_commute": (I32, [P, U32, P, P, SZ, P]),
     "stab_sample": (I32, [P, U64, U32, ctypes.POINTER(Streams), P, U64, U32]),
     "stab_sample_host": (I32, [P, U64, U32, P, U64, P, U64, P, U64, U32]),
     "stab_sample_batch": (I32, [P, ctypes.POINTER(JobGroup), SZ]),
@@ -249,6 +250,11 @@ def stab_set_tableau(ctx, index, x, z, r):
     _check(lib().stab_set_tableau(ctx, int(index), _np_ptr(x), _np_ptr(z), _np_ptr(r)))
 
 
+def stab_commute(ctx, index, d_px, d_pz, m, d_out):
+    """Device tensors: d_px, d_pz uint64/int64 [m, ceil(n/64)]; d_out [m, 2 ceil(n/64)]."""
+    _check(lib().stab_commute(ctx, int(index), _ptr(d_px), _ptr(d_pz), int(m), _ptr(d_out)))
+
+
 def stab_sample(ctx, cid, shots, streams: Streams, d_record, engine=ENGINE_AUTO):
     _check(lib().stab_sample(ctx, cid, int(shots), ctypes.byref(streams), _ptr(d_record),
                              d_record.shape[-1], int(engine)))
@@ -375,6 +381,9 @@ class Simulator:
 
     def compile(self, circ: C.Circuit) -> int:
         return stab_compile(self.ctx, circ)
+
+    def release(self, cid):
+        stab_release_circuit(self.ctx, cid)
 
     def info(self, cid) -> dict:
         return stab_circuit_info_get(self.ctx, cid)

@@ -325,6 +325,54 @@ def surface_code_memory(d: int, rounds: int | None = None, p: float = 0.0,
     return c
 
 
+def surface_code_mpp(d: int, rounds: int | None = None, p: float = 0.0) -> Circuit:
+    """Rotated surface-code Z-memory measured by Pauli products (the
+    lattice-surgery view of Sec. 2.7): d*d data qubits only, every check
+    measured directly as one MPP of its 2 or 4 corners.
+
+    Reset the data; ``rounds`` rounds of DEPOLARIZE1(p) on every data qubit
+    (``p > 0``) then MPP of every X check and every Z check (plaquette order of
+    ``surface_layout``); then M every data qubit.  Detectors: Z checks in
+    round 1, every check against the previous round, each Z check's final
+    data parity against its last round."""
+    lay = surface_layout(d)
+    rounds = d if rounds is None else rounds
+    nd = d * d
+    b = Builder(nd)
+    for q in range(nd):
+        b.reset(q)
+    b.tick()
+    meas_index, rec = {}, 0
+    for rd in range(rounds):
+        if p > 0:
+            for q in range(nd):
+                b.dep1(q, p)
+        for k, (_pr, _pc, t, _aq, sched) in enumerate(lay.plaquettes):
+            b.mpp([(dq, t) for dq in sched if dq is not None])
+            meas_index[(rd, k)] = rec
+            rec += 1
+        b.tick()
+    data_index = {}
+    for q in range(nd):
+        b.measure(q)
+        data_index[q] = rec
+        rec += 1
+    dets = []
+    for k, pl in enumerate(lay.plaquettes):
+        if pl[2] == "Z":
+            dets.append([meas_index[(0, k)]])
+    for rd in range(1, rounds):
+        for k in range(len(lay.plaquettes)):
+            dets.append([meas_index[(rd, k)], meas_index[(rd - 1, k)]])
+    for k, (_pr, _pc, t, _aq, sched) in enumerate(lay.plaquettes):
+        if t == "Z":
+            dets.append([data_index[dq] for dq in sched if dq is not None] + [meas_index[(rounds - 1, k)]])
+    c = b.build(kind="surface_code_mpp", d=d, rounds=rounds, p=p)
+    c.meta["detectors"] = dets
+    c.meta["observable"] = [data_index[q] for q in range(d)]
+    return c
+
+
 def surface_detectors(lay: SurfaceLayout, rounds: int, meas_index: dict,
                       data_index: dict) -> list:
     """Record-bit sets whose parity is 0 in a noiseless Z-memory run:

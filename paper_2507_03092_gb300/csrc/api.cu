@@ -185,22 +185,30 @@ stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n) {
 
 // One device allocation holds every array of a compiled program, followed by
 // its DevProg descriptor (used by the resident engine's job table).
-static size_t prog_layout(const HostProg &P, size_t off[7]) {
+static constexpr int PROG_ARRAYS = 7;
+static size_t prog_layout(const HostProg &P, size_t off[PROG_ARRAYS + 1]) {
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t sz[6] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
-                          P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
-                          P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t)};
+    const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
+                                    P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
+                                    P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
+                                    P.mfactors.size() * sizeof(uint32_t)};
     size_t o = 0;
-    for (int k = 0; k < 6; k++) {
+    for (int k = 0; k < PROG_ARRAYS; k++) {
         off[k] = o;
         o += up(sz[k] + 1);
     }
-    off[6] = o;
+    off[PROG_ARRAYS] = o;
     return o + up(sizeof(DevProg));
 }
 
+static void free_prog(HostProg &P) {
+    if (P.lay) free_prog(*P.lay);
+    if (P.dmem) cudaFree(P.dmem);
+    P.dmem = nullptr;
+}
+
 static int upload_prog(HostProg &P) {
-    size_t off[7];
+    size_t off[PROG_ARRAYS + 1];
     const size_t total = prog_layout(P, off);
     if (cudaMalloc(&P.dmem, total) != cudaSuccess) {
         cudaGetLastError();
@@ -214,28 +222,32 @@ static int upload_prog(HostProg &P) {
     P.dev.thr = (const Thr *)(b + off[3]);
     P.dev.sitems = (const SItem *)(b + off[4]);
     P.dev.item_layer = (const uint32_t *)(b + off[5]);
-    const void *src[6] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
-                          P.sitems.data(), P.item_layer.data()};
-    const size_t sz[6] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
-                          P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
-                          P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t)};
+    P.dev.mfactors = (const uint32_t *)(b + off[6]);
+    const void *src[PROG_ARRAYS] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
+                                    P.sitems.data(), P.item_layer.data(), P.mfactors.data()};
+    const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
+                                    P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
+                                    P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
+                                    P.mfactors.size() * sizeof(uint32_t)};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 6 && !e; k++)
+    for (int k = 0; k < PROG_ARRAYS && !e; k++)
         if (sz[k]) e = cudaMemcpy(b + off[k], src[k], sz[k], cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(b + off[6], &P.dev, sizeof(DevProg), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(b + off[PROG_ARRAYS], &P.dev, sizeof(DevProg), cudaMemcpyHostToDevice);
     if (e) return cuda_fail(e, "uploading the compiled circuit");
+    if (P.lay) return upload_prog(*P.lay);
     return STAB_OK;
 }
 
 const DevProg *prog_desc(const HostProg &P) {
-    size_t off[7];
+    size_t off[PROG_ARRAYS + 1];
     prog_layout(P, off);
-    return (const DevProg *)((char *)P.dmem + off[6]);
+    return (const DevProg *)((char *)P.dmem + off[PROG_ARRAYS]);
 }
 
-int run_layered_shots(stab_ctx *ctx, const HostProg &p, uint32_t shots, const stab_streams &st,
+int run_layered_shots(stab_ctx *ctx, const HostProg &user_prog, uint32_t shots, const stab_streams &st,
                       uint64_t *d_record, uint64_t record_words, cudaStream_t s, Batch &work,
                       MeasScratch &ms, DevBuf &ms_buf) {
+    const HostProg &p = layered_prog(user_prog);
     if (!layered_supported(p.n, ctx->lc))
         return fail(STAB_ERR_UNSUPPORTED, "n = " + std::to_string(p.n) + " exceeds the layered engine's shared-memory slice");
     // chunk so the batch stays within a fixed device budget
@@ -395,7 +407,7 @@ void stab_destroy(stab_ctx *ctx) {
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
         for (auto &kv : ctx->progs)
-            if (kv.second->dmem) cudaFree(kv.second->dmem);
+            free_prog(*kv.second);
         batch_free(ctx->resident);
         batch_free(ctx->tmp);
         ctx->ms_buf.release();
@@ -465,7 +477,7 @@ int stab_release_circuit(stab_ctx *ctx, uint64_t circuit_id) {
     auto it = ctx->progs.find(circuit_id);
     if (it == ctx->progs.end()) return fail(STAB_ERR_NOT_FOUND, "unknown circuit id");
     cudaStreamSynchronize(ctx->stream);
-    if (it->second->dmem) cudaFree(it->second->dmem);
+    free_prog(*it->second);
     ctx->progs.erase(it);
     return STAB_OK;
 }
@@ -497,11 +509,11 @@ int stab_apply_circuit(stab_ctx *ctx, uint64_t circuit_id, const stab_streams *s
     if (rc) return rc;
     if (!d_record) return fail(STAB_ERR_ARG, "record buffer is NULL");
     if (record_words < p->info.record_words) return fail(STAB_ERR_STREAM_SHORT, "record buffer too short");
-    rc = ensure_ms(ctx->ms, ctx->ms_buf, *p, b.count);
+    rc = ensure_ms(ctx->ms, ctx->ms_buf, layered_prog(*p), b.count);
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(d_record, 0, (size_t)b.count * record_words * 8, ctx->stream);
     if (e) return cuda_fail(e, "clearing records");
-    e = layered_run(*p, b, ctx->ms, to_dev(*streams), (unsigned long long *)d_record, record_words,
+    e = layered_run(layered_prog(*p), b, ctx->ms, to_dev(*streams), (unsigned long long *)d_record, record_words,
                     ctx->d_err, ctx->lc, ctx->stream, &ctx->prof, ctx->d_stats);
     if (e) return cuda_fail(e, "apply_circuit");
     return STAB_OK;
@@ -533,6 +545,20 @@ int stab_get_tableau(stab_ctx *ctx, uint32_t index, uint64_t *hx, uint64_t *hz, 
         }
         hr[row] = (uint8_t)((r[w] >> sh) & 1u);
     }
+    return STAB_OK;
+}
+
+int stab_commute(stab_ctx *ctx, uint32_t index, const uint64_t *d_px, const uint64_t *d_pz, size_t m,
+                 uint64_t *d_out) {
+    CTX_GUARD;
+    Batch &b = ctx->resident;
+    if (!b.count) return fail(STAB_ERR_ARG, "no resident tableaux: call stab_tableau_init first");
+    if (index >= b.count) return fail(STAB_ERR_ARG, "tableau index out of range");
+    if (!m) return STAB_OK;
+    if (!d_px || !d_pz || !d_out) return fail(STAB_ERR_ARG, "Pauli or output buffer is NULL");
+    cudaError_t e = layered_commute(b, index, (const unsigned long long *)d_px, (const unsigned long long *)d_pz, m,
+                                    (unsigned long long *)d_out, ctx->stream, &ctx->prof);
+    if (e) return cuda_fail(e, "commutation kernel");
     return STAB_OK;
 }
 

@@ -26,6 +26,44 @@ static bool is_two(uint8_t k) { return k == STAB_CX || k == STAB_CZ || k == STAB
 static bool is_noise(uint8_t k) { return k == STAB_DEP1 || k == STAB_DEP2 || k == STAB_PC1; }
 static bool is_meas_class(uint8_t k) { return k == STAB_M || k == STAB_R || k == STAB_RESET_ERR; }
 
+// Pauli-product measurement as a Clifford conjugation (the PBC rewriting of
+// Sec. 2.7: a measurement absorbs the Cliffords around it).  U maps the
+// product P of the factors to +Z on the last factor's qubit t:
+//   X factor: H (X -> Z);  Y factor: Z, S, H (Y -> -Y -> X -> Z);  Z: nothing;
+//   then CX(q_i, t) for every other factor q_i (Z_i Z_t -> Z_t).
+// Measuring P equals applying U, measuring Z_t and applying U^dag, since
+// U^dag (I +- Z_t) U / 2 = (I +- P) / 2; U^dag is CX(q_i, t) again, then H
+// for X factors and H, S for Y factors.  Records are identical to the direct
+// rule's: a measurement's outcome depends only on the state and its coin.
+static void expand_mpp(const stab_op *ops, size_t n_ops, std::vector<stab_op> &out) {
+    out.clear();
+    out.reserve(n_ops * 2);
+    auto one = [&](uint8_t kind, uint32_t a, uint32_t b = 0) {
+        stab_op o{};
+        o.kind = kind; o.q0 = a; o.q1 = b;
+        out.push_back(o);
+    };
+    for (size_t k = 0; k < n_ops; k++) {
+        const stab_op &o = ops[k];
+        if (o.kind != STAB_MPP) { out.push_back(o); continue; }
+        const uint32_t nf = o.q0;
+        const stab_op *f = ops + k + 1;
+        const uint32_t t = f[nf - 1].q0;
+        for (uint32_t i = 0; i < nf; i++) {
+            if (f[i].q1 == 1) one(STAB_H, f[i].q0);
+            else if (f[i].q1 == 2) { one(STAB_Z, f[i].q0); one(STAB_S, f[i].q0); one(STAB_H, f[i].q0); }
+        }
+        for (uint32_t i = 0; i + 1 < nf; i++) one(STAB_CX, f[i].q0, t);
+        one(STAB_M, t);
+        for (uint32_t i = nf - 1; i-- > 0;) one(STAB_CX, f[i].q0, t);
+        for (uint32_t i = 0; i < nf; i++) {
+            if (f[i].q1 == 1) one(STAB_H, f[i].q0);
+            else if (f[i].q1 == 2) { one(STAB_H, f[i].q0); one(STAB_S, f[i].q0); }
+        }
+        k += nf;
+    }
+}
+
 int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
                     size_t n_params, HostProg &P, std::string *err) {
     if (n == 0) { *err = "n must be positive"; return STAB_ERR_ARG; }
@@ -46,10 +84,37 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         }
     }
     // ---- validate ----
+    bool has_mpp = false;
     for (size_t k = 0; k < n_ops; k++) {
         const stab_op &o = ops[k];
-        if (o.kind > STAB_RESET_ERR) { *err = "op " + std::to_string(k) + ": unknown kind"; return STAB_ERR_ARG; }
+        if (o.kind > STAB_PAULI) { *err = "op " + std::to_string(k) + ": unknown kind"; return STAB_ERR_ARG; }
         if (o.kind == STAB_NOP || o.kind == STAB_TICK) continue;
+        if (o.kind == STAB_PAULI) {
+            *err = "op " + std::to_string(k) + ": PAULI outside the factor list of an MPP";
+            return STAB_ERR_ARG;
+        }
+        if (o.kind == STAB_MPP) {
+            const uint32_t nf = o.q0;
+            if (nf < 1 || nf > 64 || nf > n || k + nf >= n_ops) {
+                *err = "op " + std::to_string(k) + ": MPP needs 1..64 (and at most n) factors following it";
+                return STAB_ERR_ARG;
+            }
+            for (uint32_t i = 1; i <= nf; i++) {
+                const stab_op &f = ops[k + i];
+                if (f.kind != STAB_PAULI || f.q0 >= n || f.q1 < 1 || f.q1 > 3) {
+                    *err = "op " + std::to_string(k + i) + ": MPP factor must be PAULI with qubit < n and code 1..3";
+                    return STAB_ERR_ARG;
+                }
+                for (uint32_t i2 = 1; i2 < i; i2++)
+                    if (ops[k + i2].q0 == f.q0) {
+                        *err = "op " + std::to_string(k + i) + ": MPP factors must be on distinct qubits";
+                        return STAB_ERR_ARG;
+                    }
+            }
+            has_mpp = true;
+            k += nf;
+            continue;
+        }
         if (o.q0 >= n) { *err = "op " + std::to_string(k) + ": qubit out of range"; return STAB_ERR_ARG; }
         if (is_two(o.kind) && (o.q1 >= n || o.q1 == o.q0)) {
             *err = "op " + std::to_string(k) + ": two-qubit op needs two distinct qubits < n";
@@ -84,7 +149,7 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         L.has_cond = 0;
         if (cur == LT_MEAS)
             for (uint32_t i = L.first; i < L.first + L.count; i++)
-                if (P.mitems[i].flags) L.has_cond = 1;
+                if (P.mitems[i].flags & (MF_RESET | MF_RESET_ERR | MF_RESET_AFTER)) L.has_cond = 1;
         if (L.count) P.layers.push_back(L);
         for (uint32_t q : touched) owner[q] = -1;
         touched.clear();
@@ -104,6 +169,28 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         uint8_t kind = o.kind;
         if (kind == STAB_NOP || kind == STAB_TICK) continue;
         n_real++;
+        if (kind == STAB_MPP) {
+            const uint32_t nf = o.q0;
+            bool clash = cur != LT_MEAS;
+            for (uint32_t i = 1; i <= nf; i++) clash |= owner[ops[k + i].q0] >= 0;
+            if (clash) open_layer(LT_MEAS);
+            MItem m{};
+            m.q = ops[k + nf].q0;
+            m.coin = (uint32_t)c_ord++;
+            m.rec = (uint32_t)m_ord++;
+            m.flags = MF_MPP;
+            m.nl = (uint32_t)P.mfactors.size();
+            m.np = nf;
+            for (uint32_t i = 1; i <= nf; i++) {
+                const stab_op &f = ops[k + i];
+                P.mfactors.push_back(f.q0 | (f.q1 << 30));
+                touch(f.q0, (int64_t)P.mitems.size());
+                last_m[f.q0] = -1;
+            }
+            P.mitems.push_back(m);
+            k += nf;
+            continue;
+        }
         uint32_t a = o.q0, b = is_two(kind) ? o.q1 : o.q0;
         if (kind == STAB_R && last_m[a] >= 0) {
             // R right after M/R on the same qubit: deterministic, outcome = that
@@ -183,7 +270,7 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         if (L.type == LT_MEAS) {
             L.has_cond = 0;
             for (uint32_t i = L.first; i < L.first + L.count; i++)
-                if (P.mitems[i].flags) L.has_cond = 1;
+                if (P.mitems[i].flags & (MF_RESET | MF_RESET_ERR | MF_RESET_AFTER)) L.has_cond = 1;
         }
     if (m_ord > 0xfffffff0ull || c_ord > 0xfffffff0ull || l_ord > 0xfffffff0ull) {
         *err = "circuit too long (more than 2^32 measurements or noise draws)";
@@ -283,6 +370,14 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
     P.dev.max_gitems = max_g;
     P.dev.n_gitems = (uint32_t)P.gitems.size();
     P.dev.n_mitems = (uint32_t)P.mitems.size();
+    P.dev.n_mfactors = (uint32_t)P.mfactors.size();
+    if (has_mpp) {
+        std::vector<stab_op> ex;
+        expand_mpp(ops, n_ops, ex);
+        P.lay = std::make_unique<HostProg>();
+        int rc = compile_program(n, ex.data(), ex.size(), params, n_params, *P.lay, err);
+        if (rc) return rc;
+    }
     return STAB_OK;
 }
 

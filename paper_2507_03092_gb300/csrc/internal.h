@@ -30,7 +30,9 @@ enum LayerType : uint32_t { LT_GATE = 0, LT_MEAS = 1 };
 // noise target of an item's noise op
 enum : uint8_t { NT_A = 0, NT_B = 1, NT_AB = 2, NT_BA = 3 };
 // measurement item flags
-enum : uint32_t { MF_RESET = 1u, MF_RESET_ERR = 2u, MF_RESET_AFTER = 4u };
+enum : uint32_t { MF_RESET = 1u, MF_RESET_ERR = 2u, MF_RESET_AFTER = 4u, MF_MPP = 8u };
+// MF_MPP: a Pauli-product measurement; its factors are mfactors[nl, nl + np),
+// each packed as qubit | code << 30 (code 1 X, 2 Y, 3 Z).
 // MF_RESET_AFTER: an R that followed this M on the same qubit with no op on the
 // qubit in between was folded in: that R is deterministic with this M's outcome,
 // so it reduces to X after the measurement when the outcome is 1.
@@ -52,8 +54,8 @@ struct MItem {            // 24 bytes
     uint32_t coin;        // coin ordinal (M / R); unused for RESET_ERR
     uint32_t rec;         // record ordinal, 0xffffffff if not recorded
     uint32_t flags;       // MF_*
-    uint32_t nl;          // RESET_ERR: ordinal of its first noise draw
-    uint32_t np;          // RESET_ERR: parameter row
+    uint32_t nl;          // RESET_ERR: ordinal of its first noise draw; MPP: first factor
+    uint32_t np;          // RESET_ERR: parameter row; MPP: number of factors
 };
 static_assert(sizeof(MItem) == 24, "MItem layout");
 
@@ -83,6 +85,8 @@ struct DevProg {          // by-value descriptor handed to kernels
     const uint32_t *item_layer; // layer index of each gate item
     uint32_t record_words, coin_words, noise_words, max_meas;
     uint32_t max_gitems, n_gitems, n_mitems, ev_total;
+    const uint32_t *mfactors;   // MPP factors (MF_MPP items)
+    uint32_t n_mfactors, pad;
 };
 
 struct Run {              // layered engine schedule entry
@@ -102,6 +106,11 @@ struct HostProg {
     std::vector<SItem> sitems;
     std::vector<uint32_t> item_layer;
     std::vector<Run> runs;
+    std::vector<uint32_t> mfactors;
+    // The layered engine runs a Pauli-product measurement as the Clifford
+    // conjugation U^dag M_Z U of one qubit; `lay` is the program compiled
+    // from that rewritten op list (null when the circuit has no MPP).
+    std::unique_ptr<HostProg> lay;
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
     void *dmem = nullptr;       // device copy of the arrays
@@ -112,6 +121,8 @@ struct HostProg {
 // writes a message to *err.
 int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
                     size_t n_params, HostProg &out, std::string *err);
+// The program the layered engine runs (the conjugated form if there is one).
+inline const HostProg &layered_prog(const HostProg &p) { return p.lay ? *p.lay : p; }
 
 // ---------------------------------------------------------------------------
 // Streams
@@ -215,6 +226,8 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
                         unsigned long long *d_stats);
 cudaError_t layered_sync_qm(Batch &b, cudaStream_t s);
+cudaError_t layered_commute(Batch &b, uint32_t index, const unsigned long long *px, const unsigned long long *pz,
+                            size_t m, unsigned long long *out, cudaStream_t s, KernelProf *kp);
 size_t layered_gate_smem(uint32_t n);
 int layered_supported(uint32_t n, const LaunchCfg &lc);
 

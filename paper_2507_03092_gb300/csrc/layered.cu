@@ -1470,6 +1470,80 @@ cudaError_t layered_sync_qm(Batch &b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Commutation of m Paulis with every row of one tableau (Sec. 3.2): row S
+// anticommutes with P iff x_P . z_S + z_P . x_S is odd.  On the column-packed
+// copy this is, for each 32-row slot word w, the XOR over the qubits j of
+// z_j[w] where x_P has bit j and x_j[w] where z_P has bit j.  One warp per
+// (Pauli, CT consecutive slot words); lanes stride over the qubits, so each
+// load instruction reads 32 consecutive words of a [plane][word][qubit] row.
+constexpr uint32_t CT = 4;
+__global__ void __launch_bounds__(256) k_commute(const uint32_t *__restrict__ qx, uint32_t n, uint32_t H,
+                                                 uint32_t CW, const unsigned long long *__restrict__ px,
+                                                 const unsigned long long *__restrict__ pz, uint32_t m,
+                                                 uint32_t *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ntile = (CW + CT - 1) / CT;
+    const uint64_t warp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (warp >= (uint64_t)m * ntile) return;
+    const uint32_t k = (uint32_t)(warp / ntile), w0 = (uint32_t)(warp % ntile) * CT;
+    const uint32_t Wq = (n + 63) / 64;
+    const uint32_t *qz = qx + (size_t)CW * n;
+    const unsigned long long *xk = px + (size_t)k * Wq, *zk = pz + (size_t)k * Wq;
+    uint32_t acc[CT];
+#pragma unroll
+    for (uint32_t t = 0; t < CT; t++) acc[t] = 0;
+    for (uint32_t j = lane; j < n; j += 32) {
+        const uint32_t xb = (uint32_t)(xk[j >> 6] >> (j & 63)) & 1u;
+        const uint32_t zb = (uint32_t)(zk[j >> 6] >> (j & 63)) & 1u;
+        if (!(xb | zb)) continue;
+#pragma unroll
+        for (uint32_t t = 0; t < CT; t++) {
+            const uint32_t w = w0 + t;
+            if (w >= CW) break;
+            if (xb) acc[t] ^= qz[(size_t)w * n + j];
+            if (zb) acc[t] ^= qx[(size_t)w * n + j];
+        }
+    }
+#pragma unroll
+    for (uint32_t t = 0; t < CT; t++)
+        for (int o = 16; o; o >>= 1) acc[t] ^= __shfl_xor_sync(FULL_MASK, acc[t], o);
+    if (lane != 0) return;
+    // output: per Pauli [destabilizer half | stabilizer half], 2 Wq uint32 words each
+    uint32_t *o = out + (size_t)k * 4 * Wq;
+    const uint32_t tail = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xffffffffu;
+#pragma unroll
+    for (uint32_t t = 0; t < CT; t++) {
+        const uint32_t w = w0 + t;
+        if (w >= CW) break;
+        const bool stab = w >= H;
+        const uint32_t wh = stab ? w - H : w;
+        uint32_t v = acc[t];
+        if (wh == H - 1) v &= tail;
+        o[(stab ? 2 * Wq : 0) + wh] = v;
+        if (wh == H - 1 && H < 2 * Wq) o[(stab ? 2 * Wq : 0) + H] = 0;   // pad word of an odd H
+    }
+}
+
+cudaError_t layered_commute(Batch &b, uint32_t index, const unsigned long long *px, const unsigned long long *pz,
+                            size_t m, unsigned long long *out, cudaStream_t s, KernelProf *kp) {
+    if (!m) return cudaSuccess;
+    cudaError_t e = layered_sync_qm(b, s);
+    if (e) return e;
+    const uint64_t warps = (uint64_t)m * ((b.CW + CT - 1) / CT);
+    const uint64_t blocks = (warps + 7) / 8;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+    KernelProf::Rec rec;
+    const bool timed = kp && (kp->mask & (1u << STAB_KERNEL_COMMUTE));
+    if (kp) kp->launches++;
+    // bytes per launch: the tableau's column-packed planes once, the Paulis, the output
+    const double bytes = 8.0 * b.CW * b.n + 16.0 * m * ((b.n + 63) / 64) + 16.0 * m * ((b.n + 63) / 64);
+    if (timed) kp->begin(STAB_KERNEL_COMMUTE, s, rec);
+    k_commute<<<(unsigned)blocks, 256, 0, s>>>(b.qm + (size_t)index * b.qm_stride, b.n, b.H, b.CW, px, pz,
+                                               (uint32_t)m, (uint32_t *)out);
+    if (timed) kp->end(rec, s, bytes);
+    return cudaGetLastError();
+}
+
 static bool g_attr_set = false;
 WaveCaps g_caps;
 

@@ -77,6 +77,55 @@ int resident_supported(uint32_t n, const LaunchCfg &lc) {
     return resident_smem_per_tableau(n) + 64 <= lc.smem_optin;
 }
 
+// rowsum(s, p) for every row s set in the snapshot `acol` except the pivot
+// p and its destabilizer partner q (Appendix B, column by column): x/z update
+// and per-row power of i, then the signs.  prow[j] & 3 = the pivot row's
+// Pauli in column j (1 x, 2 z).  Returns the pivot row's sign.
+__device__ uint32_t res_rowsum_rows(const GroupCtx &g, uint32_t n, uint32_t CW, uint32_t *X, uint32_t *Z,
+                                    uint32_t *r, int *cnt, const uint32_t *acol, const uint32_t *prow,
+                                    uint32_t pwd, uint32_t qwd, uint32_t pm, uint32_t qm, int *err) {
+    const uint32_t *colA = acol;
+    for (uint32_t idx = g.gtid; idx < n * CW; idx += g.G) {
+        const uint32_t j = idx / CW, w = idx - j * CW;
+        const uint32_t P = prow[j] & 3u;
+        if (!P) continue;
+        uint32_t M = colA[w];
+        if (w == pwd) M &= ~pm;
+        if (w == qwd) M &= ~qm;
+        if (!M) continue;
+        uint32_t &xw = X[(size_t)j * CW + w], &zw = Z[(size_t)j * CW + w];
+        const uint32_t x = xw, z = zw;
+        uint32_t plus, minus;
+        if (P == 1) { plus = z & x; minus = z & ~x; }          // pivot X: g = z(2x-1)
+        else if (P == 3) { plus = z & ~x; minus = x & ~z; }    // pivot Y: g = z - x
+        else { plus = x & ~z; minus = x & z; }                 // pivot Z: g = x(1-2z)
+        plus &= M; minus &= M;
+        if (P & 1u) xw = x ^ M;
+        if (P & 2u) zw = z ^ M;
+        while (plus) { const int b = __ffs(plus) - 1; plus &= plus - 1; atomicAdd(&cnt[32 * w + b], 1); }
+        while (minus) { const int b = __ffs(minus) - 1; minus &= minus - 1; atomicAdd(&cnt[32 * w + b], -1); }
+    }
+    gsync(g);
+    const uint32_t rp = (r[pwd] & pm) ? 1u : 0u;
+    for (uint32_t w = g.gtid; w < CW; w += g.G) {
+        uint32_t M = colA[w];
+        if (w == pwd) M &= ~pm;
+        if (w == qwd) M &= ~qm;
+        uint32_t flip = 0;
+        while (M) {
+            const int b = __ffs(M) - 1;
+            M &= M - 1;
+            const uint32_t rs = (r[w] >> b) & 1u;
+            const int e = (int)(2 * rs + 2 * rp) + cnt[32 * w + b];
+            if (e & 1) set_err(err, DERR_ODD_PHASE);
+            if ((uint32_t)((e & 3) >> 1) != rs) flip |= 1u << b;
+        }
+        if (flip) r[w] ^= flip;          // each word owned by one thread here
+    }
+    gsync(g);
+    return rp;
+}
+
 // Z measurement of qubit a in the group's shared-memory tableau.
 // Returns the outcome; `coin` is used only if the outcome is random.
 __device__ uint32_t res_measure(const GroupCtx &g, uint32_t n, uint32_t H, uint32_t CW,
@@ -144,47 +193,7 @@ __device__ uint32_t res_measure(const GroupCtx &g, uint32_t n, uint32_t H, uint3
         prow[j] = ((X[(size_t)j * CW + pwd] & pm) ? 1u : 0u) | ((Z[(size_t)j * CW + pwd] & pm) ? 2u : 0u);
     for (uint32_t s = g.gtid; s < 64 * H; s += g.G) cnt[s] = 0;
     gsync(g);
-    // rowsum(s, p) for all s in A = column a minus {p, q}: x/z update and
-    // per-row power of i, column by column (g of Appendix B per bit)
-    const uint32_t *colA = acol;
-    for (uint32_t idx = g.gtid; idx < n * CW; idx += g.G) {
-        const uint32_t j = idx / CW, w = idx - j * CW;
-        const uint32_t P = prow[j];
-        if (!P) continue;
-        uint32_t M = colA[w];
-        if (w == pwd) M &= ~pm;
-        if (w == qwd) M &= ~qm;
-        if (!M) continue;
-        uint32_t &xw = X[(size_t)j * CW + w], &zw = Z[(size_t)j * CW + w];
-        const uint32_t x = xw, z = zw;
-        uint32_t plus, minus;
-        if (P == 1) { plus = z & x; minus = z & ~x; }          // pivot X: g = z(2x-1)
-        else if (P == 3) { plus = z & ~x; minus = x & ~z; }    // pivot Y: g = z - x
-        else { plus = x & ~z; minus = x & z; }                 // pivot Z: g = x(1-2z)
-        plus &= M; minus &= M;
-        if (P & 1u) xw = x ^ M;
-        if (P & 2u) zw = z ^ M;
-        while (plus) { const int b = __ffs(plus) - 1; plus &= plus - 1; atomicAdd(&cnt[32 * w + b], 1); }
-        while (minus) { const int b = __ffs(minus) - 1; minus &= minus - 1; atomicAdd(&cnt[32 * w + b], -1); }
-    }
-    gsync(g);
-    const uint32_t rp = (r[pwd] & pm) ? 1u : 0u;
-    for (uint32_t w = g.gtid; w < CW; w += g.G) {
-        uint32_t M = colA[w];
-        if (w == pwd) M &= ~pm;
-        if (w == qwd) M &= ~qm;
-        uint32_t flip = 0;
-        while (M) {
-            const int b = __ffs(M) - 1;
-            M &= M - 1;
-            const uint32_t rs = (r[w] >> b) & 1u;
-            const int e = (int)(2 * rs + 2 * rp) + cnt[32 * w + b];
-            if (e & 1) set_err(err, DERR_ODD_PHASE);
-            if ((uint32_t)((e & 3) >> 1) != rs) flip |= 1u << b;
-        }
-        if (flip) r[w] ^= flip;          // each word owned by one thread here
-    }
-    gsync(g);
+    const uint32_t rp = res_rowsum_rows(g, n, CW, X, Z, r, cnt, acol, prow, pwd, qwd, pm, qm, err);
     // row q <- row p, row p <- +-Z_a (column by column; bits p and q of a
     // column are handled by one thread)
     for (uint32_t j = g.gtid; j < n; j += g.G) {
@@ -195,6 +204,112 @@ __device__ uint32_t res_measure(const GroupCtx &g, uint32_t n, uint32_t H, uint3
         X[(size_t)j * CW + pwd] &= ~pm;
         if (j == a) Z[(size_t)j * CW + pwd] |= pm;
         else Z[(size_t)j * CW + pwd] &= ~pm;
+    }
+    if (g.gtid == 0) {
+        r[qwd] = rp ? (r[qwd] | qm) : (r[qwd] & ~qm);
+        r[pwd] = coin ? (r[pwd] | pm) : (r[pwd] & ~pm);
+    }
+    gsync(g);
+    return coin;
+}
+
+// Measurement of the Pauli product P of `nf` packed factors (qubit | code << 30,
+// code 1 X, 2 Y, 3 Z) in the group's tableau.  A row anticommutes with P iff
+// x_P . z_S + z_P . x_S is odd (Sec. 3.2), so the column of anticommuting rows
+// is the XOR of the factor columns (z for X/Y factors, x for Y/Z factors);
+// the rest is the Z measurement with that column in place of x_a, and P in
+// place of Z_a as the new stabilizer row.  Returns the outcome.
+__device__ uint32_t res_measure_mpp(const GroupCtx &g, uint32_t n, uint32_t H, uint32_t CW,
+                                    uint32_t *X, uint32_t *Z, uint32_t *r, int *cnt, uint32_t *acol,
+                                    uint32_t *prow, uint32_t *misc, const uint32_t *fac, uint32_t nf,
+                                    uint32_t coin, int *err) {
+    // P per column in prow bits 2..3 (4 = x, 8 = z)
+    for (uint32_t j = g.gtid; j < n; j += g.G) prow[j] = 0;
+    gsync(g);
+    for (uint32_t i = g.gtid; i < nf; i += g.G) {
+        const uint32_t f = fac[i], c = f >> 30;
+        prow[f & 0x3fffffffu] = (c <= 2 ? 4u : 0u) | (c >= 2 ? 8u : 0u);
+    }
+    for (uint32_t w = g.gtid; w < CW; w += g.G) {
+        uint32_t v = 0;
+        for (uint32_t i = 0; i < nf; i++) {
+            const uint32_t f = fac[i], c = f >> 30, q = f & 0x3fffffffu;
+            if (c <= 2) v ^= Z[(size_t)q * CW + w];
+            if (c >= 2) v ^= X[(size_t)q * CW + w];
+        }
+        acol[w] = v;
+    }
+    if (g.gtid == 0) misc[0] = 0x7fffffffu;
+    gsync(g);
+    for (uint32_t w = g.gtid; w < H; w += g.G)
+        if (acol[H + w]) atomicMin(&misc[0], w);
+    gsync(g);
+    const uint32_t pw = misc[0];
+    if (pw == 0x7fffffffu) {
+        // deterministic: P = +-(product of the stabilizers whose destabilizers
+        // anticommute with P); sign by the ordered-product closed form, whose
+        // last term removes the i per Y of the product
+        if (g.gtid == 0) { misc[1] = 0; misc[2] = 0; }
+        gsync(g);
+        int acc = 0;
+        uint32_t bad = 0;
+        const uint32_t *K = acol;
+        for (uint32_t j = g.gtid; j < n; j += g.G) {
+            const uint32_t *xj = X + (size_t)j * CW + H, *zj = Z + (size_t)j * CW + H;
+            uint32_t carry = 0, px = 0, pz = 0;
+            for (uint32_t w = 0; w < H; w++) {
+                const uint32_t k = K[w];
+                if (!k) continue;
+                const uint32_t kx = xj[w] & k, kz = zj[w] & k;
+                uint32_t pre = kz;
+                pre ^= pre << 1; pre ^= pre << 2; pre ^= pre << 4; pre ^= pre << 8; pre ^= pre << 16;
+                pre <<= 1;
+                acc += __popc(kx & kz) + 2 * ((__popc(kx & pre) + (int)(carry & __popc(kx))) & 1);
+                carry ^= __popc(kz) & 1u;
+                px ^= __popc(kx) & 1u;
+                pz ^= __popc(kz) & 1u;
+            }
+            const uint32_t want = prow[j] >> 2;
+            bad |= (px ^ (want & 1u)) | (pz ^ (want >> 1));
+            acc -= (int)(px & pz);
+        }
+        for (uint32_t w = g.gtid; w < H; w += g.G) acc += 2 * __popc(r[H + w] & K[w]);
+        for (int o = 16; o; o >>= 1) {
+            acc += __shfl_xor_sync(FULL_MASK, acc, o);
+            bad |= __shfl_xor_sync(FULL_MASK, bad, o);
+        }
+        if ((g.gtid & 31) == 0) {
+            atomicAdd(&misc[1], (uint32_t)acc);
+            if (bad) misc[2] = 1;
+        }
+        gsync(g);
+        const uint32_t e = misc[1] & 3u;
+        if (g.gtid == 0) {
+            if (e & 1u) set_err(err, DERR_ODD_PHASE);
+            if (misc[2]) set_err(err, DERR_BAD_PRODUCT);
+        }
+        gsync(g);
+        return (e >> 1) & 1u;
+    }
+    // random: pivot p = first stabilizer anticommuting with P
+    const uint32_t pbit = __ffs(acol[H + pw]) - 1;
+    const uint32_t q = 32 * pw + pbit, p = 32 * H + q;
+    const uint32_t pwd = p >> 5, qwd = q >> 5;
+    const uint32_t pm = 1u << (p & 31), qm = 1u << (q & 31);
+    for (uint32_t j = g.gtid; j < n; j += g.G)
+        prow[j] |= ((X[(size_t)j * CW + pwd] & pm) ? 1u : 0u) | ((Z[(size_t)j * CW + pwd] & pm) ? 2u : 0u);
+    for (uint32_t s = g.gtid; s < 64 * H; s += g.G) cnt[s] = 0;
+    gsync(g);
+    const uint32_t rp = res_rowsum_rows(g, n, CW, X, Z, r, cnt, acol, prow, pwd, qwd, pm, qm, err);
+    // row q <- row p, row p <- (-1)^coin P
+    for (uint32_t j = g.gtid; j < n; j += g.G) {
+        const uint32_t Pv = prow[j];
+        uint32_t *xq = X + (size_t)j * CW + qwd, *zq = Z + (size_t)j * CW + qwd;
+        *xq = (Pv & 1u) ? (*xq | qm) : (*xq & ~qm);
+        *zq = (Pv & 2u) ? (*zq | qm) : (*zq & ~qm);
+        uint32_t *xp = X + (size_t)j * CW + pwd, *zp = Z + (size_t)j * CW + pwd;
+        *xp = (Pv & 4u) ? (*xp | pm) : (*xp & ~pm);
+        *zp = (Pv & 8u) ? (*zp | pm) : (*zp & ~pm);
     }
     if (g.gtid == 0) {
         r[qwd] = rp ? (r[qwd] | qm) : (r[qwd] & ~qm);
@@ -266,10 +381,12 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
                 for (uint32_t i = gw; i < L.count; i += ngw) {
                     const MItem m = P.mitems[L.first + i];
                     uint32_t any = 0;
-                    if (!(m.flags & MF_RESET_ERR))
+                    if (!(m.flags & (MF_RESET_ERR | MF_MPP)))
                         for (uint32_t w = g.gtid & 31; w < H; w += 32) any |= X[(size_t)m.q * CW + H + w];
                     any = __any_sync(FULL_MASK, any != 0);
-                    if ((g.gtid & 31) == 0) mflag[i] = (m.flags & MF_RESET_ERR) ? 2 : (any ? 1 : 0);
+                    // Pauli products run in order with the random ones (res_measure_mpp decides)
+                    if ((g.gtid & 31) == 0)
+                        mflag[i] = (m.flags & MF_RESET_ERR) ? 2 : ((any || (m.flags & MF_MPP)) ? 1 : 0);
                 }
                 gsync(g);
                 for (uint32_t i = gw; i < L.count; i += ngw) {
@@ -312,7 +429,9 @@ __global__ void k_resident(const ResJob *__restrict__ jobs, uint32_t n_jobs, uns
                         continue;
                     }
                     coin = coin_bit(job.st, job.shot, m.coin);
-                    const uint32_t o = res_measure(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, m.q, coin, err);
+                    const uint32_t o = (m.flags & MF_MPP)
+                        ? res_measure_mpp(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, P.mfactors + m.nl, m.np, coin, err)
+                        : res_measure(g, n, H, CW, X, Z, r, cnt, acol, prow, misc, m.q, coin, err);
                     if (m.rec != 0xffffffffu && o && g.gtid == 0)
                         atomicOr(&job.record[(unsigned long long)job.shot * job.rec_stride + (m.rec >> 6)],
                                  1ull << (m.rec & 63));

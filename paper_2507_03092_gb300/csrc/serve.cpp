@@ -87,7 +87,7 @@ static void CUDART_CB on_done(void *arg) {
 
 static size_t request_footprint(const HostProg &p, uint32_t shots, bool resident) {
     if (resident) return (size_t)shots * (sizeof(ResJob) + resident_smem_per_tableau(p.n));
-    const size_t mm = std::max<uint32_t>(1, p.dev.max_meas);
+    const size_t mm = std::max<uint32_t>(1, layered_prog(p).dev.max_meas);
     return batch_bytes(p.n, shots) + (size_t)shots * mm * (4 * p.CW + 2);
 }
 
