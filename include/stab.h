@@ -292,7 +292,7 @@ int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
  * [3] deterministic measurements resolved by the batched kernel,
  * [4] sum over deterministic measurements of |K| (stabilizer rows multiplied),
  * [5] sum over random measurements of |A| (rows that received a rowsum),
- * [6] cached pivots recomputed, [7] reserved, [8..18] SM clock cycles spent by
+ * [6] cached pivots recomputed, [7] rowsum passes (one per wave), [8..18] SM clock cycles spent by
  * the random-measurement kernel in its eleven per-wave phases (pending list,
  * pivots, newly deterministic ops, window, marking, selection, work lists,
  * rowsums, column updates, row copies, other).  n <= 24 entries are written. */

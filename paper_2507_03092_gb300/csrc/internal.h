@@ -249,7 +249,7 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
 
 // device counters (unsigned long long) kept next to the error flag
 enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
-             DC_PIV_RECOMP = 6, DC_PHASE0 = 8, DC_N_PHASES = 11, DC_N = 24 };
+             DC_PIV_RECOMP = 6, DC_ROWSUM_PASSES = 7, DC_PHASE0 = 8, DC_N_PHASES = 11, DC_N = 24 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_wt[32];
     __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any;
-    __shared__ uint32_t s_tw, s_tt, s_more;
+    __shared__ uint32_t s_tt;
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint8_t *dirty = a.dirty + (size_t)t * CW;
     uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
     uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
-    uint32_t *claim = firstp + 64 * H;                                // rowsum claims
+    uint32_t *claim = firstp + 64 * H;                                // first rowsum pair per row
     // qubit -> item map: shared memory when n is small enough, else global
     int *qmap = n <= QMAP_SMEM_MAX ? (int *)(smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW)
                                    : a.qmap + (size_t)t * n;
@@ -842,10 +842,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }                                                                     \
     } while (0)
     bool full_scan = true;          // pending list rebuilt from all items (first wave, or overflow)
-    // Stamps only decrease (marks per wave, claims per claim round), so entries
-    // left from earlier waves never win an atomicMin; when a counter runs out
-    // its arrays are cleared and it restarts.
-    uint32_t wave = 0, cround = 0;
+    // Stamps only decrease (marks per wave), so entries left from earlier
+    // waves never win an atomicMin; when the counter runs out the arrays are
+    // cleared and it restarts.
+    uint32_t wave = 0;
     // every wave resolves at least one op (the first pending random op always
     // qualifies), so 2*count+2 waves bound the loop; exceeding it is a bug
     for (uint32_t guard = 0;; guard++) {
@@ -1100,99 +1100,106 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             count(a, DC_SUM_A, npair);
         }
         // ---- (8) rowsums of the wave.  A row in the columns of several wave
-        // ops is multiplied by their (commuting) pivots one at a time: each
-        // round every pending pair claims its row and the winners go.
+        // ops receives the product of their pivots; the pivots are commuting
+        // stabilizers, so that product -- and the row's final sign -- does not
+        // depend on the order in which they are applied.  The pairs of each
+        // row are linked into a chain; a task is one (pair, nonzero pivot
+        // word): it runs only if no earlier pair of its chain has that word
+        // nonzero, and applies its pivot and every later pivot of the chain to
+        // that word in chain order.  The powers of i add up per row and the
+        // sign is set once from 2 r_s + sum 2 r_p + sum of the powers.  Chains
+        // holding a pivot with more than PWCAP nonzero words go to one warp,
+        // which applies them in the same order with the warp rowsums.
         if (npair <= paircap) {
-            // a row is held by at most nsel wave ops, so nsel rounds suffice.
-            // Within a round the winning pairs have distinct rows; each (pair,
-            // nonzero pivot word) is one thread task, the per-pair power of i
-            // is summed in shared memory and the sign set afterwards.
-            bool done = false;
-            for (uint32_t round = 0; round <= nsel; round++) {
-                if (cround >= 0xfff0u) {
-                    for (uint32_t s = threadIdx.x; s < 64 * H; s += blockDim.x) claim[s] = 0xffffffffu;
-                    cround = 0;
-                    __syncthreads();
-                }
-                const uint32_t cst = (0xfffeu - cround) << 16;
-                cround++;
-                for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x)
-                    if (!(pairs[e] >> 31)) atomicMin(&claim[pairs[e] & 0xffffu], cst | e);
-                if (threadIdx.x == 0) s_more = 0;
-                __syncthreads();
-                // winners of this round and their task counts (contiguous pairs per thread)
-                const uint32_t per = (npair + blockDim.x - 1) / blockDim.x;
-                const uint32_t e0 = threadIdx.x * per, e1 = min(npair, e0 + per);
-                uint32_t nwin = 0, ntask = 0;
-                bool losers = false;
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t pe = pairs[e];
-                    if (pe >> 31) continue;
-                    if (claim[pe & 0xffffu] != (cst | e)) { losers = true; continue; }
-                    const uint32_t x = (pe >> 16) & 0x7fffu;
-                    nwin++;
-                    ntask += pwn[x] <= PWCAP ? pwn[x] : 0u;
-                }
-                if (losers) s_more = 1;
-                uint32_t kw = block_excl_scan(nwin, s_wt, &s_tw);
-                uint32_t kt = block_excl_scan(ntask, s_wt, &s_tt);
-                for (uint32_t e = e0; e < e1; e++) {
-                    const uint32_t pe = pairs[e];
-                    if ((pe >> 31) || claim[pe & 0xffffu] != (cst | e)) continue;
-                    const uint32_t x = (pe >> 16) & 0x7fffu;
-                    wl_e[kw] = (uint16_t)e;
-                    wl_off[kw] = kt;
-                    pacc[kw] = 0;
-                    kw++;
-                    kt += pwn[x] <= PWCAP ? pwn[x] : 0u;
-                }
-                __syncthreads();
-                const uint32_t totw = s_tw, tott = s_tt;
-                // tasks: thread per (winning pair, nonzero pivot word)
-                for (uint32_t tk = threadIdx.x; tk < tott; tk += blockDim.x) {
-                    uint32_t lo = 0, hi = totw;                 // upper bound of tk in wl_off
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (wl_off[mid] <= tk) lo = mid + 1; else hi = mid;
-                    }
-                    const uint32_t k = lo - 1;                  // wl_off[0] = 0 <= tk, so lo >= 1
-                    const uint32_t pe = pairs[wl_e[k]], row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
-                    const uint32_t c = pwl[x * PWCAP + (tk - wl_off[k])];
-                    const uint32_t p = 32 * H + piv[sel[x]];
-                    const uint32_t xp = rm[(size_t)p * RS + c], zp = rm[(size_t)p * RS + Hr + c];
-                    uint32_t *rs = rm + (size_t)row * RS;
-                    const uint32_t xs = rs[c], zs = rs[Hr + c];
-                    atomicAdd(&pacc[k], phase_word(xp, zp, xs, zs));
-                    rs[c] = xs ^ xp;
-                    rs[Hr + c] = zs ^ zp;
-                }
-                __syncthreads();
-                // signs of the winning sparse pairs; dense-pivot winners by warps
-                for (uint32_t k = threadIdx.x; k < totw; k += blockDim.x) {
-                    const uint32_t e = wl_e[k], pe = pairs[e];
-                    const uint32_t x = (pe >> 16) & 0x7fffu;
-                    if (pwn[x] > PWCAP) continue;
-                    const uint32_t row = pe & 0xffffu, p = 32 * H + piv[sel[x]];
-                    const uint32_t r_s = rbit(r, row), r_p = rbit(r, p);
-                    const int ev = (int)(2 * r_s + 2 * r_p) + pacc[k];
-                    if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
-                    if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
-                    pairs[e] = pe | 0x80000000u;
-                }
-                for (uint32_t k = (uint32_t)warp; k < totw; k += (uint32_t)nw) {
-                    const uint32_t e = wl_e[k], pe = pairs[e];
-                    const uint32_t x = (pe >> 16) & 0x7fffu;
-                    if (pwn[x] <= PWCAP) continue;
-                    rowsum_warp(rm, RS, Hr, H, r, pe & 0xffffu, 32 * H + piv[sel[x]], a.err);
-                    __syncwarp();
-                    if (lane == 0) pairs[e] = pe | 0x80000000u;
-                }
-                __syncthreads();
-                const bool more = s_more != 0;
-                __syncthreads();          // everyone has read the flag before it is reset
-                if (!more) { done = true; break; }
+            uint32_t *head = claim;                    // [64H] first pair of each row, or ~0
+            uint16_t *nxt = wl_e;                      // next pair of the same row, 0xffff ends
+            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
+                const uint32_t old = atomicExch(&head[pairs[e] & 0xffffu], e);
+                nxt[e] = old == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)old;
             }
-            if (!done && threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+            __syncthreads();
+            // chains with a dense pivot are flagged in the head word (bit 31)
+            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
+                const uint32_t row = pairs[e] & 0xffffu;
+                if (head[row] != e) continue;
+                bool dense = false;
+                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) dense |= pwn[(pairs[f] >> 16) & 0x7fffu] > PWCAP;
+                if (dense) head[row] = e | 0x80000000u;
+            }
+            __syncthreads();
+            // task offsets: pairs in contiguous chunks per thread
+            const uint32_t per = (npair + blockDim.x - 1) / blockDim.x;
+            const uint32_t e0 = threadIdx.x * per, e1 = min(npair, e0 + per);
+            uint32_t ntask = 0;
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t pe = pairs[e];
+                pacc[e] = 0;
+                if (head[pe & 0xffffu] >> 31) continue;
+                ntask += pwn[(pe >> 16) & 0x7fffu];
+            }
+            uint32_t kt = block_excl_scan(ntask, s_wt, &s_tt);
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint32_t pe = pairs[e];
+                wl_off[e] = kt;
+                if (!(head[pe & 0xffffu] >> 31)) kt += pwn[(pe >> 16) & 0x7fffu];
+            }
+            __syncthreads();
+            const uint32_t tott = s_tt;
+            for (uint32_t tk = threadIdx.x; tk < tott; tk += blockDim.x) {
+                uint32_t lo = 0, hi = npair;                // upper bound of tk in wl_off
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (wl_off[mid] <= tk) lo = mid + 1; else hi = mid;
+                }
+                const uint32_t e = lo - 1;                  // wl_off[0] = 0 <= tk, so lo >= 1
+                const uint32_t pe = pairs[e], row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
+                const uint32_t c = pwl[x * PWCAP + (tk - wl_off[e])];
+                const uint32_t hd = head[row];
+                bool first_here = true;
+                for (uint32_t f = hd; f != e; f = nxt[f]) {
+                    const uint32_t pf = 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]];
+                    if ((rm[(size_t)pf * RS + c] | rm[(size_t)pf * RS + Hr + c]) != 0u) { first_here = false; break; }
+                }
+                if (!first_here) continue;
+                uint32_t *rs = rm + (size_t)row * RS;
+                uint32_t xs = rs[c], zs = rs[Hr + c];
+                int acc = 0;
+                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
+                    const uint32_t pf = 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]];
+                    const uint32_t xp = rm[(size_t)pf * RS + c], zp = rm[(size_t)pf * RS + Hr + c];
+                    acc += phase_word(xp, zp, xs, zs);
+                    xs ^= xp;
+                    zs ^= zp;
+                }
+                rs[c] = xs;
+                rs[Hr + c] = zs;
+                if (acc) atomicAdd(&pacc[hd], acc);
+            }
+            __syncthreads();
+            // signs of the sparse chains (head thread); dense chains by warps
+            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
+                const uint32_t row = pairs[e] & 0xffffu;
+                if (head[row] != e) continue;
+                const uint32_t r_s = rbit(r, row);
+                int ev = (int)(2 * r_s) + pacc[e];
+                for (uint32_t f = e; f != 0xffffu; f = nxt[f])
+                    ev += (int)(2 * rbit(r, 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]]));
+                if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
+                if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
+            }
+            for (uint32_t e = (uint32_t)warp; e < npair; e += (uint32_t)nw) {
+                const uint32_t row = pairs[e] & 0xffffu;
+                if (head[row] != (e | 0x80000000u)) continue;
+                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
+                    const uint32_t x = (pairs[f] >> 16) & 0x7fffu, p = 32 * H + piv[sel[x]];
+                    if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
+                    else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) head[pairs[e] & 0xffffu] = 0xffffffffu;
+            if (threadIdx.x == 0) count(a, DC_ROWSUM_PASSES, 1);
             PHASE(7);
         } else {
             // list overflow: one warp applies the pivots row by row, in wave order
