@@ -744,10 +744,14 @@ constexpr uint16_t NOPIV = 0xffffu;
 constexpr uint32_t QMAP_SMEM_MAX = 16384;   // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
 
-size_t rand_smem(uint32_t n, uint32_t H) {
-    return (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H +
-           (n <= QMAP_SMEM_MAX ? 4 * (size_t)n : 0) + 2 * WCAP + 10 * (size_t)PAIRCAP + 64;
+// k_meas_rand's dynamic shared memory: lists, qubit map (when n is small
+// enough) and, last, the sign column (CW words, 16-byte aligned).
+__host__ __device__ __forceinline__ size_t rand_r_offset(uint32_t n, uint32_t H) {
+    const size_t bytes = (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H +
+                         (n <= QMAP_SMEM_MAX ? 4 * (size_t)n : 0) + 2 * WCAP + 10 * (size_t)PAIRCAP;
+    return ((bytes + 15) & ~(size_t)15) / 4;           // in words
 }
+size_t rand_smem(uint32_t n, uint32_t H) { return 4 * rand_r_offset(n, H) + 8 * (size_t)H + 64; }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total) {
@@ -786,10 +790,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     const Layer M = a.P.layers[layer];
     const uint32_t pcap = a.caps.pcap, wcap = a.caps.wcap, paircap = a.caps.paircap, jcap = a.caps.jcap;
     const uint32_t budget = a.caps.mark_budget, wmax = max(1u, a.caps.window);
-    uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
+    uint8_t *const gstat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     uint32_t *cols = a.cols + t * a.cols_stride;
     uint32_t *rm = a.rm + t * a.rm_stride;
-    uint32_t *r = a.r + (size_t)t * CW;
+    uint32_t *const gr = a.r + (size_t)t * CW;
     uint8_t *dirty = a.dirty + (size_t)t * CW;
     uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
     uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
@@ -799,7 +803,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                                    : a.qmap + (size_t)t * n;
     uint32_t *detz = a.detz + (size_t)t * 32 * 2 * H + (size_t)warp * 2 * H;
     uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
-    uint8_t *mstale = a.mstale + t * a.m_stride;
+    uint8_t *const gmstale = a.mstale + t * a.m_stride;
     uint16_t *msup = a.msup + t * a.m_stride * SUPCAP;
     uint16_t *pend = (uint16_t *)smem;             // pending item indices, circuit order
     uint16_t *piv = pend + PCAP;                   // their pivot (slot - 32H), NOPIV
@@ -811,19 +815,24 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *pwn = (uint16_t *)(qmask + CW + (n <= QMAP_SMEM_MAX ? n : 0));   // nonzero words per pivot
     uint32_t *wl_off = (uint32_t *)(pwn + WCAP);   // task offsets of the round's winning pairs [PAIRCAP]
     int *pacc = (int *)(wl_off + PAIRCAP);         // their accumulated powers of i [PAIRCAP]
-    uint16_t *wl_e = (uint16_t *)(pacc + PAIRCAP); // their pair indices [PAIRCAP]
+    uint16_t *wl_e = (uint16_t *)(pacc + PAIRCAP); // chain links of the rowsum pairs [PAIRCAP]
     uint16_t *pwl = a.pwl + (size_t)t * WCAP * PWCAP;
+    // The sign column lives in shared memory for the whole kernel (copied
+    // back at the end).
+    uint32_t *r = smem + rand_r_offset(n, H);
+    uint8_t *stat = gstat, *mstale = gmstale;
 
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
-        if (stat[i] == MS_RANDOM) s_any = 1;
+        if (gstat[i] == MS_RANDOM) s_any = 1;
     __syncthreads();
     if (threadIdx.x == 0) {
         // k_destab_to_rm has made the destabilizer half current if it was not
         if (a.tflags[t] & TF_RAND_LAYER) a.tflags[t] = TF_DESTAB_FRESH;
     }
     if (!s_any) return;
+    for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) r[w] = gr[w];
     for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = -1;
     for (uint32_t s = threadIdx.x; s < 3 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
     __syncthreads();
@@ -1294,26 +1303,25 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             const MItem m = a.P.mitems[M.first + i];
             const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.st, t, m.nl + 1) & 1u)
                                                            : coin_bit(a.st, t, m.coin);
-            uint32_t *__restrict__ rowp = rm + (size_t)p * RS;
-            uint32_t *__restrict__ rowq = rm + (size_t)q * RS;
-            for (uint32_t c0 = 0; c0 < H; c0 += 32 * 6) {
-                uint32_t xv[6], zv[6];
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const uint32_t c = c0 + 32 * k + lane;
-                    xv[k] = c < H ? rowp[c] : 0u;
-                    zv[k] = c < H ? rowp[Hr + c] : 0u;
-                }
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const uint32_t c = c0 + 32 * k + lane;
-                    if (c < H) {
-                        rowq[c] = xv[k];
-                        rowq[Hr + c] = zv[k];
-                        rowp[c] = 0u;
-                        rowp[Hr + c] = (c == (m.q >> 5)) ? (1u << (m.q & 31)) : 0u;
-                    }
-                }
+            // row q <- row p, row p <- Z_a: 16-byte words over the Hr-word rows
+            // (the words past H are zero in every row)
+            const uint32_t H4 = Hr >> 2;
+            const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
+            uint4 *__restrict__ dq = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+#pragma unroll 4
+            for (uint32_t c = lane; c < H4; c += 32) {
+                const uint4 xv = src[c], zv = src[H4 + c];
+                dq[c] = xv;
+                dq[H4 + c] = zv;
+            }
+            __syncwarp();
+            uint4 *dp = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
+            const uint32_t za = 1u << (m.q & 31), zsub = (m.q >> 5) & 3u;
+            for (uint32_t c = lane; c < H4; c += 32) {
+                dp[c] = make_uint4(0u, 0u, 0u, 0u);
+                const bool here = c == (m.q >> 7);
+                dp[H4 + c] = make_uint4(here && zsub == 0 ? za : 0u, here && zsub == 1 ? za : 0u,
+                                        here && zsub == 2 ? za : 0u, here && zsub == 3 ? za : 0u);
             }
             if (lane == 0) {
                 const uint32_t rp = rbit(r, p);
@@ -1331,6 +1339,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         PHASE(9);
     }
 #undef PHASE
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
 }
 
 // X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a),
@@ -1580,6 +1590,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     }
     LArgs a = make_args(&p, b, &ms, &st, record, rec_stride, d_err);
     a.stats = d_stats;
+    const size_t rsm = rand_smem(b.n, b.H);
     cudaMemsetAsync(ms.flip_cnt, 0, sizeof(uint32_t) * std::max<size_t>(1, p.layers.size()) * b.count, s);
     if (p.dev.ev_total) {
         cudaMemsetAsync(ms.ev_cnt, 0, sizeof(uint32_t) * p.layers.size() * b.count, s);
@@ -1620,7 +1631,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
             launch(kp, STAB_KERNEL_OTHER, s, 0.0,
                    [&] { k_destab_to_rm<<<dim3(b.H, b.count), 256, 0, s>>>(a); });
             launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
-                   [&] { k_meas_rand<<<b.count, RAND_THREADS, rand_smem(b.n, b.H), s>>>(a, l); });
+                   [&] { k_meas_rand<<<b.count, RAND_THREADS, rsm, s>>>(a, l); });
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_late<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
             });
