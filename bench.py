@@ -33,6 +33,14 @@ from paper_2507_03092_gb300 import circuit as C  # noqa: E402
 from paper_2507_03092_gb300 import streams as S  # noqa: E402
 
 METRIC = "surface-code d=71 gate+measure ops/s"
+
+# DRAM bytes (read + write) per launch from one ncu capture of the d=71 step
+# (summaries and commands under profiles/).  A kernel changed since its
+# capture has no entry here (traffic reported as null).
+NCU_TRAFFIC = {
+    "k_gate_run": {"bytes_per_launch": 83.2e6,
+                   "source": "profiles/k_gate_run_d71.md (steady syndrome-round launch)"},
+}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -313,7 +321,7 @@ def main():
     B.stab_profile(sim.ctx, 0)
     launches = B.stab_launch_count(sim.ctx, reset=True)
     counters = B.stab_engine_counters(sim.ctx, reset=True)
-    kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in range(5)}
+    kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in sorted(B.KERNEL_NAMES)}
     step_ms = [a.elapsed_time(b) for a, b in evs]
     value, t_dev = aggregate(sum(step_ms) / 1e3, ops_per_step, K, world, dist, sim.device)
 
@@ -349,23 +357,38 @@ def main():
     dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
     ds = kstats[dom]
     hbm, src = peaks()
-    roof = None
-    if ds["launches"] and ds["alg_bytes"] > 0:
-        ach = ds["alg_bytes"] / (ds["total_ms"] / 1e3) / 1e9
+    row_bytes = 2 * circ.n / 8.0          # a tableau row (x and z) or column (2n rows), in bytes
+    alg = ds["alg_bytes"]
+    model = "library model" if alg > 0 else None
+    if dom == "k_meas_rand" and counters.get("wave_ops"):
+        # per random measurement: read its column, copy the pivot row into its
+        # destabilizer, write the new stabilizer row (4 row/column transfers);
+        # per rowsum: read the pivot row and the row, write the row (3)
+        alg = (4 * counters["wave_ops"] + 3 * counters["sum_A"]) * row_bytes
+        model = "(4 x random measurements + 3 x rowsums) x 2n/8 bytes"
+    if ds["launches"] and alg > 0:
+        ach = alg / (ds["total_ms"] / 1e3) / 1e9
+        tr = NCU_TRAFFIC.get(dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_source": src, "traffic": None,
-                "alg_bytes_per_launch": ds["alg_bytes"] / ds["launches"],
+                "frac": ach / hbm, "peak_source": src,
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_source": tr["source"] if tr else None,
+                "alg_bytes_per_launch": alg / ds["launches"], "alg_model": model,
                 "avg_launch_us": 1e3 * ds["total_ms"] / ds["launches"]}
     else:
-        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "peak_source": src, "traffic": None,
-                "note": "dominant kernel has no algorithmic-byte model in the library"}
+                "note": "dominant kernel has no algorithmic-byte model"}
     gr = kstats.get("k_gate_run")
     gate_roof = None
     if gr and gr["launches"]:
         ach = gr["alg_bytes"] / (gr["total_ms"] / 1e3) / 1e9
+        tr = NCU_TRAFFIC.get("k_gate_run")
         gate_roof = {"kernel": "k_gate_run", "achieved": ach, "peak": hbm, "frac": ach / hbm,
                      "unit": "GB/s", "launches": gr["launches"],
+                     "alg_bytes_per_launch": gr["alg_bytes"] / gr["launches"],
+                     "traffic": tr["bytes_per_launch"] if tr else None,
+                     "traffic_source": tr["source"] if tr else None,
                      "avg_launch_us": 1e3 * gr["total_ms"] / gr["launches"]}
 
     line = {
