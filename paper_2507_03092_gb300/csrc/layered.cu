@@ -35,7 +35,8 @@
 //    the slice kernels after the layer's gates.
 //  * k_cond: the X of resets whose outcome was 1 (and the Z of RESET_ERROR)
 //    as sign flips r ^= z_a (x_a); these Paulis commute with the layer's other
-//    measurements, so they are applied after it.
+//    measurements, so they are applied after it -- by the next gate run as it
+//    loads each slice when one follows, else by this kernel.
 #include "device_common.cuh"
 
 #include <algorithm>
@@ -185,6 +186,7 @@ __device__ __forceinline__ uint32_t rm_col_word(const uint32_t *rm, uint32_t RS,
 struct GRun {
     uint32_t l0, l1, want_rm;
     int32_t cols_layer;
+    int32_t cond_layer;     // measurement layer whose reset/RESET_ERROR flips act first, or -1
 };
 
 // Combined Pauli (2-bit x|z<<1 form) of an item's noise ops on its two qubits.
@@ -264,6 +266,18 @@ __global__ void __launch_bounds__(1024) k_gate_run(LArgs a, GRun g) {
     }
     __syncthreads();
     uint32_t racc = 0;
+    if (g.cond_layer >= 0) {
+        // X after resets with outcome 1 and RESET_ERROR's Z from the preceding
+        // measurement layer: sign flips on the rows anticommuting with them,
+        // applied before this run's first gate
+        const uint32_t cnt = a.flip_cnt[(size_t)t * a.P.n_layers + (uint32_t)g.cond_layer];
+        const uint32_t *fl = a.flips + t * 2 * a.m_stride;
+        for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const uint32_t f = fl[e], q = f & 0x3fffffffu;
+            racc ^= (f >> 30) == 1u ? sz[q] : sx[q];
+        }
+        __syncthreads();          // every flip has read its pre-gate word
+    }
     for (uint32_t l = g.l0; l < g.l1; l++) {
         const Layer L = a.P.layers[l];
         // gates: packed items through the read-only path, next item prefetched
@@ -1601,11 +1615,14 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     const uint32_t gthreads = std::min<uint32_t>(1024, std::max<uint32_t>(64, (p.dev.max_gitems / 2 + 31) / 32 * 32));
     const size_t gsm = layered_gate_smem(b.n);
     bool cols_ready = false;
+    int32_t cond_pending = -1;      // measurement layer whose flips the next gate run applies
     for (size_t k = 0; k < p.runs.size(); k++) {
         const Run &R = p.runs[k];
         if (R.type == LT_GATE) {
             GRun g{};
             g.l0 = R.l0; g.l1 = R.l1;
+            g.cond_layer = cond_pending;
+            cond_pending = -1;
             const bool next_meas = k + 1 < p.runs.size() && p.runs[k + 1].type == LT_MEAS;
             g.want_rm = next_meas ? 1u : 0u;
             g.cols_layer = next_meas ? (int32_t)p.runs[k + 1].l0 : -1;
@@ -1635,9 +1652,14 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_late<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
             });
-            if (L.has_cond)
-                launch(kp, STAB_KERNEL_OTHER, s, 0.0,
-                       [&] { k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
+            if (L.has_cond) {
+                // a following gate run applies the flips as it loads each slice
+                if (k + 1 < p.runs.size() && p.runs[k + 1].type == LT_GATE)
+                    cond_pending = (int32_t)l;
+                else
+                    launch(kp, STAB_KERNEL_OTHER, s, 0.0,
+                           [&] { k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
+            }
             cols_ready = false;
         }
         cudaError_t e = cudaGetLastError();
