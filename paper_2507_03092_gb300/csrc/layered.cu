@@ -185,7 +185,6 @@ __device__ __forceinline__ uint32_t rm_col_word(const uint32_t *rm, uint32_t RS,
 // ---------------------------------------------------------------- gate runs
 struct GRun {
     uint32_t l0, l1, want_rm;
-    int32_t cols_layer;
     int32_t cond_layer;     // measurement layer whose reset/RESET_ERROR flips act first, or -1
 };
 
@@ -333,12 +332,6 @@ __global__ void __launch_bounds__(1024) k_gate_run(LArgs a, GRun g) {
         qx[(size_t)w * n + j] = sx[j];
         qz[(size_t)w * n + j] = sz[j];
     }
-    if (g.cols_layer >= 0) {
-        const Layer M = a.P.layers[g.cols_layer];
-        uint32_t *cols = a.cols + t * a.cols_stride;
-        for (uint32_t k = threadIdx.x; k < M.count; k += blockDim.x)
-            cols[(size_t)k * CW + w] = sx[a.P.mitems[M.first + k].q];
-    }
     __syncthreads();
     if (warp == 0) {
         uint32_t v = lane < nw ? sred[lane] : 0u;
@@ -400,18 +393,37 @@ __global__ void k_rm_to_qm(LArgs a) {
 }
 
 // ---------------------------------------------------------------- measurement
-__global__ void k_gather_cols(LArgs a, uint32_t layer) {
+// Measured columns of a layer's ops (x plane, all CW words) into the
+// item-major scratch cols[item][CW].  Tiles of 8 words x 128 items: two lanes
+// per item, each reading 4 consecutive words (from the column-packed copy, or
+// the row-packed one for dirty slices) and storing them as one 16-byte half
+// of the item's 32-byte segment, so a warp's stores fill whole sectors.
+constexpr uint32_t GATHER_ITEMS = 128;
+__global__ void __launch_bounds__(2 * GATHER_ITEMS) k_gather_cols(LArgs a, uint32_t layer) {
     const uint32_t n = a.P.n, CW = a.P.CW;
-    const uint32_t w = blockIdx.x, t = blockIdx.y;
+    const uint32_t t = blockIdx.z;
     const Layer M = a.P.layers[layer];
-    const bool dty = a.dirty[(size_t)t * CW + w] != 0;
+    const uint32_t i = blockIdx.y * GATHER_ITEMS + (threadIdx.x >> 1);
+    if (i >= M.count) return;
+    const uint32_t w0 = 8 * blockIdx.x + 4 * (threadIdx.x & 1);
+    if (w0 >= CW) return;
+    const uint32_t q = a.P.mitems[M.first + i].q;
+    const uint8_t *dirty = a.dirty + (size_t)t * CW;
     const uint32_t *qx = a.qm + t * a.qm_stride;
     const uint32_t *rm = a.rm + t * a.rm_stride;
-    uint32_t *cols = a.cols + t * a.cols_stride;
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
-        const uint32_t q = a.P.mitems[M.first + i].q;
-        cols[(size_t)i * CW + w] = dty ? rm_col_word(rm, a.RS, a.Hr, w, q, false)
-                                       : qx[(size_t)w * n + q];
+    uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t w = w0 + k;
+        v[k] = w >= CW ? 0u : dirty[w] ? rm_col_word(rm, a.RS, a.Hr, w, q, false) : qx[(size_t)w * n + q];
+    }
+    if ((CW & 3u) == 0 && ((uintptr_t)col & 15u) == 0) {
+        *reinterpret_cast<uint4 *>(col + w0) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (w0 + k < CW) col[w0 + k] = v[k];
     }
 }
 
@@ -1614,7 +1626,6 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     }
     const uint32_t gthreads = std::min<uint32_t>(1024, std::max<uint32_t>(64, (p.dev.max_gitems / 2 + 31) / 32 * 32));
     const size_t gsm = layered_gate_smem(b.n);
-    bool cols_ready = false;
     int32_t cond_pending = -1;      // measurement layer whose flips the next gate run applies
     for (size_t k = 0; k < p.runs.size(); k++) {
         const Run &R = p.runs[k];
@@ -1625,11 +1636,9 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
             cond_pending = -1;
             const bool next_meas = k + 1 < p.runs.size() && p.runs[k + 1].type == LT_MEAS;
             g.want_rm = next_meas ? 1u : 0u;
-            g.cols_layer = next_meas ? (int32_t)p.runs[k + 1].l0 : -1;
             launch(kp, STAB_KERNEL_GATE_RUN, s, R.alg_bytes * b.count,
                    [&] { k_gate_run<<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g); });
             b.rm_valid = next_meas;
-            cols_ready = next_meas;
         } else {
             const uint32_t l = R.l0;
             const Layer &L = p.layers[l];
@@ -1638,9 +1647,10 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                        [&] { k_qm_to_rm<<<dim3(b.CW, b.count), 256, 0, s>>>(a); });
                 b.rm_valid = true;
             }
-            if (!cols_ready)
-                launch(kp, STAB_KERNEL_OTHER, s, 0.0,
-                       [&] { k_gather_cols<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
+            launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
+                k_gather_cols<<<dim3((b.CW + 7) / 8, (L.count + GATHER_ITEMS - 1) / GATHER_ITEMS, b.count),
+                                2 * GATHER_ITEMS, 0, s>>>(a, l);
+            });
             const uint32_t nb = (L.count + DET_WARPS - 1) / DET_WARPS;
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
@@ -1660,7 +1670,6 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                     launch(kp, STAB_KERNEL_OTHER, s, 0.0,
                            [&] { k_cond<<<dim3(b.CW, b.count), 256, 0, s>>>(a, l); });
             }
-            cols_ready = false;
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
