@@ -37,10 +37,7 @@ METRIC = "surface-code d=71 gate+measure ops/s"
 # DRAM bytes (read + write) per launch from one ncu capture of the d=71 step
 # (summaries and commands under profiles/).  A kernel changed since its
 # capture has no entry here (traffic reported as null).
-NCU_TRAFFIC = {
-    "k_gate_run": {"bytes_per_launch": 83.2e6,
-                   "source": "profiles/k_gate_run_d71.md (steady syndrome-round launch)"},
-}
+NCU_TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -299,35 +296,48 @@ def main():
     torch.cuda.synchronize()
     B.stab_launch_count(sim.ctx, reset=True)
     B.stab_engine_counters(sim.ctx, reset=True)
-    B.stab_profile(sim.ctx, 0x1F)
-    for k in range(5):
-        B.stab_profile_read(sim.ctx, k, reset=True)
+    B.stab_profile(sim.ctx, 0)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    evs = []
+
+    def run_steps(profiled):
+        evs = []
+        for s in range(W, W + K):
+            flush.fill_(s)                   # L2 flush between timed steps (outside the events)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step(s)
+            e1.record()
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # timed region: the library replays each step's launch sequence as a CUDA graph
     t_wall0 = time.perf_counter()
-    for s in range(W, W + K):
-        flush.fill_(s)                       # L2 flush between timed steps (outside the events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step(s)
-        e1.record()
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
+    step_ms = run_steps(False)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     sim.sync()
-    B.stab_profile(sim.ctx, 0)
     launches = B.stab_launch_count(sim.ctx, reset=True)
     counters = B.stab_engine_counters(sim.ctx, reset=True)
-    kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in sorted(B.KERNEL_NAMES)}
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     value, t_dev = aggregate(sum(step_ms) / 1e3, ops_per_step, K, world, dist, sim.device)
-
-    # parity spot check of the timed shots (first rounds, oracle) is done by the
-    # tests; here only the noiseless-free sanity: the record is non-trivial.
     recs = B.records_to_numpy(rec)
+    # per-kernel durations: CUDA events around every launch, over K more steps
+    # on the same inputs (per-launch events turn graph replay off, so they are
+    # kept out of the timed steps); the records must come out the same
+    B.stab_profile(sim.ctx, 0xFF)
+    for k in sorted(B.KERNEL_NAMES):
+        B.stab_profile_read(sim.ctx, k, reset=True)
+    step_ms_prof = run_steps(True)
+    sim.sync()
+    B.stab_profile(sim.ctx, 0)
+    B.stab_launch_count(sim.ctx, reset=True)
+    counters_prof = B.stab_engine_counters(sim.ctx, reset=True)
+    kstats = {B.KERNEL_NAMES[k]: B.stab_profile_read(sim.ctx, k, reset=True) for k in sorted(B.KERNEL_NAMES)}
+    if not np.array_equal(B.records_to_numpy(rec), recs):
+        raise AssertionError("graph replay and plain launches gave different records")
+
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region
     pin_c = torch.from_numpy(coins.view(np.int64)).pin_memory()
@@ -360,11 +370,11 @@ def main():
     row_bytes = 2 * circ.n / 8.0          # a tableau row (x and z) or column (2n rows), in bytes
     alg = ds["alg_bytes"]
     model = "library model" if alg > 0 else None
-    if dom == "k_meas_rand" and counters.get("wave_ops"):
+    if dom == "k_meas_rand" and counters_prof.get("wave_ops"):
         # per random measurement: read its column, copy the pivot row into its
         # destabilizer, write the new stabilizer row (4 row/column transfers);
         # per rowsum: read the pivot row and the row, write the row (3)
-        alg = (4 * counters["wave_ops"] + 3 * counters["sum_A"]) * row_bytes
+        alg = (4 * counters_prof["wave_ops"] + 3 * counters_prof["sum_A"]) * row_bytes
         model = "(4 x random measurements + 3 x rowsums) x 2n/8 bytes"
     if ds["launches"] and alg > 0:
         ach = alg / (ds["total_ms"] / 1e3) / 1e9
@@ -411,6 +421,8 @@ def main():
         "roofline_gate_run": gate_roof,
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()},
         "engine_counters_per_step": {k: v / K for k, v in counters.items()},
+        "kernel_timing": "CUDA events around each launch over K further steps (plain launches, "
+                         f"{float(np.mean(step_ms_prof)):.3f} ms per step); the timed steps replay CUDA graphs",
         "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu:

@@ -203,6 +203,7 @@ static size_t prog_layout(const HostProg &P, size_t off[PROG_ARRAYS + 1]) {
 
 static void free_prog(HostProg &P) {
     if (P.lay) free_prog(*P.lay);
+    prog_graphs_free(P);
     if (P.dmem) cudaFree(P.dmem);
     P.dmem = nullptr;
 }
@@ -276,8 +277,9 @@ int run_layered_shots(stab_ctx *ctx, const HostProg &user_prog, uint32_t shots, 
             if (ds.coins) ds.coins += (size_t)s0 * ds.coin_stride;
             if (ds.noise) ds.noise += (size_t)s0 * ds.noise_stride;
         }
+        GraphSlot *gsl = (s == ctx->stream && graph_slot_init(ctx->gslot) == 0) ? &ctx->gslot : nullptr;
         e = layered_run(p, b, ms, ds, (unsigned long long *)(d_record + (size_t)s0 * record_words),
-                        record_words, ctx->d_err, ctx->lc, s, &ctx->prof, ctx->d_stats);
+                        record_words, ctx->d_err, ctx->lc, s, &ctx->prof, ctx->d_stats, gsl);
         if (e) return cuda_fail(e, "layered run");
         work.rm_valid = b.rm_valid;
     }
@@ -408,6 +410,8 @@ void stab_destroy(stab_ctx *ctx) {
         cudaStreamSynchronize(ctx->stream);
         for (auto &kv : ctx->progs)
             free_prog(*kv.second);
+        if (ctx->gslot.gs) cudaStreamSynchronize(ctx->gslot.gs);
+        graph_slot_free(ctx->gslot);
         batch_free(ctx->resident);
         batch_free(ctx->tmp);
         ctx->ms_buf.release();
@@ -513,8 +517,9 @@ int stab_apply_circuit(stab_ctx *ctx, uint64_t circuit_id, const stab_streams *s
     if (rc) return rc;
     cudaError_t e = cudaMemsetAsync(d_record, 0, (size_t)b.count * record_words * 8, ctx->stream);
     if (e) return cuda_fail(e, "clearing records");
+    GraphSlot *gsl = graph_slot_init(ctx->gslot) == 0 ? &ctx->gslot : nullptr;
     e = layered_run(layered_prog(*p), b, ctx->ms, to_dev(*streams), (unsigned long long *)d_record, record_words,
-                    ctx->d_err, ctx->lc, ctx->stream, &ctx->prof, ctx->d_stats);
+                    ctx->d_err, ctx->lc, ctx->stream, &ctx->prof, ctx->d_stats, gsl);
     if (e) return cuda_fail(e, "apply_circuit");
     return STAB_OK;
 }

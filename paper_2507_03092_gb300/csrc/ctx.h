@@ -40,6 +40,7 @@ struct stab_ctx {
     unsigned long long *d_stats = nullptr;          // DC_* counters
     std::map<uint32_t, stab_tune> tune;              // bucket ceil(n/32) -> shape
     stab::KernelProf prof;
+    stab::GraphSlot gslot;                          // graph replay for work on `stream`
     stab::ServeState *serve = nullptr;
 };
 

@@ -111,6 +111,12 @@ struct HostProg {
     // conjugation U^dag M_Z U of one qubit; `lay` is the program compiled
     // from that rewritten op list (null when the circuit has no MPP).
     std::unique_ptr<HostProg> lay;
+    // Layered-engine launch sequence replayed as a CUDA graph: two executable
+    // graphs used in turn, each updated in place from a fresh capture once its
+    // previous launch has finished (event `gdone`).
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaEvent_t gdone[2] = {nullptr, nullptr};
+    int gnext = 0;
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
     void *dmem = nullptr;       // device copy of the arrays
@@ -221,10 +227,21 @@ void batch_free(Batch &b);
 
 // Layered engine (layered.cu)
 cudaError_t layered_init(Batch &b, cudaStream_t s, KernelProf *kp);
+// A capturable stream joined to the caller's stream by two events: the
+// layered engine captures its launch sequence there and replays it as a graph.
+struct GraphSlot {
+    cudaStream_t gs = nullptr;
+    cudaEvent_t in = nullptr, out = nullptr;
+};
+int graph_slot_init(GraphSlot &g);
+void graph_slot_free(GraphSlot &g);
+void prog_graphs_free(HostProg &p);
+// gsl: replay as a CUDA graph through this slot when per-launch profiling is
+// off (nullptr: plain launches on s)
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
-                        unsigned long long *d_stats);
+                        unsigned long long *d_stats, GraphSlot *gsl = nullptr);
 cudaError_t layered_sync_qm(Batch &b, cudaStream_t s);
 cudaError_t layered_commute(Batch &b, uint32_t index, const unsigned long long *px, const unsigned long long *pz,
                             size_t m, unsigned long long *out, cudaStream_t s, KernelProf *kp);

@@ -1599,10 +1599,44 @@ void set_wave_caps(const WaveCaps &c) {
     g_caps.window = std::max(1u, c.window);
 }
 
+static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
+                                 unsigned long long *record, size_t rec_stride, int *d_err,
+                                 const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
+                                 unsigned long long *d_stats);
+
+int graph_slot_init(GraphSlot &g) {
+    if (g.gs) return 0;
+    if (cudaStreamCreateWithFlags(&g.gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        graph_slot_free(g);
+        return -1;
+    }
+    return 0;
+}
+
+void graph_slot_free(GraphSlot &g) {
+    if (g.gs) cudaStreamDestroy(g.gs);
+    if (g.in) cudaEventDestroy(g.in);
+    if (g.out) cudaEventDestroy(g.out);
+    g = GraphSlot{};
+}
+
+void prog_graphs_free(HostProg &p) {
+    for (int k = 0; k < 2; k++) {
+        if (p.gdone[k]) cudaEventSynchronize(p.gdone[k]);
+        if (p.gexec[k]) cudaGraphExecDestroy(p.gexec[k]);
+        if (p.gdone[k]) cudaEventDestroy(p.gdone[k]);
+        p.gexec[k] = nullptr;
+        p.gdone[k] = nullptr;
+    }
+}
+
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
-                        unsigned long long *d_stats) {
+                        unsigned long long *d_stats, GraphSlot *gsl) {
     if (!g_attr_set) {
         cudaFuncSetAttribute(k_gate_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(lc.smem_optin - 1024));
@@ -1614,6 +1648,51 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                              (int)(lc.smem_optin - 1024));
         g_attr_set = true;
     }
+    if (!gsl || !gsl->gs || (kp && kp->mask))
+        return layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, s, kp, d_stats);
+    // capture the launch sequence on the slot's stream, after the work already
+    // queued on s, and replay it as one graph
+    HostProg &hp = const_cast<HostProg &>(p);
+    const int k = hp.gnext;
+    if (!hp.gdone[k] && cudaEventCreateWithFlags(&hp.gdone[k], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, s, kp, d_stats);
+    }
+    cudaError_t e = cudaEventRecord(gsl->in, s);
+    if (!e) e = cudaStreamWaitEvent(gsl->gs, gsl->in, 0);
+    if (!e) e = cudaStreamBeginCapture(gsl->gs, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    const cudaError_t ei = layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, gsl->gs, kp, d_stats);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(gsl->gs, &g);
+    if (ei || ec) {
+        if (g) cudaGraphDestroy(g);
+        return ei ? ei : ec;
+    }
+    // this exec's previous launch must be done before it is updated
+    e = cudaEventSynchronize(hp.gdone[k]);
+    if (!e && hp.gexec[k]) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(hp.gexec[k], g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(hp.gexec[k]);
+            hp.gexec[k] = nullptr;
+        }
+    }
+    if (!e && !hp.gexec[k]) e = cudaGraphInstantiate(&hp.gexec[k], g, 0);
+    cudaGraphDestroy(g);
+    if (!e) e = cudaGraphLaunch(hp.gexec[k], gsl->gs);
+    if (!e) e = cudaEventRecord(hp.gdone[k], gsl->gs);
+    if (!e) e = cudaEventRecord(gsl->out, gsl->gs);
+    if (!e) e = cudaStreamWaitEvent(s, gsl->out, 0);
+    hp.gnext = k ^ 1;
+    return e;
+}
+
+static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
+                                 unsigned long long *record, size_t rec_stride, int *d_err,
+                                 const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
+                                 unsigned long long *d_stats) {
     LArgs a = make_args(&p, b, &ms, &st, record, rec_stride, d_err);
     a.stats = d_stats;
     const size_t rsm = rand_smem(b.n, b.H);

@@ -1,0 +1,88 @@
+"""The layered engine replays its launch sequence as a CUDA graph when
+per-launch profiling is off.  Graph replay must give the records (and the
+tableau) of plain launches: over repeated calls (executable graphs updated in
+place), changing shot counts (new graph topology), circuits with Pauli-product
+measurements, and interleaved with other work on the caller's stream."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_03092_gb300 import binding as B
+from paper_2507_03092_gb300 import circuit as C
+from paper_2507_03092_gb300 import streams as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s = B.Simulator(0)
+    yield s
+    s.close()
+
+
+def _run(sim, cid, circ, coins, noise, profiled):
+    B.stab_profile(sim.ctx, 0xFF if profiled else 0)
+    try:
+        out = B.records_to_numpy(sim.sample(cid, circ, coins.shape[0], coins, noise, engine=B.ENGINE_LAYERED))
+        sim.sync()
+    finally:
+        B.stab_profile(sim.ctx, 0)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["surface", "random", "mpp"])
+def test_graph_replay_equals_plain_launches(sim, kind):
+    if kind == "surface":
+        circ = C.surface_code_memory(9, p=5e-3)
+    elif kind == "random":
+        circ = C.random_clifford_layers(300, 40, seed=3)
+    else:
+        circ = C.random_small_circuit(70, 400, seed=4, mpp=True)
+    cid = sim.compile(circ)
+    for rep, shots in enumerate((5, 5, 5, 2, 7, 7)):
+        coins, noise = S.streams_for(circ, 40 + rep, range(shots))
+        g = _run(sim, cid, circ, coins, noise, profiled=False)
+        p = _run(sim, cid, circ, coins, noise, profiled=True)
+        assert np.array_equal(g, p), (kind, rep)
+        if rep in (0, 3):
+            want, _ = oracle.sample(circ, coins, noise)
+            assert np.array_equal(g, want), (kind, rep)
+
+
+def test_graph_replay_orders_with_caller_stream(sim):
+    """Work queued on the caller's stream before and after a replayed call
+    sees the call's results in order (records copied right after the call)."""
+    torch = pytest.importorskip("torch")
+    circ = C.surface_code_memory(5, p=1e-2)
+    cid = sim.compile(circ)
+    coins, noise = S.streams_for(circ, 9, range(16))
+    want, _ = oracle.sample(circ, coins, noise)
+    dc, dn = sim.to_dev(coins), sim.to_dev(noise)
+    for _ in range(3):
+        rec = sim.record_buffer(16, circ.record_words)
+        rec.fill_(-1)                                 # queued before the call
+        B.stab_sample(sim.ctx, cid, 16, B.make_streams(B.STREAM_BUFFER, coins=dc, noise=dn), rec,
+                      B.ENGINE_LAYERED)
+        copy = rec.clone()                            # queued after the call
+        torch.cuda.synchronize()
+        assert np.array_equal(B.records_to_numpy(copy), want)
+
+
+def test_apply_circuit_graph_replay_tableau(sim):
+    circ = C.random_small_circuit(40, 200, seed=8)
+    coins, noise = S.streams_for(circ, 2, [0])
+    want, wtab, _ = oracle.run(circ, coins[0], noise[0], return_tableau=True)
+    cid = sim.compile(circ)
+    for _ in range(2):
+        B.stab_tableau_init(sim.ctx, circ.n, 1)
+        rec = sim.record_buffer(1, circ.record_words)
+        B.stab_apply_circuit(sim.ctx, cid, B.make_streams(B.STREAM_BUFFER, coins=sim.to_dev(coins),
+                                                          noise=sim.to_dev(noise)), rec)
+        sim.sync()
+        assert np.array_equal(B.records_to_numpy(rec)[0], want)
+        for g, w in zip(B.stab_get_tableau(sim.ctx, 0, circ.n), wtab):
+            assert np.array_equal(g, w)
