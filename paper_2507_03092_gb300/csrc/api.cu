@@ -138,7 +138,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     const size_t cnt_b = 4 * (size_t)std::max<size_t>(1, p.layers.size()) * count;
     const size_t bytes = up(4 * words) + up(2 * items) + up(first_b) + up(ev_b) + up(cnt_b) +
                          up(qmap_b) + up(detz_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b) + up(pwl_b) +
-                         up(flips_b) + up(cnt_b);
+                         up(flips_b) + up(cnt_b) + up(sizeof(CallArgs));
     int rc = buf.ensure(bytes);
     if (rc) return rc;
     char *b = (char *)buf.p;
@@ -156,7 +156,8 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     ms.msup = (uint16_t *)b; b += up(sup_b);
     ms.pwl = (uint16_t *)b; b += up(pwl_b);
     ms.flips = (uint32_t *)b; b += up(flips_b);
-    ms.flip_cnt = (uint32_t *)b;
+    ms.flip_cnt = (uint32_t *)b; b += up(cnt_b);
+    ms.call = (CallArgs *)b;
     ms.cap_words = words;
     ms.cap_items = items;
     return STAB_OK;

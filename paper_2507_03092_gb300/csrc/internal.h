@@ -111,12 +111,15 @@ struct HostProg {
     // conjugation U^dag M_Z U of one qubit; `lay` is the program compiled
     // from that rewritten op list (null when the circuit has no MPP).
     std::unique_ptr<HostProg> lay;
-    // Layered-engine launch sequence replayed as a CUDA graph: two executable
-    // graphs used in turn, each updated in place from a fresh capture once its
-    // previous launch has finished (event `gdone`).
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaEvent_t gdone[2] = {nullptr, nullptr};
-    int gnext = 0;
+    // Layered-engine launch sequence replayed as a CUDA graph.  The graph is
+    // valid for the kernel arguments and entry state in `gkey`; a different
+    // key recaptures it and updates the executable graph in place once its
+    // last launch has finished (event `gdone`).
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gdone = nullptr;
+    std::vector<unsigned char> gkey;
+    unsigned long long glaunches = 0;   // kernel launches in the graph
+    bool grm_after = false;             // batch's row-packed copy valid after the run
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
     void *dmem = nullptr;       // device copy of the arrays
@@ -180,7 +183,17 @@ struct MeasScratch {
     uint32_t *flip_cnt = nullptr; // [count][n_layers]
     uint32_t *ev = nullptr;       // [count][ev_total] noise events
     uint32_t *ev_cnt = nullptr;   // [count][n_layers] noise-event counts
+    struct CallArgs *call = nullptr;   // per-call inputs of the layered engine (device)
     size_t cap_words = 0, cap_items = 0;
+};
+
+// Inputs that change from call to call (streams, record buffer): kept in
+// device memory, written before each run, so a captured launch sequence can be
+// replayed unchanged.
+struct CallArgs {
+    DevStreams st;
+    unsigned long long *record;
+    unsigned long long rec_stride;
 };
 
 struct LaunchCfg {

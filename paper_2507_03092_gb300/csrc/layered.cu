@@ -40,6 +40,7 @@
 #include "device_common.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace stab {
 
@@ -78,9 +79,7 @@ struct LArgs {
     uint32_t *flips, *flip_cnt;      // [B][2*max_meas], [B][n_layers]
     unsigned long long *stats;       // DC_* counters (may be null)
     WaveCaps caps;                   // k_meas_rand list capacities (<= compile-time maxima)
-    DevStreams st;
-    unsigned long long *record;
-    unsigned long long rec_stride;
+    const CallArgs *call;            // streams and record of this call (device)
     int *err;
     uint32_t B;
 };
@@ -225,7 +224,7 @@ __global__ void k_noise_events(LArgs a) {
         const GItem g = a.P.gitems[i];
         if (!g.nn) continue;
         uint32_t Pa, Pb;
-        item_noise(g, a.st, t, a.P.thr, Pa, Pb);
+        item_noise(g, a.call->st, t, a.P.thr, Pa, Pb);
         if (!(Pa | Pb)) continue;
         const uint32_t l = a.P.item_layer[i];
         const Layer L = a.P.layers[l];
@@ -242,7 +241,23 @@ __global__ void k_noise_events(LArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(1024) k_gate_run(LArgs a, GRun g) {
+// A layer whose noise events overflowed their slots: every draw of the layer
+// evaluated again (kept out of line: the common path needs none of this).
+__device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t count, const Thr *thr,
+                                                 const CallArgs *call, uint32_t t, const uint32_t *sx,
+                                                 const uint32_t *sz) {
+    uint32_t racc = 0;
+    for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) {
+        const GItem gi = items[k];
+        if (!gi.nn) continue;
+        uint32_t Pa, Pb;
+        item_noise(gi, call->st, t, thr, Pa, Pb);
+        racc ^= xz_flip(Pa, sx[gi.a], sz[gi.a]) ^ xz_flip(Pb, sx[gi.b], sz[gi.b]);
+    }
+    return racc;
+}
+
+__global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t sred[32];
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
@@ -313,13 +328,7 @@ __global__ void __launch_bounds__(1024) k_gate_run(LArgs a, GRun g) {
                     racc ^= xz_flip(v >> 30, sx[q], sz[q]);
                 }
             } else {
-                for (uint32_t k = threadIdx.x; k < L.count; k += blockDim.x) {
-                    const GItem gi = a.P.gitems[L.first + k];
-                    if (!gi.nn) continue;
-                    uint32_t Pa, Pb;
-                    item_noise(gi, a.st, t, a.P.thr, Pa, Pb);
-                    racc ^= xz_flip(Pa, sx[gi.a], sz[gi.a]) ^ xz_flip(Pb, sx[gi.b], sz[gi.b]);
-                }
+                racc ^= layer_noise_all(a.P.gitems + L.first, L.count, a.P.thr, a.call, t, sx, sz);
             }
             __syncthreads();
         }
@@ -559,7 +568,7 @@ __device__ __forceinline__ void outcome_flips(const LArgs &a, uint32_t t, uint32
 
 __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_t rec, uint32_t out) {
     if (rec != 0xffffffffu && out)
-        atomicOr(&a.record[(unsigned long long)t * a.rec_stride + (rec >> 6)], 1ull << (rec & 63));
+        atomicOr(&a.call->record[(unsigned long long)t * a.call->rec_stride + (rec >> 6)], 1ull << (rec & 63));
 }
 
 // One warp scans a measured column (CW words): pivot = first set row of the
@@ -622,10 +631,10 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
     uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     if (m.flags & MF_RESET_ERR) {
         if (lane == 0) {
-            const uint32_t u2 = noise_word(a.st, t, m.nl + 2);
+            const uint32_t u2 = noise_word(a.call->st, t, m.nl + 2);
             if ((unsigned long long)u2 < a.P.thr[m.np].t[1]) push_flip(a, t, layer, m.q, 3u);
         }
-        const uint32_t u0 = noise_word(a.st, t, m.nl);
+        const uint32_t u0 = noise_word(a.call->st, t, m.nl);
         if ((unsigned long long)u0 >= a.P.thr[m.np].t[0]) {
             if (lane == 0) { stat[i] = MS_SKIP; out[i] = 0; }
             return;
@@ -1327,8 +1336,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
             const uint32_t k = sel[x], i = pend[k], q = piv[k], p = 32 * H + q;
             const MItem m = a.P.mitems[M.first + i];
-            const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.st, t, m.nl + 1) & 1u)
-                                                           : coin_bit(a.st, t, m.coin);
+            const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
+                                                           : coin_bit(a.call->st, t, m.coin);
             // row q <- row p, row p <- Z_a: 16-byte words over the Hr-word rows
             // (the words past H are zero in every row)
             const uint32_t H4 = Hr >> 2;
@@ -1448,9 +1457,10 @@ void batch_free(Batch &b) {
     b = Batch{};
 }
 
-static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevStreams *st,
-                       unsigned long long *record, size_t rec_stride, int *d_err) {
-    LArgs a{};
+static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err) {
+    // zeroed bytes, padding included: the graph cache compares LArgs byte for byte
+    LArgs a;
+    memset(&a, 0, sizeof a);
     a.caps = g_caps;
     if (p) a.P = p->dev;
     a.P.n = b.n; a.P.H = b.H; a.P.CW = b.CW;
@@ -1476,9 +1486,7 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, const DevSt
         a.flips = ms->flips;
         a.flip_cnt = ms->flip_cnt;
     }
-    if (st) a.st = *st;
-    a.record = record;
-    a.rec_stride = rec_stride;
+    a.call = ms ? ms->call : nullptr;
     a.err = d_err;
     a.B = b.count;
     return a;
@@ -1501,14 +1509,14 @@ static void launch(KernelProf *kp, uint32_t kind, cudaStream_t s, double bytes, 
 }
 
 cudaError_t layered_init(Batch &b, cudaStream_t s, KernelProf *kp) {
-    LArgs a = make_args(nullptr, b, nullptr, nullptr, nullptr, 0, nullptr);
+    LArgs a = make_args(nullptr, b, nullptr, nullptr);
     launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] { k_init<<<1024, 256, 0, s>>>(a); });
     b.rm_valid = true;
     return cudaGetLastError();
 }
 
 cudaError_t layered_sync_qm(Batch &b, cudaStream_t s) {
-    LArgs a = make_args(nullptr, b, nullptr, nullptr, nullptr, 0, nullptr);
+    LArgs a = make_args(nullptr, b, nullptr, nullptr);
     k_rm_to_qm<<<dim3(b.CW, b.count), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -1599,8 +1607,7 @@ void set_wave_caps(const WaveCaps &c) {
     g_caps.window = std::max(1u, c.window);
 }
 
-static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
-                                 unsigned long long *record, size_t rec_stride, int *d_err,
+static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, int *d_err,
                                  const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
                                  unsigned long long *d_stats);
 
@@ -1624,13 +1631,12 @@ void graph_slot_free(GraphSlot &g) {
 }
 
 void prog_graphs_free(HostProg &p) {
-    for (int k = 0; k < 2; k++) {
-        if (p.gdone[k]) cudaEventSynchronize(p.gdone[k]);
-        if (p.gexec[k]) cudaGraphExecDestroy(p.gexec[k]);
-        if (p.gdone[k]) cudaEventDestroy(p.gdone[k]);
-        p.gexec[k] = nullptr;
-        p.gdone[k] = nullptr;
-    }
+    if (p.gdone) cudaEventSynchronize(p.gdone);
+    if (p.gexec) cudaGraphExecDestroy(p.gexec);
+    if (p.gdone) cudaEventDestroy(p.gdone);
+    p.gexec = nullptr;
+    p.gdone = nullptr;
+    p.gkey.clear();
 }
 
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
@@ -1648,52 +1654,75 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                              (int)(lc.smem_optin - 1024));
         g_attr_set = true;
     }
-    if (!gsl || !gsl->gs || (kp && kp->mask))
-        return layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, s, kp, d_stats);
-    // capture the launch sequence on the slot's stream, after the work already
-    // queued on s, and replay it as one graph
-    HostProg &hp = const_cast<HostProg &>(p);
-    const int k = hp.gnext;
-    if (!hp.gdone[k] && cudaEventCreateWithFlags(&hp.gdone[k], cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, s, kp, d_stats);
-    }
-    cudaError_t e = cudaEventRecord(gsl->in, s);
-    if (!e) e = cudaStreamWaitEvent(gsl->gs, gsl->in, 0);
-    if (!e) e = cudaStreamBeginCapture(gsl->gs, cudaStreamCaptureModeThreadLocal);
+    // this call's inputs, read by the kernels from device memory (a pageable
+    // source is staged before cudaMemcpyAsync returns)
+    CallArgs ca{};
+    ca.st = st;
+    ca.record = record;
+    ca.rec_stride = rec_stride;
+    cudaError_t e = cudaMemcpyAsync(ms.call, &ca, sizeof ca, cudaMemcpyHostToDevice, s);
     if (e) return e;
-    const cudaError_t ei = layered_issue(p, b, ms, st, record, rec_stride, d_err, lc, gsl->gs, kp, d_stats);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(gsl->gs, &g);
-    if (ei || ec) {
-        if (g) cudaGraphDestroy(g);
-        return ei ? ei : ec;
+    if (!gsl || !gsl->gs || (kp && kp->mask))
+        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
+    // Graph replay on the slot's stream, after the work already queued on s.
+    // The captured sequence depends only on the kernel arguments (per-call
+    // inputs excluded) and on whether the row-packed copy is valid on entry.
+    HostProg &hp = const_cast<HostProg &>(p);
+    LArgs ka = make_args(&p, b, &ms, d_err);
+    ka.stats = d_stats;
+    std::vector<unsigned char> key(sizeof(LArgs) + 1);
+    memcpy(key.data(), &ka, sizeof ka);
+    key[sizeof ka] = b.rm_valid ? 1 : 0;
+    if (!hp.gdone && cudaEventCreateWithFlags(&hp.gdone, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
     }
-    // this exec's previous launch must be done before it is updated
-    e = cudaEventSynchronize(hp.gdone[k]);
-    if (!e && hp.gexec[k]) {
-        cudaGraphExecUpdateResultInfo info{};
-        if (cudaGraphExecUpdate(hp.gexec[k], g, &info) != cudaSuccess) {
-            cudaGetLastError();
-            cudaGraphExecDestroy(hp.gexec[k]);
-            hp.gexec[k] = nullptr;
+    e = cudaEventRecord(gsl->in, s);
+    if (!e) e = cudaStreamWaitEvent(gsl->gs, gsl->in, 0);
+    if (e) return e;
+    if (hp.gexec && hp.gkey == key) {
+        e = cudaGraphLaunch(hp.gexec, gsl->gs);
+        if (kp) kp->launches += hp.glaunches;
+        b.rm_valid = hp.grm_after;
+    } else {
+        e = cudaStreamBeginCapture(gsl->gs, cudaStreamCaptureModeThreadLocal);
+        if (e) return e;
+        const unsigned long long n0 = kp ? kp->launches : 0;
+        const cudaError_t ei = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(gsl->gs, &g);
+        if (ei || ec) {
+            if (g) cudaGraphDestroy(g);
+            hp.gkey.clear();
+            return ei ? ei : ec;
         }
+        hp.glaunches = kp ? kp->launches - n0 : 0;
+        hp.grm_after = b.rm_valid;
+        // the executable graph is updated only after its last launch finished
+        e = cudaEventSynchronize(hp.gdone);
+        if (!e && hp.gexec) {
+            cudaGraphExecUpdateResultInfo info{};
+            if (cudaGraphExecUpdate(hp.gexec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(hp.gexec);
+                hp.gexec = nullptr;
+            }
+        }
+        if (!e && !hp.gexec) e = cudaGraphInstantiate(&hp.gexec, g, 0);
+        cudaGraphDestroy(g);
+        hp.gkey = e ? std::vector<unsigned char>() : key;
+        if (!e) e = cudaGraphLaunch(hp.gexec, gsl->gs);
     }
-    if (!e && !hp.gexec[k]) e = cudaGraphInstantiate(&hp.gexec[k], g, 0);
-    cudaGraphDestroy(g);
-    if (!e) e = cudaGraphLaunch(hp.gexec[k], gsl->gs);
-    if (!e) e = cudaEventRecord(hp.gdone[k], gsl->gs);
+    if (!e) e = cudaEventRecord(hp.gdone, gsl->gs);
     if (!e) e = cudaEventRecord(gsl->out, gsl->gs);
     if (!e) e = cudaStreamWaitEvent(s, gsl->out, 0);
-    hp.gnext = k ^ 1;
     return e;
 }
 
-static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
-                                 unsigned long long *record, size_t rec_stride, int *d_err,
+static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, int *d_err,
                                  const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
                                  unsigned long long *d_stats) {
-    LArgs a = make_args(&p, b, &ms, &st, record, rec_stride, d_err);
+    LArgs a = make_args(&p, b, &ms, d_err);
     a.stats = d_stats;
     const size_t rsm = rand_smem(b.n, b.H);
     cudaMemsetAsync(ms.flip_cnt, 0, sizeof(uint32_t) * std::max<size_t>(1, p.layers.size()) * b.count, s);
