@@ -121,7 +121,8 @@ typedef struct stab_circuit_info {
 } stab_circuit_info;
 
 /* engines for stab_sample */
-#define STAB_ENGINE_AUTO 0u
+#define STAB_ENGINE_AUTO 0u      /* resident for tableaux of <= 24 KB (n <= ~200) with >= 512 shots
+                                   or n <= 32, layered otherwise (from measured per-shot costs) */
 #define STAB_ENGINE_LAYERED 1u  /* tableau in HBM/L2, one launch per gate run / measurement layer */
 #define STAB_ENGINE_RESIDENT 2u /* tableau in shared memory, whole circuit in one persistent launch */
 

@@ -339,11 +339,23 @@ int run_resident_groups(stab_ctx *ctx, const stab_job_group *groups, size_t n_gr
     return STAB_OK;
 }
 
-static uint32_t pick_engine(const stab_ctx *ctx, const HostProg &p, uint32_t engine) {
+// Engine for `shots` shots of p.  The resident engine runs one shot per
+// thread group for the whole circuit, so it needs many shots to fill the GPU
+// and its time per shot grows quickly with n; the layered engine spreads each
+// layer over 32-row slices of every tableau.  Measured on GB300 (rotated
+// surface codes, 128 and ~800 shots): resident is faster only for tableaux of
+// at most about 24 KB (d <= 9) given several hundred shots, or single-word
+// tableaux (n <= 32).
+bool prefer_resident(const stab_ctx *ctx, uint32_t n, uint64_t shots) {
+    if (!resident_supported(n, ctx->lc)) return false;
+    if (!layered_supported(n, ctx->lc)) return true;
+    if ((n + 31) / 32 == 1) return true;
+    return resident_smem_per_tableau(n) <= (24u << 10) && shots >= 512;
+}
+
+static uint32_t pick_engine(const stab_ctx *ctx, const HostProg &p, uint32_t engine, uint32_t shots) {
     if (engine != STAB_ENGINE_AUTO) return engine;
-    if (resident_supported(p.n, ctx->lc) && resident_smem_per_tableau(p.n) <= (100u << 10))
-        return STAB_ENGINE_RESIDENT;
-    return STAB_ENGINE_LAYERED;
+    return prefer_resident(ctx, p.n, shots) ? STAB_ENGINE_RESIDENT : STAB_ENGINE_LAYERED;
 }
 
 }  // namespace stab
@@ -606,7 +618,7 @@ int stab_sample(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, const stab_s
     if (shots == 0) return STAB_OK;
     if (!d_record) return fail(STAB_ERR_ARG, "record buffer is NULL");
     if (record_words < p->info.record_words) return fail(STAB_ERR_STREAM_SHORT, "record buffer too short");
-    const uint32_t eng = pick_engine(ctx, *p, engine);
+    const uint32_t eng = pick_engine(ctx, *p, engine, shots);
     if (eng == STAB_ENGINE_RESIDENT) {
         stab_job_group g{};
         g.circuit_id = circuit_id;

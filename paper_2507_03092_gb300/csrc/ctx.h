@@ -48,6 +48,8 @@ namespace stab {
 stab_tune default_tune(const stab_ctx *ctx, uint32_t n);
 stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n);
 const HostProg *find_prog(stab_ctx *ctx, uint64_t id);
+// engine choice from measured per-shot costs (AUTO and serving)
+bool prefer_resident(const stab_ctx *ctx, uint32_t n, uint64_t shots);
 const DevProg *prog_desc(const HostProg &p);     // device copy of p's descriptor
 DevStreams to_dev(const stab_streams &s);
 int check_streams(const HostProg &p, const stab_streams *s, uint32_t shots);

@@ -226,8 +226,10 @@ int stab_serve_submit(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, uint64
         const HostProg *p = find_prog(ctx, circuit_id);
         if (!p) return fail(STAB_ERR_NOT_FOUND, "unknown circuit id");
         if (record_words < p->info.record_words) return fail(STAB_ERR_STREAM_SHORT, "record buffer too short");
-        r.resident = resident_supported(p->n, ctx->lc) &&
-                     resident_smem_per_tableau(p->n) <= (100u << 10);
+        // small tableaux go to the resident engine, where waiting requests
+        // are merged into one launch (so a single request's shot count does
+        // not decide); larger ones get their own layered launch sequence
+        r.resident = prefer_resident(ctx, p->n, 1u << 20);
         if (!r.resident && !layered_supported(p->n, ctx->lc))
             return fail(STAB_ERR_UNSUPPORTED, "circuit too large for either engine");
         r.footprint = request_footprint(*p, shots, r.resident);
