@@ -426,7 +426,7 @@ def main():
         "roofline": roof,
         "roofline_gate_run": gate_roof,
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()},
-        "engine_counters_per_step": {k: v / K for k, v in counters.items()},
+        "engine_counters_per_step": {k: v / K for k, v in counters_prof.items()},
         "kernel_timing": "CUDA events around each launch over K further steps (plain launches, "
                          f"{float(np.mean(step_ms_prof)):.3f} ms per step); the timed steps replay CUDA graphs",
         "wall_s_timed": t_wall,

@@ -287,7 +287,8 @@ int stab_profile(stab_ctx *ctx, uint32_t kind_mask);
 int stab_profile_read(stab_ctx *ctx, uint32_t kind, stab_kernel_stats *out, int reset);
 /* Kernel launches issued by this context since the last reset. */
 int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
-/* Layered-engine work counters since the last reset (synchronizes):
+/* Layered-engine work counters since the last reset (synchronizes); counted
+ * only while per-launch profiling is on (stab_profile with a nonzero mask):
  * [0] random-measurement waves, [1] random measurements applied in waves,
  * [2] measurements found deterministic inside the random-measurement kernel,
  * [3] deterministic measurements resolved by the batched kernel,

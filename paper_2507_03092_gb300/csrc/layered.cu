@@ -362,15 +362,19 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
 // measurement layer has random ops and whose copy is stale.  The column-packed
 // copy is current then: it is only left behind by random measurements, which
 // first make the destabilizer half current.
+// (a fixed grid striding over the (tableau, slice) pairs: most tableaux need
+// nothing here)
 __global__ void k_destab_to_rm(LArgs a) {
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
-    const uint32_t w = blockIdx.x, t = blockIdx.y;
-    const uint32_t f = a.tflags[t];
-    if (!(f & TF_RAND_LAYER) || (f & TF_DESTAB_FRESH)) return;
-    const uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
-    slice_store_rm(a.rm + t * a.rm_stride, a.RS, a.Hr, H, w,
-                   [&](uint32_t j) { return j < n ? qx[(size_t)w * n + j] : 0u; },
-                   [&](uint32_t j) { return j < n ? qz[(size_t)w * n + j] : 0u; });
+    for (unsigned long long pidx = blockIdx.x; pidx < (unsigned long long)H * a.B; pidx += gridDim.x) {
+        const uint32_t t = (uint32_t)(pidx / H), w = (uint32_t)(pidx % H);
+        const uint32_t f = a.tflags[t];
+        if (!(f & TF_RAND_LAYER) || (f & TF_DESTAB_FRESH)) continue;
+        const uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
+        slice_store_rm(a.rm + t * a.rm_stride, a.RS, a.Hr, H, w,
+                       [&](uint32_t j) { return j < n ? qx[(size_t)w * n + j] : 0u; },
+                       [&](uint32_t j) { return j < n ? qz[(size_t)w * n + j] : 0u; });
+    }
 }
 
 // Full column-packed -> row-packed copy (used when a measurement layer comes
@@ -676,26 +680,31 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
 }
 
 // Outcomes of the ops that became deterministic during k_meas_rand (one warp
-// each), from the layer's final tableau.
+// each), from the layer's final tableau.  Most layers have none, so a fixed
+// grid of warps strides over the (tableau, op) pairs instead of one CTA per
+// 8 ops of every tableau.
 __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_late(LArgs a, uint32_t layer) {
     extern __shared__ uint32_t smem[];
     const uint32_t H = a.P.H, CW = a.P.CW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t t = blockIdx.y;
     const Layer M = a.P.layers[layer];
-    const uint32_t i = blockIdx.x * DET_WARPS + warp;
-    if (i >= M.count) return;
-    uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
-    if (stat[i] != MS_DETLATE) return;
-    const MItem m = a.P.mitems[M.first + i];
-    const uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
-    const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
-                                   col, m.q, smem + (size_t)warp * 2 * H, a.err);
-    if (lane == 0) {
-        stat[i] = MS_DONE;
-        out[i] = (uint8_t)o;
-        write_record(a, t, m.rec, (uint32_t)o);
-        outcome_flips(a, t, layer, m, (uint32_t)o);
+    const unsigned long long total = (unsigned long long)M.count * a.B;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * DET_WARPS;
+    for (unsigned long long idx = (unsigned long long)blockIdx.x * DET_WARPS + warp; idx < total; idx += nwarps) {
+        const uint32_t t = (uint32_t)(idx / M.count), i = (uint32_t)(idx % M.count);
+        uint8_t *stat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
+        if (stat[i] != MS_DETLATE) continue;
+        const MItem m = a.P.mitems[M.first + i];
+        const uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
+        const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
+                                       col, m.q, smem + (size_t)warp * 2 * H, a.err);
+        if (lane == 0) {
+            stat[i] = MS_DONE;
+            out[i] = (uint8_t)o;
+            write_record(a, t, m.rec, (uint32_t)o);
+            outcome_flips(a, t, layer, m, (uint32_t)o);
+        }
+        __syncwarp();
     }
 }
 
@@ -1669,7 +1678,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     // inputs excluded) and on whether the row-packed copy is valid on entry.
     HostProg &hp = const_cast<HostProg &>(p);
     LArgs ka = make_args(&p, b, &ms, d_err);
-    ka.stats = d_stats;
+    ka.stats = nullptr;                  // (this path runs only with profiling off)
     std::vector<unsigned char> key(sizeof(LArgs) + 1);
     memcpy(key.data(), &ka, sizeof ka);
     key[sizeof ka] = b.rm_valid ? 1 : 0;
@@ -1723,7 +1732,7 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
                                  const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
                                  unsigned long long *d_stats) {
     LArgs a = make_args(&p, b, &ms, d_err);
-    a.stats = d_stats;
+    a.stats = (kp && kp->mask) ? d_stats : nullptr;     // counters only while profiling
     const size_t rsm = rand_smem(b.n, b.H);
     cudaMemsetAsync(ms.flip_cnt, 0, sizeof(uint32_t) * std::max<size_t>(1, p.layers.size()) * b.count, s);
     if (p.dev.ev_total) {
@@ -1769,12 +1778,17 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
             });
-            launch(kp, STAB_KERNEL_OTHER, s, 0.0,
-                   [&] { k_destab_to_rm<<<dim3(b.H, b.count), 256, 0, s>>>(a); });
+            const uint32_t fixed = 4u * (uint32_t)lc.sm_count;
+            launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
+                const unsigned long long pairs = (unsigned long long)b.H * b.count;
+                k_destab_to_rm<<<(uint32_t)std::min<unsigned long long>(pairs, fixed), 256, 0, s>>>(a);
+            });
             launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
                    [&] { k_meas_rand<<<b.count, RAND_THREADS, rsm, s>>>(a, l); });
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
-                k_meas_late<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
+                const unsigned long long ctas = ((unsigned long long)L.count * b.count + DET_WARPS - 1) / DET_WARPS;
+                k_meas_late<<<(uint32_t)std::min<unsigned long long>(ctas, 2ull * fixed), DET_WARPS * 32,
+                              (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
             });
             if (L.has_cond) {
                 // a following gate run applies the flips as it loads each slice
