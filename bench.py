@@ -218,7 +218,9 @@ def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
         tot += (time.perf_counter() - t0) * (np.count_nonzero(dists == d) / k)
         n_plain += k
     plain = shots / tot
-    return {"workload": "4096 shots, d uniform in {3,5,7,9,11}, d rounds, twirled T1/T2 Pauli noise",
+    return {"workload": "4096 shots, d uniform in {3,5,7,9,11}, d rounds, twirled T1/T2 Pauli noise; "
+                        "one stab_sample_batch call (d <= 9: one persistent resident launch, autotuned; "
+                        "d = 11: layered engine)",
             "batched_shots_per_s": batched, "plain_shots_per_s": plain,
             "speedup": batched / plain, "plain_sample_shots": n_plain,
             "tune": {str(k): v for k, v in tunes.items()}}

@@ -196,9 +196,16 @@ typedef struct stab_job_group {
     uint64_t record_words;
 } stab_job_group;
 
+/* Every shot of every group, records keyed by (group streams, shot index) as in
+ * stab_sample.  Groups of small tableaux (the same rule as STAB_ENGINE_AUTO,
+ * with the batch's total shot count) run together in one persistent
+ * resident-engine launch shaped by the autotuner; the other groups then run
+ * through the layered engine, one launch sequence per group.  Asynchronous on
+ * the context's stream except for the job-table upload. */
 int stab_sample_batch(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
 
-/* Same launch as stab_sample_batch, for callers that cannot allocate device
+/* One persistent resident-engine launch like stab_sample_batch's (every group
+ * on the resident engine), for callers that cannot allocate device
  * memory at call time: code running where every device allocation is owned by
  * a host framework's pool, or latency-critical loops that cannot afford
  * cudaMalloc's implicit synchronisation.  (The paper has no counterpart; this

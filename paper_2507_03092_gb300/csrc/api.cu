@@ -673,7 +673,40 @@ int stab_sample_host(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, const u
 int stab_sample_batch(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups) {
     CTX_GUARD;
     if (n_groups && !groups) return fail(STAB_ERR_ARG, "groups is NULL");
-    return run_resident_groups(ctx, groups, n_groups, nullptr, ctx->stream, ctx->jobs_buf, ctx->d_counter);
+    // Groups of small tableaux share one persistent resident-engine launch;
+    // groups whose tableaux are too large for it to win run through the
+    // layered engine afterwards (the resident launch fills every SM, so the
+    // two would not overlap anyway).
+    uint64_t total = 0;
+    for (size_t gi = 0; gi < n_groups; gi++) total += groups[gi].shots;
+    std::vector<stab_job_group> res, lay;
+    for (size_t gi = 0; gi < n_groups; gi++) {
+        const HostProg *p = find_prog(ctx, groups[gi].circuit_id);
+        if (!p) return fail(STAB_ERR_NOT_FOUND, "unknown circuit id " + std::to_string(groups[gi].circuit_id));
+        if (prefer_resident(ctx, p->n, total)) res.push_back(groups[gi]);
+        else lay.push_back(groups[gi]);
+    }
+    // validate every layered group before launching anything
+    for (const stab_job_group &G : lay) {
+        const HostProg *p = find_prog(ctx, G.circuit_id);
+        int rc = check_streams(*p, &G.streams, G.shots);
+        if (rc) return rc;
+        if (G.shots && !G.d_record) return fail(STAB_ERR_ARG, "record buffer is NULL");
+        if (G.record_words < p->info.record_words)
+            return fail(STAB_ERR_STREAM_SHORT, "record has fewer words per shot than the circuit needs");
+    }
+    int rc = run_resident_groups(ctx, res.data(), res.size(), nullptr, ctx->stream, ctx->jobs_buf, ctx->d_counter);
+    if (rc) return rc;
+    for (const stab_job_group &G : lay) {
+        if (!G.shots) continue;
+        const HostProg *p = find_prog(ctx, G.circuit_id);
+        cudaError_t e = cudaMemsetAsync(G.d_record, 0, (size_t)G.shots * G.record_words * 8, ctx->stream);
+        if (e) return cuda_fail(e, "clearing records");
+        rc = run_layered_shots(ctx, *p, G.shots, G.streams, G.d_record, G.record_words, ctx->stream, ctx->tmp,
+                               ctx->ms, ctx->ms_buf);
+        if (rc) return rc;
+    }
+    return STAB_OK;
 }
 
 int stab_get_tune(stab_ctx *ctx, uint32_t n, stab_tune *out) {

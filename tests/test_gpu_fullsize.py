@@ -91,7 +91,9 @@ def test_config3_d71_noisy_prefix_bit_exact(sim):
     assert 0 < det.mean() < 0.05
 
 
-def test_config4_4096_mixed_distance_shots_one_launch(sim):
+def test_config4_4096_mixed_distance_shots_one_batch_call(sim):
+    """4096 shots of five distances in one stab_sample_batch call (small
+    tableaux in one persistent resident launch, d = 11 on the layered engine)."""
     T = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
     dists = S.shot_distances(0, 4096)
     groups, checks, keep = [], [], []
