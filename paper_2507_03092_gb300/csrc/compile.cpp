@@ -288,13 +288,16 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         L.ev_off = ev_total;
         L.ev_cap = 0;
         L.n_noisy = 0;
+        L.uniform = 0;
         if (L.type != LT_GATE) continue;
+        L.uniform = L.count ? P.gitems[L.first].gate : 0u;
         for (uint32_t i = L.first; i < L.first + L.count; i++) {
             const GItem &g = P.gitems[i];
             P.sitems[i].ab = (g.a & 0xffffu) | ((g.b & 0xffffu) << 16);
             P.sitems[i].g = g.gate;
             P.item_layer[i] = l;
             if (g.nn) L.n_noisy++;
+            if (g.gate != L.uniform) L.uniform = 0;
         }
         // room for the expected events with a wide margin; a layer whose events
         // overflow falls back to evaluating every draw in the slice kernel

@@ -62,7 +62,8 @@ static_assert(sizeof(MItem) == 24, "MItem layout");
 struct Layer {
     uint32_t type, first, count, has_cond;   // has_cond: R or RESET_ERR items present
     uint32_t ev_off, ev_cap;                 // gate layers: noise-event slots [ev_off, ev_off+ev_cap)
-    uint32_t n_noisy, pad;                   // items carrying noise
+    uint32_t n_noisy;                        // items carrying noise
+    uint32_t uniform;                        // gate layers: the gate kind every item has, else 0
 };
 
 // Packed gate item for the layered engine's slice kernel (noise handled by

@@ -241,6 +241,43 @@ __global__ void k_noise_events(LArgs a) {
     }
 }
 
+// The gate items of one layer on a slice held in shared memory (items in
+// groups of 4 per thread, all four loaded before any is used).  KIND != 0:
+// every item of the layer is that gate (no per-item dispatch).
+template <uint32_t KIND>
+__device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_t count, uint32_t *sx,
+                                           uint32_t *sz, uint32_t &racc) {
+    for (uint32_t i0 = threadIdx.x; i0 < count; i0 += 4 * blockDim.x) {
+        uint2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t i = i0 + k * blockDim.x;
+            v[k] = i < count ? __ldg(it + i) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t ga = v[k].x & 0xffffu, gb = v[k].x >> 16, gk = v[k].y;
+            if (!gk) continue;
+            if (KIND == STAB_H || KIND == STAB_S) {
+                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                racc ^= apply_gate(KIND, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za;
+            } else if (KIND == STAB_CX || KIND == STAB_CZ) {
+                uint32_t xa = sx[ga], za = sz[ga], xb = sx[gb], zb = sz[gb];
+                racc ^= apply_gate(KIND, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za; sx[gb] = xb; sz[gb] = zb;
+            } else {
+                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                const bool two = gb != ga;
+                if (two) { xb = sx[gb]; zb = sz[gb]; }
+                racc ^= apply_gate(gk, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za;
+                if (two) { sx[gb] = xb; sz[gb] = zb; }
+            }
+        }
+    }
+}
+
 // A layer whose noise events overflowed their slots: every draw of the layer
 // evaluated again (kept out of line: the common path needs none of this).
 __device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t count, const Thr *thr,
@@ -296,26 +333,15 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         const Layer L = a.P.layers[l];
         // gates: packed items through the read-only path, next item prefetched
         const uint2 *__restrict__ it = reinterpret_cast<const uint2 *>(a.P.sitems + L.first);
-        // items in groups of 4 per thread, all four loaded before any is used
-        for (uint32_t i0 = threadIdx.x; i0 < L.count; i0 += 4 * blockDim.x) {
-            uint2 v[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t i = i0 + k * blockDim.x;
-                v[k] = i < L.count ? __ldg(it + i) : make_uint2(0u, 0u);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t ga = v[k].x & 0xffffu, gb = v[k].x >> 16, gk = v[k].y;
-                if (gk) {
-                    uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
-                    const bool two = gb != ga;
-                    if (two) { xb = sx[gb]; zb = sz[gb]; }
-                    racc ^= apply_gate(gk, xa, za, xb, zb);
-                    sx[ga] = xa; sz[ga] = za;
-                    if (two) { sx[gb] = xb; sz[gb] = zb; }
-                }
-            }
+        // items in groups of 4 per thread, all four loaded before any is used;
+        // layers made of one gate kind (every layer of a surface-code round)
+        // run a loop specialised to it
+        switch (L.uniform) {
+        case STAB_H: gate_items<STAB_H>(it, L.count, sx, sz, racc); break;
+        case STAB_CX: gate_items<STAB_CX>(it, L.count, sx, sz, racc); break;
+        case STAB_CZ: gate_items<STAB_CZ>(it, L.count, sx, sz, racc); break;
+        case STAB_S: gate_items<STAB_S>(it, L.count, sx, sz, racc); break;
+        default: gate_items<0>(it, L.count, sx, sz, racc); break;
         }
         __syncthreads();
         if (L.n_noisy) {
