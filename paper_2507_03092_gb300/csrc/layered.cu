@@ -294,11 +294,21 @@ __device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t co
     return racc;
 }
 
+constexpr uint32_t RUN_STAGE = 16;       // layers of a run whose descriptors are staged
 __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t sred[32];
+    __shared__ Layer s_layer[RUN_STAGE];
+    __shared__ uint32_t s_evc[RUN_STAGE];
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW;
     const uint32_t w = blockIdx.x, t = blockIdx.y;
+    // the run's first layers (descriptors and noise-event counts), staged
+    // while the slice loads
+    if (threadIdx.x < min(RUN_STAGE, g.l1 - g.l0)) {
+        const uint32_t l = g.l0 + threadIdx.x;
+        s_layer[threadIdx.x] = a.P.layers[l];
+        s_evc[threadIdx.x] = a.ev_cnt ? a.ev_cnt[(size_t)t * a.P.n_layers + l] : 0u;
+    }
     uint32_t *sx = smem, *sz = smem + n;
     uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
     uint32_t *rm = a.rm + t * a.rm_stride;
@@ -330,8 +340,17 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         __syncthreads();          // every flip has read its pre-gate word
     }
     for (uint32_t l = g.l0; l < g.l1; l++) {
-        const Layer L = a.P.layers[l];
-        // gates: packed items through the read-only path, next item prefetched
+        const bool staged = l - g.l0 < RUN_STAGE;
+        const Layer L = staged ? s_layer[l - g.l0] : a.P.layers[l];
+        // the layer's Pauli errors (a few dozen at most per layer, normally):
+        // counts staged above, one event per thread loaded before the gates run
+        uint32_t ecnt = 0, my_ev = 0;
+        if (L.n_noisy) {
+            ecnt = staged ? s_evc[l - g.l0] : a.ev_cnt[(size_t)t * a.P.n_layers + l];
+            if (ecnt <= L.ev_cap && threadIdx.x < ecnt)
+                my_ev = a.ev[(size_t)t * a.P.ev_total + L.ev_off + threadIdx.x];
+        }
+        // gates: packed items through the read-only path
         const uint2 *__restrict__ it = reinterpret_cast<const uint2 *>(a.P.sitems + L.first);
         // items in groups of 4 per thread, all four loaded before any is used;
         // layers made of one gate kind (every layer of a surface-code round)
@@ -346,10 +365,11 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         __syncthreads();
         if (L.n_noisy) {
             // the layer's Pauli errors act after its gates
-            const uint32_t cnt = a.ev_cnt[(size_t)t * a.P.n_layers + l];
+            const uint32_t cnt = ecnt;
             if (cnt <= L.ev_cap) {
+                if (threadIdx.x < cnt) racc ^= xz_flip(my_ev >> 30, sx[my_ev & 0x3fffffffu], sz[my_ev & 0x3fffffffu]);
                 const uint32_t *ev = a.ev + (size_t)t * a.P.ev_total + L.ev_off;
-                for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+                for (uint32_t e = threadIdx.x + blockDim.x; e < cnt; e += blockDim.x) {
                     const uint32_t v = ev[e], q = v & 0x3fffffffu;
                     racc ^= xz_flip(v >> 30, sx[q], sz[q]);
                 }
