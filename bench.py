@@ -277,6 +277,9 @@ def main():
     d, p = args.d, args.p
     circ = C.surface_code_memory(d, p=p)
     ops_per_step = C.gate_measure_ops(circ)
+    kinds_ = circ.ops["kind"]
+    n_gates = int(np.count_nonzero(np.isin(kinds_, C.ONE_QUBIT_GATES + C.TWO_QUBIT_GATES)))
+    n_meas_ops = int(np.count_nonzero(np.isin(kinds_, (C.M, C.R, C.MPP))))
     K, W = args.steps, args.warmup
     shots_idx = shot_indices(rank, K, W)
     coins, noise = S.streams_for(circ, 0, shots_idx)
@@ -421,6 +424,9 @@ def main():
         "e2e": {"value": e2e_val, "unit": "ops/s",
                 "h2d_bytes_per_step": int(coins[0].nbytes + noise[0].nbytes),
                 "d2h_bytes_per_step": int(circ.record_words * 8)},
+        "rates": {"gates_per_s": n_gates * world * K / t_dev, "measurements_per_s": n_meas_ops * world * K / t_dev,
+                  "shots_per_s": world * K / t_dev,
+                  "note": "gates: H/S/X/Y/Z/CX/CZ/SWAP ops; measurements: M and R ops (both Z measurements)"},
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,

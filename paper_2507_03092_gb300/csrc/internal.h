@@ -206,7 +206,13 @@ struct LaunchCfg {
 // Overflowing a list is handled by slower fallback loops; tests shrink the
 // capacities (STAB_WAVE_CAPS="pcap,wcap,paircap,jcap,budget") to exercise them.
 struct WaveCaps {
-    static constexpr uint32_t PCAP_MAX = 8192, WCAP_MAX = 1024, PAIRCAP_MAX = 4096, JCAP_MAX = 4096;
+    // Maxima size k_meas_rand's shared memory, which shares each SM's 256 KB
+    // with its L1 cache: smaller lists leave more L1 for the kernel's global
+    // data (measured on GB300, d = 71: 8192/4096/4096 -> 4096/2048/2048 entries
+    // is 3 % faster per step).  A wave's rowsum pairs are bounded by the mark
+    // budget below, so PAIRCAP_MAX = mark_budget loses nothing; larger lists
+    // only fall back to slower loops when they overflow.
+    static constexpr uint32_t PCAP_MAX = 4096, WCAP_MAX = 1024, PAIRCAP_MAX = 2048, JCAP_MAX = 2048;
     uint32_t pcap = PCAP_MAX;          // pending measurements considered per wave
     uint32_t wcap = WCAP_MAX;          // measurements applied per wave
     uint32_t paircap = PAIRCAP_MAX;    // (row, pivot) rowsum pairs listed per wave

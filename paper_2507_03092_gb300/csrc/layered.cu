@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         }
     }
     // sign flips: XOR-reduce over the CTA, one plain update per slice
-    for (int o = 16; o; o >>= 1) racc ^= __shfl_xor_sync(FULL_MASK, racc, o);
+    racc = __reduce_xor_sync(FULL_MASK, racc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sred[warp] = racc;
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     __syncthreads();
     if (warp == 0) {
         uint32_t v = lane < nw ? sred[lane] : 0u;
-        for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(FULL_MASK, v, o);
+        v = __reduce_xor_sync(FULL_MASK, v);
         if (lane == 0) {
             a.r[(size_t)t * CW + w] ^= v;
             dirty[w] = 0;
@@ -588,10 +588,8 @@ __device__ int det_outcome_warp(const uint32_t *__restrict__ rm, uint32_t RS, ui
             ok &= (Xp[c] == 0u) && (Zp[c] == wantz);
         }
     }
-    for (int o = 16; o; o >>= 1) {
-        acc += __shfl_xor_sync(FULL_MASK, acc, o);
-        rsum += __shfl_xor_sync(FULL_MASK, rsum, o);
-    }
+    acc = __reduce_add_sync(FULL_MASK, acc);
+    rsum = __reduce_add_sync(FULL_MASK, rsum);
     const int e = (acc + 2 * rsum) & 3;
     if (!__all_sync(FULL_MASK, ok)) set_err(err, DERR_BAD_PRODUCT);
     if (e & 1) set_err(err, DERR_ODD_PHASE);
@@ -643,7 +641,7 @@ __device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ co
             const uint32_t w = w0 + 32 * k + lane;
             if (mine == 0xffffffffu && w >= H && v[k]) mine = 32 * (w - H) + __ffs(v[k]) - 1;
         }
-        for (int o = 16; o; o >>= 1) mine = min(mine, __shfl_xor_sync(FULL_MASK, mine, o));
+        mine = __reduce_min_sync(FULL_MASK, mine);
         if (pv == 0xffffffffu) pv = mine;
         uint32_t x = c;
         for (int o = 1; o < 32; o <<= 1) {
@@ -709,7 +707,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
     if (a.stats) {
         uint32_t k = 0;
         for (uint32_t w = lane; w < H; w += 32) k += __popc(col[w]);
-        for (int o = 16; o; o >>= 1) k += __shfl_xor_sync(FULL_MASK, k, o);
+        k = __reduce_add_sync(FULL_MASK, k);
         if (lane == 0) {
             count(a, DC_DET, 1);
             count(a, DC_SUM_K, k);
@@ -786,7 +784,7 @@ __device__ __forceinline__ void rowsum_warp(uint32_t *rm, uint32_t RS, uint32_t 
             }
         }
     }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);   // (keeps k_meas_rand spill-free)
     if (lane == 0) {
         const uint32_t r_s = rwords & 1u, r_p = rwords >> 1;
         const int e = (int)(2 * r_s + 2 * r_p) + acc;
@@ -815,7 +813,7 @@ __device__ __forceinline__ void rowsum_warp_sparse(uint32_t *rm, uint32_t RS, ui
     int acc = phase_word(xp0, zp0, xs0, zs0) + phase_word(xp1, zp1, xs1, zs1);
     if (in0) { rs[c0] = xs0 ^ xp0; rs[Hr + c0] = zs0 ^ zp0; }
     if (in1) { rs[c1] = xs1 ^ xp1; rs[Hr + c1] = zs1 ^ zp1; }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);   // (keeps k_meas_rand spill-free)
     if (lane == 0) {
         const uint32_t r_s = rwords & 1u, r_p = rwords >> 1;
         const int e = (int)(2 * r_s + 2 * r_p) + acc;
@@ -1451,13 +1449,13 @@ __global__ void k_cond(LArgs a, uint32_t layer) {
         if (P == 1u) v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, q, true) : qz[(size_t)w * n + q];
         else v ^= dty ? rm_col_word(rm, a.RS, a.Hr, w, q, false) : qx[(size_t)w * n + q];
     }
-    for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(FULL_MASK, v, o);
+    v = __reduce_xor_sync(FULL_MASK, v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sred[warp] = v;
     __syncthreads();
     if (warp == 0) {
         uint32_t u = lane < nw ? sred[lane] : 0u;
-        for (int o = 16; o; o >>= 1) u ^= __shfl_xor_sync(FULL_MASK, u, o);
+        u = __reduce_xor_sync(FULL_MASK, u);
         if (lane == 0 && u) a.r[(size_t)t * CW + w] ^= u;
     }
 }
@@ -1612,7 +1610,7 @@ __global__ void __launch_bounds__(256) k_commute(const uint32_t *__restrict__ qx
     }
 #pragma unroll
     for (uint32_t t = 0; t < CT; t++)
-        for (int o = 16; o; o >>= 1) acc[t] ^= __shfl_xor_sync(FULL_MASK, acc[t], o);
+        acc[t] = __reduce_xor_sync(FULL_MASK, acc[t]);
     if (lane != 0) return;
     // output: per Pauli [destabilizer half | stabilizer half], 2 Wq uint32 words each
     uint32_t *o = out + (size_t)k * 4 * Wq;

@@ -60,10 +60,8 @@ __device__ uint32_t res_det_warp(uint32_t n, uint32_t H, uint32_t CW, const uint
         bad |= px | (pz ^ (j == a ? 1u : 0u));
     }
     for (uint32_t w = lane; w < H; w += 32) acc += 2 * __popc(r[H + w] & K[w]);
-    for (int o = 16; o; o >>= 1) {
-        acc += __shfl_xor_sync(FULL_MASK, acc, o);
-        bad |= __shfl_xor_sync(FULL_MASK, bad, o);
-    }
+    acc = __reduce_add_sync(FULL_MASK, acc);
+    bad = __reduce_or_sync(FULL_MASK, bad);
     if (lane == 0) {
         if (acc & 1) set_err(err, DERR_ODD_PHASE);
         if (bad) set_err(err, DERR_BAD_PRODUCT);
@@ -164,10 +162,8 @@ __device__ uint32_t res_measure(const GroupCtx &g, uint32_t n, uint32_t H, uint3
             bad |= px | (pz ^ (j == a ? 1u : 0u));
         }
         for (uint32_t w = g.gtid; w < H; w += g.G) acc += 2 * __popc(r[H + w] & K[w]);
-        for (int o = 16; o; o >>= 1) {
-            acc += __shfl_xor_sync(FULL_MASK, acc, o);
-            bad |= __shfl_xor_sync(FULL_MASK, bad, o);
-        }
+        acc = __reduce_add_sync(FULL_MASK, acc);
+        bad = __reduce_or_sync(FULL_MASK, bad);
         if ((g.gtid & 31) == 0) {
             atomicAdd(&misc[1], (uint32_t)acc);
             if (bad) misc[2] = 1;
@@ -274,10 +270,8 @@ __device__ uint32_t res_measure_mpp(const GroupCtx &g, uint32_t n, uint32_t H, u
             acc -= (int)(px & pz);
         }
         for (uint32_t w = g.gtid; w < H; w += g.G) acc += 2 * __popc(r[H + w] & K[w]);
-        for (int o = 16; o; o >>= 1) {
-            acc += __shfl_xor_sync(FULL_MASK, acc, o);
-            bad |= __shfl_xor_sync(FULL_MASK, bad, o);
-        }
+        acc = __reduce_add_sync(FULL_MASK, acc);
+        bad = __reduce_or_sync(FULL_MASK, bad);
         if ((g.gtid & 31) == 0) {
             atomicAdd(&misc[1], (uint32_t)acc);
             if (bad) misc[2] = 1;
