@@ -1742,7 +1742,14 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
         b.rm_valid = hp.grm_after;
     } else {
         e = cudaStreamBeginCapture(gsl->gs, cudaStreamCaptureModeThreadLocal);
-        if (e) return e;
+        if (e) {
+            // no capture on this stream: run the launches plainly on it instead
+            cudaGetLastError();
+            e = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats);
+            if (!e) e = cudaEventRecord(gsl->out, gsl->gs);
+            if (!e) e = cudaStreamWaitEvent(s, gsl->out, 0);
+            return e;
+        }
         const unsigned long long n0 = kp ? kp->launches : 0;
         const cudaError_t ei = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats);
         cudaGraph_t g = nullptr;
