@@ -133,11 +133,10 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     const size_t sup_b = 2 * (size_t)SUPCAP * items;
     const size_t pwl_b = 2 * (size_t)WaveCaps::WCAP_MAX * PWCAP * count;
     const size_t flips_b = 4 * 2 * items;
-    const size_t detz_b = 4 * (size_t)32 * 2 * p.H * count;
     const size_t ev_b = 4 * (size_t)std::max<uint32_t>(1, p.dev.ev_total) * count;
     const size_t cnt_b = 4 * (size_t)std::max<size_t>(1, p.layers.size()) * count;
     const size_t bytes = up(4 * words) + up(2 * items) + up(first_b) + up(ev_b) + up(cnt_b) +
-                         up(qmap_b) + up(detz_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b) + up(pwl_b) +
+                         up(qmap_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b) + up(pwl_b) +
                          up(flips_b) + up(cnt_b) + up(sizeof(CallArgs));
     int rc = buf.ensure(bytes);
     if (rc) return rc;
@@ -149,7 +148,6 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     ms.ev = (uint32_t *)b; b += up(ev_b);
     ms.ev_cnt = (uint32_t *)b; b += up(cnt_b);
     ms.qmap = (int *)b; b += up(qmap_b);
-    ms.detz = (uint32_t *)b; b += up(detz_b);
     ms.mpiv = (uint32_t *)b; b += up(piv_b);
     ms.mbsz = (uint32_t *)b; b += up(bsz_b);
     ms.mstale = (uint8_t *)b; b += up(stale_b);

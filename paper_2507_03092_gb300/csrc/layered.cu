@@ -70,7 +70,6 @@ struct LArgs {
     uint8_t *mstat, *mout;
     unsigned long long m_stride;     // items per tableau
     int *first, *qmap;               // [B][64H], [B][n]
-    uint32_t *detz;                  // [B][32][2H]
     uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
     uint32_t *mpiv, *mbsz;           // [B][max_meas] cached pivot / column size
     uint8_t *mstale;                 // [B][max_meas]
@@ -892,7 +891,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // qubit -> item map: shared memory when n is small enough, else global
     int *qmap = n <= QMAP_SMEM_MAX ? (int *)(smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW)
                                    : a.qmap + (size_t)t * n;
-    uint32_t *detz = a.detz + (size_t)t * 32 * 2 * H + (size_t)warp * 2 * H;
     uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
     uint8_t *const gmstale = a.mstale + t * a.m_stride;
     uint16_t *msup = a.msup + t * a.m_stride * SUPCAP;
@@ -1531,7 +1529,6 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err)
         a.m_stride = std::max<uint32_t>(1, p->dev.max_meas);
         a.first = ms->first;
         a.qmap = ms->qmap;
-        a.detz = ms->detz;
         a.ev = ms->ev;
         a.ev_cnt = ms->ev_cnt;
         a.mpiv = ms->mpiv;
