@@ -176,7 +176,14 @@ int stab_commute(stab_ctx *ctx, uint32_t index, const uint64_t *d_px, const uint
 
 /* ---- sample(shots, streams) -> records: every shot from |0...0> ---- */
 
-/* d_record: device [shots][record_words] uint64, overwritten. */
+/* d_record: device [shots][record_words] uint64, overwritten.  Asynchronous
+ * on the context's stream.  On the layered engine the call's launch sequence
+ * is captured once per (circuit, batch shape) into a CUDA graph, run on an
+ * internal stream ordered after and before the context's stream by events,
+ * and replayed on later calls (the streams and record pointer are copied to
+ * device memory for each call, so the caller may reuse its stab_streams at
+ * once); while per-launch profiling is on (stab_profile) the kernels are
+ * launched one by one instead.  Engine choice for STAB_ENGINE_AUTO: see above. */
 int stab_sample(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, const stab_streams *streams,
                 uint64_t *d_record, uint64_t record_words, uint32_t engine);
 /* Same with HOST buffers: copies coins/noise to the device, runs, copies the
