@@ -1065,46 +1065,74 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         PHASE(3);
         const uint32_t kend = s_kend;
         // ---- (5) mark rows with the earliest window op holding them in its
-        // column, and pivot rows with the earliest window op pivoting on them
+        // column, and pivot rows with the earliest window op pivoting on them.
+        // Ops with a listed support (<= SUPCAP rows) go 4 to a warp, 8 lanes
+        // each; larger columns take a whole warp.
+        {
+            const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
+            for (uint32_t k0 = (uint32_t)warp * 4; k0 < kend; k0 += (uint32_t)nw * 4) {
+                const uint32_t k = k0 + sub;
+                if (k >= kend || piv[k] == NOPIV || bsz[k] > SUPCAP) continue;
+                const uint32_t i = pend[k];
+                if (sl == 0) atomicMin(&firstp[32 * H + piv[k]], stamp | k);
+                const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                for (uint32_t e = sl; e < bsz[k]; e += 8) atomicMin(&first[sp[e]], stamp | k);
+            }
+        }
         for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
-            if (piv[k] == NOPIV) continue;
+            if (piv[k] == NOPIV || bsz[k] <= SUPCAP) continue;
             const uint32_t i = pend[k];
             if (lane == 0) atomicMin(&firstp[32 * H + piv[k]], stamp | k);
-            if (bsz[k] <= SUPCAP) {
-                const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                for (uint32_t e = lane; e < bsz[k]; e += 32) atomicMin(&first[sp[e]], stamp | k);
-            } else {
-                const uint32_t *col = cols + (size_t)i * CW;
-                for (uint32_t w = lane; w < CW; w += 32) {
-                    uint32_t m = col[w];
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        atomicMin(&first[32 * w + b], stamp | k);
-                    }
+            const uint32_t *col = cols + (size_t)i * CW;
+            for (uint32_t w = lane; w < CW; w += 32) {
+                uint32_t m = col[w];
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    atomicMin(&first[32 * w + b], stamp | k);
                 }
             }
         }
         __syncthreads();
         PHASE(4);
         // ---- (6) select op k when no earlier window op pivots on a row of its
-        // column and no earlier window op's column holds its pivot row
+        // column and no earlier window op's column holds its pivot row (same
+        // split: 8 lanes per listed-support op, a warp per larger column)
+        {
+            const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
+            for (uint32_t k0 = (uint32_t)warp * 4; k0 < kend; k0 += (uint32_t)nw * 4) {   // warp-uniform
+                const uint32_t k = k0 + sub;
+                const bool active = k < kend && piv[k] != NOPIV && bsz[k] <= SUPCAP;
+                bool ok = true;
+                uint32_t i = 0;
+                if (active) {
+                    i = pend[k];
+                    const uint32_t me = stamp | k;
+                    const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                    for (uint32_t e = sl; e < bsz[k]; e += 8) ok &= firstp[sp[e]] >= me;
+                    if (sl == 0) ok &= first[32 * H + piv[k]] == me;
+                }
+                const uint32_t bal = __ballot_sync(FULL_MASK, ok);
+                if (active && sl == 0 && ((bal >> (8 * sub)) & 0xffu) == 0xffu) {
+                    const uint32_t idx = atomicAdd(&s_nsel, 1u);
+                    if (idx < wcap) {
+                        sel[idx] = (uint16_t)k;
+                        stat[i] = MS_WAVE;
+                    }
+                }
+            }
+        }
         for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
-            if (piv[k] == NOPIV) continue;
+            if (piv[k] == NOPIV || bsz[k] <= SUPCAP) continue;
             const uint32_t i = pend[k], me = stamp | k;
             bool ok = true;
-            if (bsz[k] <= SUPCAP) {
-                const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                for (uint32_t e = lane; e < bsz[k]; e += 32) ok &= firstp[sp[e]] >= me;
-            } else {
-                const uint32_t *col = cols + (size_t)i * CW;
-                for (uint32_t w = lane; w < CW; w += 32) {
-                    uint32_t m = col[w];
-                    while (m && ok) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        ok = firstp[32 * w + b] >= me;
-                    }
+            const uint32_t *col = cols + (size_t)i * CW;
+            for (uint32_t w = lane; w < CW; w += 32) {
+                uint32_t m = col[w];
+                while (m && ok) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    ok = firstp[32 * w + b] >= me;
                 }
             }
             if (lane == 0) ok &= first[32 * H + piv[k]] == me;
