@@ -872,7 +872,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t s_wt[32];
-    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any;
+    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any, s_nstale;
     __shared__ uint32_t s_tt;
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
     const uint32_t t = blockIdx.x;
@@ -1008,26 +1008,53 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
         // ---- (2) pivots and supports of the examined ops (cached; recomputed
-        // for ops whose column an earlier wave changed)
-        for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
-            const uint32_t i = pend[k];
-            uint32_t pv, bs;
-            if (!mstale[i]) {
-                pv = mpiv[i];
-                bs = mbsz[i];
-            } else {
+        // for ops whose column an earlier wave changed).  Cached ones are read
+        // a thread per op and the stale ones listed (in `pairs`, unused until
+        // the lists below); the warps then share out the rescans.
+        auto take_pivot = [&](uint32_t k, uint32_t pv, uint32_t bs) {
+            piv[k] = pv == 0xffffffffu ? NOPIV : (uint16_t)pv;
+            bsz[k] = (uint16_t)min(bs, 65535u);
+            if (pv != 0xffffffffu) { atomicMin(&s_firstrand, k); atomicAdd(&s_nrand, 1u); }
+        };
+        if (nlook <= PAIRCAP) {
+            if (threadIdx.x == 0) s_nstale = 0;
+            __syncthreads();
+            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+                const uint32_t i = pend[k];
+                if (mstale[i]) pairs[atomicAdd(&s_nstale, 1u)] = k;
+                else take_pivot(k, mpiv[i], mbsz[i]);
+            }
+            __syncthreads();
+            const uint32_t nst = s_nstale;
+            for (uint32_t x = (uint32_t)warp; x < nst; x += (uint32_t)nw) {
+                const uint32_t k = pairs[x], i = pend[k];
+                uint32_t pv, bs;
                 warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
                 if (lane == 0) {
                     mpiv[i] = pv;
                     mbsz[i] = bs;
                     mstale[i] = 0;
                     count(a, DC_PIV_RECOMP, 1);
+                    take_pivot(k, pv, bs);
                 }
             }
-            if (lane == 0) {
-                piv[k] = pv == 0xffffffffu ? NOPIV : (uint16_t)pv;
-                bsz[k] = (uint16_t)min(bs, 65535u);
-                if (pv != 0xffffffffu) { atomicMin(&s_firstrand, k); atomicAdd(&s_nrand, 1u); }
+        } else {
+            for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
+                const uint32_t i = pend[k];
+                uint32_t pv, bs;
+                if (!mstale[i]) {
+                    pv = mpiv[i];
+                    bs = mbsz[i];
+                } else {
+                    warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
+                    if (lane == 0) {
+                        mpiv[i] = pv;
+                        mbsz[i] = bs;
+                        mstale[i] = 0;
+                        count(a, DC_PIV_RECOMP, 1);
+                    }
+                }
+                if (lane == 0) take_pivot(k, pv, bs);
             }
         }
         __syncthreads();
