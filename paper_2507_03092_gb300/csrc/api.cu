@@ -128,7 +128,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     const size_t mm = std::max<uint32_t>(1, p.dev.max_meas);
     const size_t words = mm * p.CW * count, items = mm * count;
     const size_t first_b = 3 * 4 * (size_t)64 * p.H * count;   // first-B, first-pivot, row claims
-    const size_t qmap_b = 4 * (size_t)p.n * count;
+    const size_t qmap_b = 2 * (size_t)p.n * count;
     const size_t piv_b = 4 * items, bsz_b = 4 * items, stale_b = items;
     const size_t sup_b = 2 * (size_t)SUPCAP * items;
     const size_t pwl_b = 2 * (size_t)WaveCaps::WCAP_MAX * PWCAP * count;
@@ -147,7 +147,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     ms.first = (int *)b; b += up(first_b);
     ms.ev = (uint32_t *)b; b += up(ev_b);
     ms.ev_cnt = (uint32_t *)b; b += up(cnt_b);
-    ms.qmap = (int *)b; b += up(qmap_b);
+    ms.qmap = (uint16_t *)b; b += up(qmap_b);
     ms.mpiv = (uint32_t *)b; b += up(piv_b);
     ms.mbsz = (uint32_t *)b; b += up(bsz_b);
     ms.mstale = (uint8_t *)b; b += up(stale_b);

@@ -173,7 +173,7 @@ struct MeasScratch {
     uint8_t *stat = nullptr;      // [count][max_meas]
     uint8_t *out = nullptr;       // [count][max_meas]
     int *first = nullptr;         // [count][3][64H] wave marking: column rows, pivots, row claims
-    int *qmap = nullptr;          // [count][n] qubit -> item of the current layer
+    uint16_t *qmap = nullptr;     // [count][n] qubit -> item of the current layer (0xffff: none)
     uint32_t *mpiv = nullptr;     // [count][max_meas] cached pivot (slot - 32H) or ~0
     uint32_t *mbsz = nullptr;     // [count][max_meas] cached |x-column support|
     uint8_t *mstale = nullptr;    // [count][max_meas] cache invalid

@@ -69,7 +69,8 @@ struct LArgs {
     unsigned long long cols_stride;  // words per tableau
     uint8_t *mstat, *mout;
     unsigned long long m_stride;     // items per tableau
-    int *first, *qmap;               // [B][64H], [B][n]
+    int *first;                      // [B][3][64H]
+    uint16_t *qmap;                  // [B][n]
     uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
     uint32_t *mpiv, *mbsz;           // [B][max_meas] cached pivot / column size
     uint8_t *mstale;                 // [B][max_meas]
@@ -317,9 +318,28 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     uint8_t *dirty = a.dirty + (size_t)t * CW;
     const bool dty = dirty[w] != 0;
     if (!dty) {
-        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-            sx[j] = qx[(size_t)w * n + j];
-            sz[j] = qz[(size_t)w * n + j];
+        // four words of each plane loaded per thread before any is stored, so
+        // that each thread keeps 32 bytes in flight (one pair at a time keeps
+        // too few bytes in flight per SM to cover the DRAM latency)
+        const uint32_t *__restrict__ gx = qx + (size_t)w * n;
+        const uint32_t *__restrict__ gz = qz + (size_t)w * n;
+        const uint32_t bd = blockDim.x;
+        for (uint32_t j0 = threadIdx.x; j0 < n; j0 += 4 * bd) {
+            uint32_t vx[4], vz[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t j = j0 + k * bd;
+                vx[k] = j < n ? gx[j] : 0u;
+                vz[k] = j < n ? gz[j] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t j = j0 + k * bd;
+                if (j < n) {
+                    sx[j] = vx[k];
+                    sz[j] = vz[k];
+                }
+            }
         }
     } else {
         slice_load_rm(rm, a.RS, a.Hr, H, n, w, [&](uint32_t j, uint32_t x, uint32_t z) {
@@ -834,11 +854,16 @@ constexpr uint16_t NOPIV = 0xffffu;
 constexpr uint32_t QMAP_SMEM_MAX = 16384;   // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
 
-// k_meas_rand's dynamic shared memory: lists, qubit map (when n is small
-// enough) and, last, the sign column (CW words, 16-byte aligned).
+// k_meas_rand's dynamic shared memory: lists, the layer's per-item state when
+// n is small enough (qubit -> item map as 16-bit indices, item status and
+// stale-column flags as bytes; a layer has at most n items) and, last, the
+// sign column (CW words, 16-byte aligned).
+__host__ __device__ __forceinline__ uint32_t rand_item_words(uint32_t n) {
+    return n <= QMAP_SMEM_MAX ? (n + 1) / 2 + 2 * ((n + 3) / 4) : 0u;
+}
 __host__ __device__ __forceinline__ size_t rand_r_offset(uint32_t n, uint32_t H) {
     const size_t bytes = (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H +
-                         (n <= QMAP_SMEM_MAX ? 4 * (size_t)n : 0) + 2 * WCAP + 10 * (size_t)PAIRCAP;
+                         4 * (size_t)rand_item_words(n) + 2 * WCAP + 12 * (size_t)PAIRCAP;
     return ((bytes + 15) & ~(size_t)15) / 4;           // in words
 }
 size_t rand_smem(uint32_t n, uint32_t H) { return 4 * rand_r_offset(n, H) + 8 * (size_t)H + 64; }
@@ -888,9 +913,12 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
     uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
     uint32_t *claim = firstp + 64 * H;                                // first rowsum pair per row
-    // qubit -> item map: shared memory when n is small enough, else global
-    int *qmap = n <= QMAP_SMEM_MAX ? (int *)(smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW)
-                                   : a.qmap + (size_t)t * n;
+    // qubit -> item map, item status and stale flags: shared memory when n is
+    // small enough (status and flags copied in here and back at the end), else
+    // global
+    const bool item_smem = n <= QMAP_SMEM_MAX;
+    uint32_t *const item_w = smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW;
+    uint16_t *qmap = item_smem ? (uint16_t *)item_w : a.qmap + (size_t)t * n;
     uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
     uint8_t *const gmstale = a.mstale + t * a.m_stride;
     uint16_t *msup = a.msup + t * a.m_stride * SUPCAP;
@@ -901,15 +929,17 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint32_t *pairs = (uint32_t *)(sel + WCAP);    // row | sel index << 16
     uint32_t *ents = pairs + PAIRCAP;              // item | sel index << 16 | bp << 31
     uint32_t *qmask = ents + JCAP;                 // destabilizer partners of the wave [CW]
-    uint16_t *pwn = (uint16_t *)(qmask + CW + (n <= QMAP_SMEM_MAX ? n : 0));   // nonzero words per pivot
+    uint16_t *pwn = (uint16_t *)(qmask + CW + rand_item_words(n));   // nonzero words per pivot
     uint32_t *wl_off = (uint32_t *)(pwn + WCAP);   // task offsets of the round's winning pairs [PAIRCAP]
     int *pacc = (int *)(wl_off + PAIRCAP);         // their accumulated powers of i [PAIRCAP]
     uint16_t *wl_e = (uint16_t *)(pacc + PAIRCAP); // chain links of the rowsum pairs [PAIRCAP]
+    uint16_t *phead = wl_e + PAIRCAP;              // each pair's chain head (| 0x8000: dense chain)
     uint16_t *pwl = a.pwl + (size_t)t * WCAP * PWCAP;
     // The sign column lives in shared memory for the whole kernel (copied
     // back at the end).
     uint32_t *r = smem + rand_r_offset(n, H);
-    uint8_t *stat = gstat, *mstale = gmstale;
+    uint8_t *stat = item_smem ? (uint8_t *)(item_w + (n + 1) / 2) : gstat;
+    uint8_t *mstale = item_smem ? (uint8_t *)(item_w + (n + 1) / 2 + (n + 3) / 4) : gmstale;
 
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -922,10 +952,15 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     }
     if (!s_any) return;
     for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) r[w] = gr[w];
-    for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = -1;
+    for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = 0xffffu;
+    if (item_smem)
+        for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+            stat[i] = gstat[i];
+            mstale[i] = gmstale[i];
+        }
     for (uint32_t s = threadIdx.x; s < 3 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (int)i;
+    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
     __syncthreads();
 
     // first[row] holds stamp(wave) | k for the earliest op k of the wave's window
@@ -1224,10 +1259,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     while (mm) {
                         const int b = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const int j = qmap[32 * c + b];
-                        if (j >= 0 && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
+                        const uint32_t j = qmap[32 * c + b];
+                        if (j != 0xffffu && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
                             const uint32_t f = atomicAdd(&s_nent, 1u);
-                            if (f < jcap) ents[f] = (uint32_t)j | (x << 16) | (((xp[k] >> b) & 1u) << 31);
+                            if (f < jcap) ents[f] = j | (x << 16) | (((xp[k] >> b) & 1u) << 31);
                         }
                     }
                     const bool nzw = (xp[k] | zp[k]) != 0u;
@@ -1264,20 +1299,27 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // holding a pivot with more than PWCAP nonzero words go to one warp,
         // which applies them in the same order with the warp rowsums.
         if (npair <= paircap) {
-            uint32_t *head = claim;                    // [64H] first pair of each row, or ~0
+            uint32_t *head = claim;                    // [64H] last pair linked for each row, or ~0
             uint16_t *nxt = wl_e;                      // next pair of the same row, 0xffff ends
             for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
                 const uint32_t old = atomicExch(&head[pairs[e] & 0xffffu], e);
                 nxt[e] = old == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)old;
+                phead[e] = 0xffffu;
             }
             __syncthreads();
-            // chains with a dense pivot are flagged in the head word (bit 31)
+            // the chain heads are the pairs no other pair links to; each head
+            // then gives every pair of its chain the head's index, with bit 15
+            // set when a pivot of the chain is dense (shared memory from here
+            // on: no pass below reads the global head words)
+            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x)
+                if (nxt[e] != 0xffffu) phead[nxt[e]] = 0xfffeu;
+            __syncthreads();
             for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
-                const uint32_t row = pairs[e] & 0xffffu;
-                if (head[row] != e) continue;
+                if (phead[e] != 0xffffu) continue;
                 bool dense = false;
                 for (uint32_t f = e; f != 0xffffu; f = nxt[f]) dense |= pwn[(pairs[f] >> 16) & 0x7fffu] > PWCAP;
-                if (dense) head[row] = e | 0x80000000u;
+                const uint16_t hv = (uint16_t)(e | (dense ? 0x8000u : 0u));
+                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) phead[f] = hv;
             }
             __syncthreads();
             // task offsets: pairs in contiguous chunks per thread
@@ -1285,16 +1327,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             const uint32_t e0 = threadIdx.x * per, e1 = min(npair, e0 + per);
             uint32_t ntask = 0;
             for (uint32_t e = e0; e < e1; e++) {
-                const uint32_t pe = pairs[e];
                 pacc[e] = 0;
-                if (head[pe & 0xffffu] >> 31) continue;
-                ntask += pwn[(pe >> 16) & 0x7fffu];
+                if (phead[e] >> 15) continue;
+                ntask += pwn[(pairs[e] >> 16) & 0x7fffu];
             }
             uint32_t kt = block_excl_scan(ntask, s_wt, &s_tt);
             for (uint32_t e = e0; e < e1; e++) {
-                const uint32_t pe = pairs[e];
                 wl_off[e] = kt;
-                if (!(head[pe & 0xffffu] >> 31)) kt += pwn[(pe >> 16) & 0x7fffu];
+                if (!(phead[e] >> 15)) kt += pwn[(pairs[e] >> 16) & 0x7fffu];
             }
             __syncthreads();
             const uint32_t tott = s_tt;
@@ -1307,7 +1347,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 const uint32_t e = lo - 1;                  // wl_off[0] = 0 <= tk, so lo >= 1
                 const uint32_t pe = pairs[e], row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
                 const uint32_t c = pwl[x * PWCAP + (tk - wl_off[e])];
-                const uint32_t hd = head[row];
+                const uint32_t hd = phead[e];             // not dense: dense chains have no tasks
                 bool first_here = true;
                 for (uint32_t f = hd; f != e; f = nxt[f]) {
                     const uint32_t pf = 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]];
@@ -1331,8 +1371,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             __syncthreads();
             // signs of the sparse chains (head thread); dense chains by warps
             for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
+                if (phead[e] != e) continue;
                 const uint32_t row = pairs[e] & 0xffffu;
-                if (head[row] != e) continue;
                 const uint32_t r_s = rbit(r, row);
                 int ev = (int)(2 * r_s) + pacc[e];
                 for (uint32_t f = e; f != 0xffffu; f = nxt[f])
@@ -1341,8 +1381,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
             }
             for (uint32_t e = (uint32_t)warp; e < npair; e += (uint32_t)nw) {
+                if (phead[e] != (e | 0x8000u)) continue;
                 const uint32_t row = pairs[e] & 0xffffu;
-                if (head[row] != (e | 0x80000000u)) continue;
                 for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
                     const uint32_t x = (pairs[f] >> 16) & 0x7fffu, p = 32 * H + piv[sel[x]];
                     if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
@@ -1485,6 +1525,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
 #undef PHASE
     __syncthreads();
     for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
+    if (item_smem)
+        for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+            gstat[i] = stat[i];
+            gmstale[i] = mstale[i];
+        }
 }
 
 // X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a),

@@ -259,3 +259,29 @@ def test_wave_list_overflow_fallbacks_match_oracle():
         r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and "ok" in r.stdout, (caps, r.stdout[-2000:], r.stderr[-4000:])
+
+
+def test_layered_wide_layer_item_state_in_global_memory(sim):
+    """n = 16 400 > 16 384: the wave kernel keeps the layer's qubit map, item
+    status and stale flags in global memory instead of shared memory, and the
+    one measurement layer of 16 400 ops overflows the 4096-entry pending list
+    (rebuilt from all items).  Bell pairs joined into chains of four make
+    rowsums that touch several rows per random measurement."""
+    n = 16400
+    b = C.Builder(n)
+    for q in range(n):
+        b.gate1(C.H, q)
+    for q in range(0, n, 2):
+        b.gate2(C.CX, q, q + 1)
+    for q in range(1, n - 1, 4):
+        b.gate2(C.CX, q, q + 1)
+    for q in range(0, n, 3):
+        b.gate1(C.S, q)
+    for q in range(n):
+        b.measure(q)
+    circ = b.build()
+    coins, noise = S.streams_for(circ, 5, [0])
+    rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+    orec, otab = _oracle(circ, coins[0], noise[0])
+    assert np.array_equal(rec[0], orec)
+    _assert_tableau_equal(tabs[0], otab, "n=16400")
