@@ -38,9 +38,9 @@ METRIC = "surface-code d=71 gate+measure ops/s"
 # (summaries and commands under profiles/).  A kernel changed since its
 # capture has no entry here (traffic reported as null).
 NCU_TRAFFIC = {
-    "k_meas_rand": {"bytes_per_launch": 616e3,
+    "k_meas_rand": {"bytes_per_launch": 614e3,
                     "source": "profiles/k_meas_rand_d71.md (mean over the 72 launches of a step)"},
-    "k_gate_run": {"bytes_per_launch": 70.4e6,
+    "k_gate_run": {"bytes_per_launch": 70.1e6,
                    "source": "profiles/k_gate_run_d71.md (steady syndrome-round launch)"},
 }
 L2_FLUSH_BYTES = 512 << 20
