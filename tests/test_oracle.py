@@ -590,3 +590,129 @@ def test_mpp_surface_code_flags_errors():
         bits = oracle.record_bits(oracle.run(c, coins, noise), c.n_meas)
         fired += sum(int(np.bitwise_xor.reduce(bits[det])) for det in c.meta["detectors"])
     assert fired > 0
+
+
+# ---------------------------------------------------------------- reorderings the GPU path relies on
+# The layered engine applies a layer's Z measurements out of circuit order:
+# random ones in waves of pairwise-commuting ops, deterministic ones from the
+# layer's starting state, Pauli errors (and the X after a reset) at the end of
+# the layer.  Each rule is checked here on the oracle alone, bit for bit.
+
+def _rows_bits(words, n):
+    return np.unpackbits(words.view(np.uint8).reshape(words.shape[0], -1), axis=1,
+                         bitorder="little")[:, :n].astype(bool)
+
+
+def _random_state(n, seed, n_gates=80):
+    """Tableau after a seeded random H/S/CX circuit from |0...0>."""
+    rng = np.random.default_rng(seed)
+    b = C.Builder(n)
+    for _ in range(n_gates):
+        k = int(rng.integers(3))
+        if k == 2:
+            a, c = (int(v) for v in rng.choice(n, size=2, replace=False))
+            b.gate2(C.CX, a, c)
+        else:
+            b.gate1(C.H if k == 0 else C.S, int(rng.integers(n)))
+    t = oracle.Tableau(n)
+    t.run(b.build())
+    return t.get()
+
+
+def _run_from(state, n, build, coin_bits):
+    """Apply the ops added by ``build(builder)`` to a copy of ``state``; coin k
+    goes to the k-th M.  Returns (record bits, tableau)."""
+    b = C.Builder(n)
+    build(b)
+    circ = b.build()
+    coins = np.zeros(max(1, circ.coin_words), np.uint64)
+    for k, c in enumerate(coin_bits):
+        coins[k >> 6] |= np.uint64(int(c) << (k & 63))
+    t = oracle.Tableau(n)
+    t.set(*state)
+    rec = t.run(circ, coins)
+    return oracle.record_bits(rec, circ.n_meas), t.get()
+
+
+def _pivot(xb, n, a):
+    """First stabilizer row with an X or Y on qubit a (Sec. 2.4), or None."""
+    s = np.nonzero(xb[n:, a])[0]
+    return None if len(s) == 0 else n + int(s[0])
+
+
+def _same_tableau(t1, t2):
+    return all(np.array_equal(u, v) for u, v in zip(t1, t2))
+
+
+def test_commuting_random_measurements_reorder_bit_for_bit():
+    """Two random Z measurements whose pivot rows have no X or Y on each
+    other's qubit leave the same tableau (x, z and every sign) and the same
+    outcomes in either order, for every pair of coins; this is the rule that
+    lets random measurements run in waves.  Pairs that break the condition
+    are not covered by it, and some of them do differ (so the test can
+    fail)."""
+    n = 18
+    n_cond = n_diff = 0
+    for seed in range(10):
+        state = _random_state(n, seed)
+        xb = _rows_bits(state[0], n)
+        for a, b in itertools.permutations(range(n), 2):
+            pa, pb = _pivot(xb, n, a), _pivot(xb, n, b)
+            if pa is None or pb is None or a > b:
+                continue
+            cond = not xb[pa, b] and not xb[pb, a]
+            for ca, cb in itertools.product((0, 1), repeat=2):
+                r1, t1 = _run_from(state, n, lambda B: B.measure(a).measure(b), (ca, cb))
+                r2, t2 = _run_from(state, n, lambda B: B.measure(b).measure(a), (cb, ca))
+                same = _same_tableau(t1, t2) and r1[0] == r2[1] and r1[1] == r2[0]
+                if cond:
+                    assert same, (seed, a, b, ca, cb)
+                    assert (r1[0], r1[1]) == (ca, cb)      # both stay random
+                elif not same:
+                    n_diff += 1
+            n_cond += cond
+    assert n_cond >= 50 and n_diff > 0, (n_cond, n_diff)
+
+
+def test_deterministic_outcomes_fixed_by_the_layer_start():
+    """A Z measurement that is deterministic when its layer starts has the
+    outcome it has when measured alone at the layer start, whatever the
+    layer's other Z measurements (random or not, any coins) do first; this is
+    why all deterministic ops of a layer are resolved from its starting
+    state."""
+    n = 16
+    checked = 0
+    rng = np.random.default_rng(3)
+    for seed in range(12):
+        state = _random_state(n, 100 + seed, n_gates=50)
+        xb = _rows_bits(state[0], n)
+        det = [a for a in range(n) if _pivot(xb, n, a) is None]
+        alone = {a: int(_run_from(state, n, lambda B, a=a: B.measure(a), (0,))[0][0]) for a in det}
+        for _ in range(6):
+            order = [int(q) for q in rng.permutation(n)]
+            coins = rng.integers(0, 2, size=n)
+            bits, _ = _run_from(state, n, lambda B: [B.measure(q) for q in order], coins)
+            for k, q in enumerate(order):
+                if q in alone:
+                    assert int(bits[k]) == alone[q], (seed, q, order)
+                    checked += 1
+    assert checked > 100
+
+
+@pytest.mark.parametrize("pauli", [C.X, C.Y, C.Z])
+def test_pauli_on_another_qubit_commutes_with_measurement(pauli):
+    """A Pauli on qubit c (a noise error, or the X that finishes a reset)
+    and a Z measurement of qubit a != c give the same tableau, bit for bit,
+    and the same outcome in either order; this is why the layered engine
+    applies a layer's Pauli errors and reset flips after its measurements."""
+    n = 12
+    for seed in range(8):
+        state = _random_state(n, 200 + seed, n_gates=40)
+        for a in range(n):
+            for c in range(n):
+                if a == c:
+                    continue
+                for coin in (0, 1):
+                    r1, t1 = _run_from(state, n, lambda B: B.gate1(pauli, c).measure(a), (coin,))
+                    r2, t2 = _run_from(state, n, lambda B: B.measure(a).gate1(pauli, c), (coin,))
+                    assert r1[0] == r2[0] and _same_tableau(t1, t2), (seed, a, c, coin)
