@@ -109,8 +109,8 @@ typedef struct stab_circuit_info {
     uint32_t n_layers;       /* compiled layers (gate layers + measurement layers) */
     uint64_t n_ops;          /* ops excluding NOP/TICK */
     uint64_t n_gates;        /* unitary gates */
-    uint64_t n_meas;         /* M ops = record bits */
-    uint64_t n_coin;         /* M + R ops = coin slots */
+    uint64_t n_meas;         /* M and MPP ops = record bits */
+    uint64_t n_coin;         /* M, R and MPP ops = coin slots */
     uint64_t n_noise_words;  /* noise words one shot reads */
     uint64_t record_words;   /* ceil(n_meas / 64), at least 1 */
     uint64_t coin_words;     /* ceil(n_coin / 64), at least 1 */

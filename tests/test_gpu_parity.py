@@ -285,3 +285,40 @@ def test_layered_wide_layer_item_state_in_global_memory(sim):
     orec, otab = _oracle(circ, coins[0], noise[0])
     assert np.array_equal(rec[0], orec)
     _assert_tableau_equal(tabs[0], otab, "n=16400")
+
+
+def test_layered_largest_n_and_one_past_it(sim):
+    """The layered engine's largest tableau: n such that one 32-row slice (a
+    32-bit x word and z word of every column, 8n bytes) plus 1 KB fits one
+    CTA's opt-in shared memory -- 28 928 qubits on GB300.  A sparse circuit
+    over the whole range (H and CX on 1200 random qubits and the last one,
+    600 of them measured) matches the oracle's records and full tableau; one
+    qubit more is refused before anything runs."""
+    torch = pytest.importorskip("torch")
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
+    n = (optin - 1024) // 8
+    one_more = C.Builder(n + 1).measure(n).build()
+    for bad in (lambda: B.stab_tableau_init(sim.ctx, n + 1, 1),
+                lambda: sim.sample(sim.compile(one_more), one_more, 1, seed=1, engine=B.ENGINE_LAYERED)):
+        with pytest.raises(B.StabError) as e:
+            bad()
+        assert e.value.code == B.ERR_UNSUPPORTED
+    rng = np.random.default_rng(11)
+    qs = [int(q) for q in rng.choice(n - 1, size=1200, replace=False)]
+    b = C.Builder(n)
+    for q in qs:
+        b.gate1(C.H, q)
+    for i in range(0, 1200, 2):
+        b.gate2(C.CX, qs[i], qs[i + 1])
+    for q in qs[:40]:
+        b.gate2(C.CX, q, n - 1)
+    for q in qs[::3]:
+        b.gate1(C.S, q)
+    for q in qs[:600] + [n - 1]:
+        b.measure(q)
+    circ = b.build()
+    coins, noise = S.streams_for(circ, 8, [0])
+    rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
+    orec, otab = _oracle(circ, coins[0], noise[0])
+    assert np.array_equal(rec[0], orec)
+    _assert_tableau_equal(tabs[0], otab, f"n={n}")
