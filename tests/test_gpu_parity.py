@@ -322,3 +322,34 @@ def test_layered_largest_n_and_one_past_it(sim):
     orec, otab = _oracle(circ, coins[0], noise[0])
     assert np.array_equal(rec[0], orec)
     _assert_tableau_equal(tabs[0], otab, f"n={n}")
+
+
+def _resident_bytes(n):
+    """Shared memory of one resident tableau: x and z as [n][2H] words, the
+    sign column, per-row counters [64H], the measured-column snapshot [2H],
+    pivot-row Paulis [n], per-op flag bytes [n] and 8 words of state."""
+    H = (n + 31) // 32
+    CW = 2 * H
+    return 4 * (2 * n * CW + CW + 64 * H + CW + n + (n + 3) // 4 + 8)
+
+
+def test_resident_largest_n_and_one_past_it(sim):
+    """The resident engine's largest tableau (664 qubits on GB300: its shared
+    memory plus 64 bytes fits one CTA's opt-in shared memory) matches the
+    oracle over 8 shots of a random circuit with every op kind; one qubit
+    more is refused before anything runs."""
+    torch = pytest.importorskip("torch")
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
+    n = max(m for m in range(1, 4096) if _resident_bytes(m) + 64 <= optin)
+    one_more = C.random_small_circuit(n + 1, 50, seed=2)
+    with pytest.raises(B.StabError) as e:
+        sim.sample(sim.compile(one_more), one_more, 4, seed=1, engine=B.ENGINE_RESIDENT)
+    assert e.value.code == B.ERR_UNSUPPORTED
+    circ = C.random_small_circuit(n, 4 * n, seed=n)
+    shots = 8
+    coins, noise = S.streams_for(circ, 3, range(shots))
+    cid = sim.compile(circ)
+    rec = B.records_to_numpy(sim.sample(cid, circ, shots, coins, noise, engine=B.ENGINE_RESIDENT))
+    sim.sync()
+    orec, _ = oracle.sample(circ, coins, noise, threads=4)
+    assert np.array_equal(rec, orec)
