@@ -143,6 +143,12 @@ int stab_sync(stab_ctx *ctx);
 int stab_compile(stab_ctx *ctx, uint32_t n, const stab_op *ops, size_t n_ops,
                  const double *params, size_t n_params, uint64_t *circuit_id);
 int stab_circuit_info_get(stab_ctx *ctx, uint64_t circuit_id, stab_circuit_info *out);
+/* Validate and compile a flat op list on the host only -- no context, no
+ * device, nothing kept -- and return what stab_compile would report for it
+ * (layer counts, record, coin and noise sizes).  Arguments and errors as for
+ * stab_compile; *out is written only on success. */
+int stab_compile_info(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
+                      size_t n_params, stab_circuit_info *out);
 int stab_release_circuit(stab_ctx *ctx, uint64_t circuit_id);
 
 /* ---- resident tableaux: tableau_init(n), apply_circuit(...) ---- */

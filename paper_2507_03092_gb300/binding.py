@@ -110,6 +110,7 @@ _SIGS = {
     "stab_sync": (I32, [P]),
     "stab_compile": (I32, [P, U32, P, SZ, P, SZ, PU64]),
     "stab_circuit_info_get": (I32, [P, U64, ctypes.POINTER(CircuitInfo)]),
+    "stab_compile_info": (I32, [U32, P, SZ, P, SZ, ctypes.POINTER(CircuitInfo)]),
     "stab_release_circuit": (I32, [P, U64]),
     "stab_tableau_init": (I32, [P, U32, U32]),
     "stab_apply_circuit": (I32, [P, U64, ctypes.POINTER(Streams), P, U64]),
@@ -218,6 +219,17 @@ def stab_compile(ctx, circ: C.Circuit) -> int:
 def stab_circuit_info_get(ctx, cid) -> dict:
     info = CircuitInfo()
     _check(lib().stab_circuit_info_get(ctx, cid, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def stab_compile_info(circ: C.Circuit) -> dict:
+    """Validate and compile on the host only (no context, no GPU); returns
+    the circuit info stab_compile would report."""
+    ops = np.ascontiguousarray(circ.ops, dtype=C.OP_DTYPE)
+    params = np.ascontiguousarray(circ.params, dtype=np.float64).reshape(-1, 3)
+    info = CircuitInfo()
+    _check(lib().stab_compile_info(int(circ.n), _np_ptr(ops), len(ops), _np_ptr(params), len(params),
+                                   ctypes.byref(info)))
     return info.as_dict()
 
 

@@ -487,6 +487,17 @@ int stab_circuit_info_get(stab_ctx *ctx, uint64_t circuit_id, stab_circuit_info 
     return STAB_OK;
 }
 
+int stab_compile_info(uint32_t n, const stab_op *ops, size_t n_ops, const double *params,
+                      size_t n_params, stab_circuit_info *out) {
+    if (!out) return fail(STAB_ERR_ARG, "out is NULL");
+    HostProg P;                 // host vectors only: nothing reaches the device
+    std::string err;
+    const int rc = compile_program(n, ops, n_ops, params, n_params, P, &err);
+    if (rc) return fail(rc, err);
+    *out = P.info;
+    return STAB_OK;
+}
+
 int stab_release_circuit(stab_ctx *ctx, uint64_t circuit_id) {
     CTX_GUARD;
     auto it = ctx->progs.find(circuit_id);
