@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint8_t *dirty = a.dirty + (size_t)t * CW;
     uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
     uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
-    uint32_t *claim = firstp + 64 * H;                                // first rowsum pair per row
+    uint32_t *claim = firstp + 64 * H;                                // last rowsum pair linked per row
     // qubit -> item map, item status and stale flags: shared memory when n is
     // small enough (status and flags copied in here and back at the end), else
     // global
