@@ -171,11 +171,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ batched vs plain
+C4_T1T2 = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
+C4_DISTANCES = (3, 5, 7, 9, 11)
+
+
 def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
-    T = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
+    T = C4_T1T2
     dists = S.shot_distances(seed, shots)
     groups, keep, circs = [], [], {}
-    for d in (3, 5, 7, 9, 11):
+    for d in C4_DISTANCES:
         cnt = int(np.count_nonzero(dists == d))
         circ = C.surface_code_memory(d, t1t2=T)
         cid = sim.compile(circ)
@@ -224,6 +228,39 @@ def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
             "batched_shots_per_s": batched, "plain_shots_per_s": plain,
             "speedup": batched / plain, "plain_sample_shots": n_plain,
             "tune": {str(k): v for k, v in tunes.items()}}
+
+
+def oracle_batched(shots=4096, per_d=64, seed=0, cores=None):
+    """The batched workload on the CPU oracle: the same circuits and streams
+    (shot s of distance d keyed by (seed + d, s), as the device's seeded mode),
+    a bounded sample of ``per_d`` shots per distance, timed on 1 host thread and
+    on ``cores`` threads (all host cores by default); shots/s over the whole
+    mix, each distance's time scaled by its share of the shots."""
+    import oracle
+    cores = cores or os.cpu_count() or 1
+    dists = S.shot_distances(seed, shots)
+    t1 = tn = 0.0
+    n_sample = 0
+    for d in C4_DISTANCES:
+        cnt = int(np.count_nonzero(dists == d))
+        if cnt == 0:
+            continue
+        k = min(per_d, cnt)
+        circ = C.surface_code_memory(d, t1t2=C4_T1T2)
+        coins, noise = S.streams_for(circ, seed + d, range(k))
+        t0 = time.perf_counter()
+        r1, _ = oracle.sample(circ, coins, noise, threads=1)
+        t1 += (time.perf_counter() - t0) * cnt / k
+        t0 = time.perf_counter()
+        rn, _ = oracle.sample(circ, coins, noise, threads=cores)
+        tn += (time.perf_counter() - t0) * cnt / k
+        if not np.array_equal(r1, rn):
+            raise RuntimeError("oracle records differ between thread counts")
+        n_sample += k
+    return {"kind": "oracle", "one_core_shots_per_s": shots / t1, "all_cores_shots_per_s": shots / tn,
+            "cores": cores,
+            "sample": f"{n_sample} shots ({per_d} per distance) of the {shots}-shot mix, "
+                      f"each distance's time scaled by its share of the shots"}
 
 
 # ------------------------------------------------------------------ ranks
@@ -448,6 +485,11 @@ def main():
             line["batched"] = batched_vs_plain(sim, B, torch)
         except Exception as ex:       # report, do not hide
             line["batched"] = {"error": repr(ex)}
+        if not args.no_cpu:
+            try:
+                line["batched"]["cpu_baseline"] = oracle_batched()
+            except Exception as ex:
+                line["batched"]["cpu_baseline"] = {"error": repr(ex)}
     if rank == 0 and args.serve:
         from paper_2507_03092_gb300 import serve_trace
         line["serve"] = serve_trace.replay(sim, B, torch)

@@ -52,3 +52,11 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     r = _bench(["--steps", "1", "--warmup", "3", "--no-extras", "--no-cpu", "--no-e2e"])
     assert r.returncode != 0
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_batched_oracle_baseline_keys():
+    import bench
+    r = bench.oracle_batched(shots=256, per_d=4, cores=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2
+    assert r["one_core_shots_per_s"] > 0 and r["all_cores_shots_per_s"] > 0
+    assert "20 shots" in r["sample"]
