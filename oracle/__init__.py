@@ -54,10 +54,13 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle library: built from chp.c, or the prebuilt library named by
+    the ORACLE_LIB environment variable (the planted-mistake tests point it at
+    mutated copies of chp.c)."""
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
             P, u32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
             L.chp_new.restype = P
             L.chp_new.argtypes = [u32]

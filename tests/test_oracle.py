@@ -716,3 +716,38 @@ def test_pauli_on_another_qubit_commutes_with_measurement(pauli):
                     r1, t1 = _run_from(state, n, lambda B: B.gate1(pauli, c).measure(a), (coin,))
                     r2, t2 = _run_from(state, n, lambda B: B.measure(a).gate1(pauli, c), (coin,))
                     assert r1[0] == r2[0] and _same_tableau(t1, t2), (seed, a, c, coin)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_reset_error_matches_statevector(n):
+    """RESET_ERROR (reset with the second draw's coin when the first is below
+    T(gamma), then Z when the third is below T(q)) inside random circuits:
+    records equal the statevector's for the same draws.  gamma = q = 1/2
+    makes every branch frequent, and H before some final measurements makes
+    the Z errors visible."""
+    rng = np.random.default_rng(70 + n)
+    for seed in range(12):
+        b = C.Builder(n)
+        for _ in range(40):
+            k = int(rng.integers(6))
+            q = int(rng.integers(n))
+            if k == 0:
+                b.gate1(C.H, q)
+            elif k == 1:
+                b.gate1(C.S, q)
+            elif k == 2 and n > 1:
+                b.gate2(C.CX, q, (q + 1 + int(rng.integers(n - 1))) % n)
+            elif k == 3:
+                b.measure(q)
+            else:
+                b.reset_error(q, 0.5, 0.5)
+        for q in range(n):
+            if rng.integers(2):
+                b.gate1(C.H, q)
+            b.measure(q)
+        circ = b.build()
+        for cs in (seed, seed + 500):
+            coins, noise = _streams(circ, cs)
+            bits = oracle.record_bits(oracle.run(circ, coins, noise), circ.n_meas).tolist()
+            sv_bits, _ = SV.run(circ, coins, noise)
+            assert bits == sv_bits, (n, seed, cs)
