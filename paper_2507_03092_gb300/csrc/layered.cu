@@ -1614,7 +1614,7 @@ void batch_free(Batch &b) {
 static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err) {
     // zeroed bytes, padding included: the graph cache compares LArgs byte for byte
     LArgs a;
-    memset(&a, 0, sizeof a);
+    memset(static_cast<void *>(&a), 0, sizeof a);   // trivially copyable; its members are set below
     a.caps = g_caps;
     if (p) a.P = p->dev;
     a.P.n = b.n; a.P.H = b.H; a.P.CW = b.CW;
