@@ -6,10 +6,11 @@ tableau init, every Clifford layer, noise, measurement and reset.
 
 Prints ONE JSON line: gate+measure ops/s (value: inputs resident in HBM;
 e2e: host buffers through stab_sample_host), the dominant kernel's roofline,
-the CPU oracle on a bounded sample, clocks, kernel launches, and the batched
-(mixed-distance, one persistent launch) vs plain shots/s comparison.
+the CPU oracle on a bounded sample, clocks, kernel launches, the batched
+(mixed-distance, one persistent launch) vs plain shots/s comparison and, at
+N = 1, the 60 s serving trace (p50/p99 latency, shots/s).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--serve]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--serve | --no-serve]
 
 Under torchrun (N > 1) every rank simulates its own shots on its own GPU
 (replicas; no collective on the data path); rank 0 prints the aggregate.
@@ -293,7 +294,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serve", action="store_true", help="also replay the serving trace")
+    ap.add_argument("--serve", action="store_true",
+                    help="replay the serving trace (p50/p99) also when N > 1 (it runs by default at N = 1)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -490,7 +493,7 @@ def main():
                 line["batched"]["cpu_baseline"] = oracle_batched()
             except Exception as ex:
                 line["batched"]["cpu_baseline"] = {"error": repr(ex)}
-    if rank == 0 and args.serve:
+    if rank == 0 and (args.serve or world == 1) and not args.no_serve and not args.no_extras:
         from paper_2507_03092_gb300 import serve_trace
         line["serve"] = serve_trace.replay(sim, B, torch)
     sim.close()
