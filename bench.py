@@ -422,11 +422,12 @@ def main():
     alg = ds["alg_bytes"]
     model = "library model" if alg > 0 else None
     if dom == "k_meas_rand" and counters_prof.get("wave_ops"):
-        # per random measurement: read its column, copy the pivot row into its
-        # destabilizer, write the new stabilizer row (4 row/column transfers);
-        # per rowsum: read the pivot row and the row, write the row (3)
-        alg = (4 * counters_prof["wave_ops"] + 3 * counters_prof["sum_A"]) * row_bytes
-        model = "(4 x random measurements + 3 x rowsums) x 2n/8 bytes"
+        # each needed bit read once and written once: per random measurement
+        # its column (which rows anticommute), the pivot row once, its copy into
+        # the destabilizer and the new stabilizer row (4 row/column transfers);
+        # per rowsum the row read and written (2)
+        alg = (4 * counters_prof["wave_ops"] + 2 * counters_prof["sum_A"]) * row_bytes
+        model = "(4 x random measurements + 2 x rowsums) x 2n/8 bytes"
     if ds["launches"] and alg > 0:
         ach = alg / (ds["total_ms"] / 1e3) / 1e9
         tr = NCU_TRAFFIC.get(dom)
