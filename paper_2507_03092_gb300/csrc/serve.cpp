@@ -205,8 +205,13 @@ int stab_serve_start(stab_ctx *ctx, const stab_serve_config *cfg) {
     const uint32_t ns = std::min<uint32_t>(cfg->n_streams, 256);
     for (uint32_t i = 0; i < ns; i++) {
         auto s = std::make_unique<Slot>();
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return cuda_fail(cudaGetLastError(), "cudaStreamCreate");
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            const cudaError_t e = cudaGetLastError();
+            for (auto &t : S->slots) cudaStreamDestroy(t->stream);   // nothing was launched on them
+            cudaFree(S->counters);
+            delete S;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
         s->counter = S->counters + i;
         s->owner = S;
         S->slots.push_back(std::move(s));
