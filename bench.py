@@ -35,15 +35,39 @@ from paper_2507_03092_gb300 import streams as S  # noqa: E402
 
 METRIC = "surface-code d=71 gate+measure ops/s"
 
-# DRAM bytes (read + write) per launch from one ncu capture of the d=71 step
-# (summaries and commands under profiles/).  A kernel changed since its
-# capture has no entry here (traffic reported as null).
+# DRAM bytes (read + write) per launch from one ncu capture of the d=71 step,
+# valid only while the CUDA source the capture was taken of is unchanged: each
+# entry records the SHA-256 (first 16 hex digits) of the source files, and a
+# kernel whose sources changed since reports traffic null.
 NCU_TRAFFIC = {
-    "k_meas_rand": {"bytes_per_launch": 614e3,
-                    "source": "profiles/k_meas_rand_d71.md (mean over the 72 launches of a step)"},
-    "k_gate_run": {"bytes_per_launch": 70.1e6,
-                   "source": "profiles/k_gate_run_d71.md (steady syndrome-round launch)"},
+    "k_meas_rand": {"bytes_per_launch": 614e3, "src_sha": "",
+                    "tag": "ncu capture, mean over the 72 launches of a d=71 step"},
+    "k_gate_run": {"bytes_per_launch": 70.1e6, "src_sha": "",
+                   "tag": "ncu capture, steady syndrome-round launch"},
 }
+KERNEL_SOURCES = ("paper_2507_03092_gb300/csrc/layered.cu", "paper_2507_03092_gb300/csrc/device_common.cuh",
+                  "paper_2507_03092_gb300/csrc/internal.h")
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """(bytes per launch, tag) of the committed capture, or (None, reason)."""
+    tr = NCU_TRAFFIC.get(kernel)
+    if not tr:
+        return None, "no capture"
+    if tr["src_sha"] != kernel_source_sha():
+        return None, "kernel changed since its ncu capture"
+    return tr["bytes_per_launch"], tr["tag"]
+
+
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -322,6 +346,8 @@ def main():
     kinds_ = circ.ops["kind"]
     n_gates = int(np.count_nonzero(np.isin(kinds_, C.ONE_QUBIT_GATES + C.TWO_QUBIT_GATES)))
     n_meas_ops = int(np.count_nonzero(np.isin(kinds_, (C.M, C.R, C.MPP))))
+    n_m_ops = int(np.count_nonzero(np.isin(kinds_, (C.M, C.MPP))))
+    n_r_ops = int(np.count_nonzero(kinds_ == C.R))
     K, W = args.steps, args.warmup
     shots_idx = shot_indices(rank, K, W)
     coins, noise = S.streams_for(circ, 0, shots_idx)
@@ -430,11 +456,10 @@ def main():
         model = "(4 x random measurements + 2 x rowsums) x 2n/8 bytes"
     if ds["launches"] and alg > 0:
         ach = alg / (ds["total_ms"] / 1e3) / 1e9
-        tr = NCU_TRAFFIC.get(dom)
+        tr, tr_tag = ncu_traffic(dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": src,
-                "traffic": tr["bytes_per_launch"] if tr else None,
-                "traffic_source": tr["source"] if tr else None,
+                "traffic": tr, "traffic_source": tr_tag,
                 "alg_bytes_per_launch": alg / ds["launches"], "alg_model": model,
                 "avg_launch_us": 1e3 * ds["total_ms"] / ds["launches"]}
     else:
@@ -445,12 +470,11 @@ def main():
     gate_roof = None
     if gr and gr["launches"]:
         ach = gr["alg_bytes"] / (gr["total_ms"] / 1e3) / 1e9
-        tr = NCU_TRAFFIC.get("k_gate_run")
+        tr, tr_tag = ncu_traffic("k_gate_run")
         gate_roof = {"kernel": "k_gate_run", "achieved": ach, "peak": hbm, "frac": ach / hbm,
                      "unit": "GB/s", "launches": gr["launches"],
                      "alg_bytes_per_launch": gr["alg_bytes"] / gr["launches"],
-                     "traffic": tr["bytes_per_launch"] if tr else None,
-                     "traffic_source": tr["source"] if tr else None,
+                     "traffic": tr, "traffic_source": tr_tag,
                      "avg_launch_us": 1e3 * gr["total_ms"] / gr["launches"]}
 
     line = {
@@ -468,8 +492,14 @@ def main():
                 "h2d_bytes_per_step": int(coins[0].nbytes + noise[0].nbytes),
                 "d2h_bytes_per_step": int(circ.record_words * 8)},
         "rates": {"gates_per_s": n_gates * world * K / t_dev, "measurements_per_s": n_meas_ops * world * K / t_dev,
+                  "m_per_s": n_m_ops * world * K / t_dev, "r_per_s": n_r_ops * world * K / t_dev,
+                  "gate_plus_m_ops_per_s": (n_gates + n_m_ops) * world * K / t_dev,
                   "shots_per_s": world * K / t_dev,
-                  "note": "gates: H/S/X/Y/Z/CX/CZ/SWAP ops; measurements: M and R ops (both Z measurements)"},
+                  "ops_per_step": {"gates": n_gates, "M": n_m_ops, "R": n_r_ops},
+                  "note": "gates: H/S/X/Y/Z/CX/CZ/SWAP ops; measurements: M and R ops (both Z "
+                          "measurements); an R that directly follows an M on its qubit is folded into "
+                          "that M (deterministic, an X when the outcome is 1), so gate_plus_m_ops_per_s "
+                          "is the rate without resets"},
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,

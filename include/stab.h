@@ -157,11 +157,17 @@ int stab_release_circuit(stab_ctx *ctx, uint64_t circuit_id);
  * (Sec. 2.3; 4n^2+2n bits each, stored twice: column-packed and row-packed). */
 int stab_tableau_init(stab_ctx *ctx, uint32_t n, uint32_t count);
 /* Evolve every resident tableau i through the circuit (tableau i reads stream
- * row / shot i).  d_record: device [count][record_words] uint64, overwritten. */
+ * row / shot i): the paper's sim(circuit) (Sec. 3.1.4, Scheduling Experiment),
+ * with its chunking of independent gates done at compile time; gates by the
+ * Sec. 2.4 Table, measurement and reset by the Sec. 2.4 rules with Appendix B's
+ * rowsum.  d_record: device [count][record_words] uint64, overwritten. */
 int stab_apply_circuit(stab_ctx *ctx, uint64_t circuit_id, const stab_streams *streams,
                        uint64_t *d_record, uint64_t record_words);
-/* Copy resident tableau `index` to host in row-major form: x, z as uint64
- * [2n][ceil(n/64)] (bit j of row i = qubit j), r as uint8 [2n].  Synchronizes. */
+/* Copy resident tableau `index` to host in the row-major form of Sec. 2.3 (The
+ * CHP Formalism: rows 0..n-1 destabilizers, n..2n-1 stabilizers): x, z as
+ * uint64 [2n][ceil(n/64)] (bit j of row i = qubit j), r as uint8 [2n].
+ * Synchronizes.  stab_set_tableau writes one in the same layout (checkpoint /
+ * restore); the caller is responsible for it being a valid tableau. */
 int stab_get_tableau(stab_ctx *ctx, uint32_t index, uint64_t *host_x, uint64_t *host_z,
                      uint8_t *host_r);
 int stab_set_tableau(stab_ctx *ctx, uint32_t index, const uint64_t *host_x,
@@ -182,7 +188,13 @@ int stab_commute(stab_ctx *ctx, uint32_t index, const uint64_t *d_px, const uint
 
 /* ---- sample(shots, streams) -> records: every shot from |0...0> ---- */
 
-/* d_record: device [shots][record_words] uint64, overwritten.  Asynchronous
+/* Shots of a circuit, each from |0...0> (Sec. 2.3 initial tableau) through
+ * sim(circuit) (Sec. 3.1.4), random outcomes read from the coin stream (Sec.
+ * 2.4: "a random phase bit ... is chosen") and Pauli errors injected from the
+ * noise stream (Sec. 2.6, QEC operations; Sec. 2.7, stochastic Pauli
+ * channels); the paper names sampling many shots in parallel on the GPU as
+ * future work (Sec. 6).  Records, coins and noise as in the header comment.
+ * d_record: device [shots][record_words] uint64, overwritten.  Asynchronous
  * on the context's stream.  On the layered engine the call's launch sequence
  * is captured once per (circuit, batch shape) into a CUDA graph, run on an
  * internal stream ordered after and before the context's stream by events,
@@ -193,7 +205,11 @@ int stab_commute(stab_ctx *ctx, uint32_t index, const uint64_t *d_px, const uint
 int stab_sample(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, const stab_streams *streams,
                 uint64_t *d_record, uint64_t record_words, uint32_t engine);
 /* Same with HOST buffers: copies coins/noise to the device, runs, copies the
- * records back, and synchronizes.  host_noise may be NULL for noiseless circuits. */
+ * records back, and synchronizes.  host_noise may be NULL for noiseless circuits.
+ * Arguments as stab_sample's, with host_coins [shots][coin_words] uint64,
+ * host_noise [shots][noise_words] uint32 and host_record [shots][record_words]
+ * uint64 in host memory (pinned memory makes the copies faster).  Errors as
+ * stab_sample's, plus STAB_ERR_OOM if the device staging buffers cannot grow. */
 int stab_sample_host(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots,
                      const uint64_t *host_coins, uint64_t coin_words,
                      const uint32_t *host_noise, uint64_t noise_words,
@@ -218,24 +234,26 @@ typedef struct stab_job_group {
 int stab_sample_batch(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
 
 /* One persistent resident-engine launch like stab_sample_batch's (every group
- * on the resident engine), for callers that cannot allocate device
- * memory at call time: code running where every device allocation is owned by
- * a host framework's pool, or latency-critical loops that cannot afford
+ * on the resident engine), for callers that cannot allocate device memory at
+ * call time: code running where every device allocation is owned by a host
+ * framework's memory pool, or latency-critical loops that cannot afford
  * cudaMalloc's implicit synchronisation.  (The paper has no counterpart; this
  * is a property of this library.)  The resident engine's only global scratch,
  * its job table and work counter, live in a fixed array compiled into the
- * library instead of memory from cudaMalloc: at most 8192 shots in total and 64
- * groups per call (about 0.7 MiB, held on every GPU that loads the library
+ * library instead of memory from cudaMalloc: at most 8192 shots in total and
+ * 64 groups per call (about 0.7 MiB, held on every GPU that loads the library
  * until the process exits); larger batches are rejected with
- * STAB_ERR_UNSUPPORTED before anything is launched.  The call itself allocates
- * nothing (no cudaMalloc, cudaFree or allocating library call); the caller
- * still passes the streams and record buffers, and the circuits must have been
- * compiled before.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current, so make that first
- * call before any stream capture.  Every call shares the array and a host
- * staging buffer: calls whose launches overlap on the GPU, or that run
- * concurrently from several host threads, race; the work counter is cleared by
- * each call before its launch. */
+ * STAB_ERR_UNSUPPORTED before anything is launched.  The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library call): the job table
+ * is written on the device by a small kernel from the call's group list,
+ * passed by value as a kernel argument, so there is no host staging buffer.
+ * The caller still passes the streams and record buffers, and the circuits
+ * must have been compiled before.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls whose launches overlap on the GPU (for instance calls on two
+ * contexts with different streams) race on it; each call clears the work
+ * counter before its launch. */
 int stab_sample_batch_noalloc(stab_ctx *ctx, const stab_job_group *groups, size_t n_groups);
 
 /* Resident-engine launch shape, chosen per qubit-count bucket by the autotuner. */
@@ -252,7 +270,16 @@ int stab_autotune(stab_ctx *ctx, const uint64_t *circuit_ids, size_t n_circuits,
 int stab_get_tune(stab_ctx *ctx, uint32_t n, stab_tune *out);
 int stab_set_tune(stab_ctx *ctx, uint32_t n, const stab_tune *tune);
 
-/* ---- served form: continuous batching with HBM-footprint admission ---- */
+/* ---- served form: continuous batching with HBM-footprint admission ----
+ * The paper has no serving layer; this one runs the same per-shot simulation
+ * as stab_sample (Sec. 2.3-2.4, Sec. 3.1.4) for requests that arrive over
+ * time, toward the Sec. 6 direction of parallel sampling on the GPU.  Requests
+ * are admitted in arrival order when a launch slot is free and their device
+ * footprint fits hbm_budget_bytes; small-tableau requests waiting together
+ * share one resident-engine launch, larger ones get a layered launch sequence,
+ * and each launch runs on its own stream so admitted work overlaps.  A
+ * request's records depend only on (circuit, seed, shot_offset), never on the
+ * mix it was served in. */
 typedef struct stab_serve_config {
     uint64_t hbm_budget_bytes; /* admission limit for resident request state */
     uint32_t max_inflight;     /* concurrently admitted requests (slots) */
@@ -270,6 +297,9 @@ typedef struct stab_request_status {
     double t_done;
 } stab_request_status;
 
+/* Start the request loop (one scheduler thread, n_streams device streams).
+ * Errors: STAB_ERR_ARG (NULL or zero-sized config), STAB_ERR_BUSY (already
+ * started), STAB_ERR_CUDA / STAB_ERR_OOM (stream or counter creation). */
 int stab_serve_start(stab_ctx *ctx, const stab_serve_config *cfg);
 /* Queue a request: `shots` shots of a compiled circuit with SEEDED streams
  * (seed, shot_offset); records land in d_record ([shots][record_words], device,
@@ -277,10 +307,12 @@ int stab_serve_start(stab_ctx *ctx, const stab_serve_config *cfg);
 int stab_serve_submit(stab_ctx *ctx, uint64_t circuit_id, uint32_t shots, uint64_t seed,
                       uint64_t shot_offset, uint64_t *d_record, uint64_t record_words,
                       uint64_t *req_id);
-/* Collect up to `cap` completed requests (non-blocking). */
+/* Collect up to `cap` completed requests (non-blocking); *n_done = number written. */
 int stab_serve_poll(stab_ctx *ctx, stab_request_status *done, size_t cap, size_t *n_done);
 /* Wait until every submitted request completed or `timeout_s` elapsed. */
 int stab_serve_drain(stab_ctx *ctx, double timeout_s);
+/* Stop the loop after the launches in flight finish; queued requests that were
+ * never admitted are dropped.  Frees the loop's streams and device state. */
 int stab_serve_stop(stab_ctx *ctx);
 
 /* ---- instrumentation (benchmarks) ---- */

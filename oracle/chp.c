@@ -45,7 +45,7 @@
  *    scratch <- 0, rowsum(scratch, i+n) for each destabilizer i anticommuting
  *    with P (ascending i); the product must be +-P and the outcome is
  *    r_scratch.  Factors are X (x=1), Y (x=z=1), Z (z=1) on distinct qubits.
- *  - Pauli noise (Sec. 2.6, stochastic Pauli channels): a Pauli P on qubit a
+ *  - Pauli noise (Sec. 2.7, stochastic Pauli channels): a Pauli P on qubit a
  *    flips r on the rows it anticommutes with: X -> z_a, Z -> x_a, Y -> x_a^z_a.
  *    Draw semantics (one uint32 u per noise op): T = floor(p * 2^32);
  *      DEPOLARIZE1(p): error iff u < T, Pauli index (u*3)/T -> X, Y, Z;

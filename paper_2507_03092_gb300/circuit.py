@@ -14,8 +14,8 @@ Workloads (the paper measures only on generated circuits):
 * random Clifford layers on n qubits with mid-circuit Z measurements;
 * the random n-wide, n-round H/S/CX/M/R benchmark (Sec. 4.1, Fig. "random").
 
-Noise channels are the stochastic Pauli channels of Sec. 2.6; the
-Pauli-twirled T1/T2 probabilities (Sec. 2.6, twirling) are computed here on
+Noise channels are the stochastic Pauli channels of Sec. 2.7; the
+Pauli-twirled T1/T2 probabilities (Sec. 2.7, twirling) are computed here on
 the host because they are channel *parameters*, not simulation steps.
 """
 from __future__ import annotations
@@ -327,7 +327,7 @@ def surface_code_memory(d: int, rounds: int | None = None, p: float = 0.0,
 
 def surface_code_mpp(d: int, rounds: int | None = None, p: float = 0.0) -> Circuit:
     """Rotated surface-code Z-memory measured by Pauli products (the
-    lattice-surgery view of Sec. 2.7): d*d data qubits only, every check
+    lattice-surgery view of Sec. 2.8): d*d data qubits only, every check
     measured directly as one MPP of its 2 or 4 corners.
 
     Reset the data; ``rounds`` rounds of DEPOLARIZE1(p) on every data qubit

@@ -23,6 +23,23 @@ int cuda_fail(cudaError_t e, const char *what) {
     return STAB_ERR_CUDA;
 }
 
+void smem_attr_once(int slot, const void *func, int bytes) {
+    static std::mutex mu;
+    static uint64_t done[32];            // bit d of done[slot]: set on device d
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || slot < 0 || slot >= 32) {
+        cudaGetLastError();
+        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[slot] >> dev & 1u) return;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        done[slot] |= 1ull << dev;
+    else
+        cudaGetLastError();
+}
+
 int DevBuf::ensure(size_t bytes) {
     if (bytes <= cap) return STAB_OK;
     release();
@@ -398,11 +415,12 @@ int stab_create(stab_ctx **out, int device, void *cuda_stream) {
     if (const char *env = getenv("STAB_WAVE_CAPS")) {
         WaveCaps c;
         unsigned v[5];
-        unsigned w6 = 0;
-        const int got = sscanf(env, "%u,%u,%u,%u,%u,%u", &v[0], &v[1], &v[2], &v[3], &v[4], &w6);
+        unsigned w6 = 0, w7 = 0;
+        const int got = sscanf(env, "%u,%u,%u,%u,%u,%u,%u", &v[0], &v[1], &v[2], &v[3], &v[4], &w6, &w7);
         if (got >= 5) {
             c.pcap = v[0]; c.wcap = v[1]; c.paircap = v[2]; c.jcap = v[3]; c.mark_budget = v[4];
-            if (got == 6) c.window = w6;
+            if (got >= 6) c.window = w6;
+            if (got >= 7) c.wave_limit = w7;
             set_wave_caps(c);
         }
     }

@@ -27,7 +27,7 @@ static bool is_noise(uint8_t k) { return k == STAB_DEP1 || k == STAB_DEP2 || k =
 static bool is_meas_class(uint8_t k) { return k == STAB_M || k == STAB_R || k == STAB_RESET_ERR; }
 
 // Pauli-product measurement as a Clifford conjugation (the PBC rewriting of
-// Sec. 2.7: a measurement absorbs the Cliffords around it).  U maps the
+// Sec. 2.8: a measurement absorbs the Cliffords around it).  U maps the
 // product P of the factors to +Z on the last factor's qubit t:
 //   X factor: H (X -> Z);  Y factor: Z, S, H (Y -> -Y -> X -> Z);  Z: nothing;
 //   then CX(q_i, t) for every other factor q_i (Z_i Z_t -> Z_t).

@@ -203,7 +203,8 @@ struct LaunchCfg {
 
 // Capacities of the random-measurement wave kernel's shared-memory lists.
 // Overflowing a list is handled by slower fallback loops; tests shrink the
-// capacities (STAB_WAVE_CAPS="pcap,wcap,paircap,jcap,budget") to exercise them.
+// capacities (STAB_WAVE_CAPS="pcap,wcap,paircap,jcap,budget[,window[,wave_limit]]")
+// to exercise them.
 struct WaveCaps {
     // Maxima size k_meas_rand's shared memory, which shares each SM's 256 KB
     // with its L1 cache: smaller lists leave more L1 for the kernel's global
@@ -218,6 +219,10 @@ struct WaveCaps {
     uint32_t jcap = JCAP_MAX;          // measured-column updates listed per wave
     uint32_t mark_budget = 2048;       // rows marked per wave (bounds the window)
     uint32_t window = 128;             // pending measurements examined per wave
+    // Waves allowed per measurement layer before the kernel gives up with a
+    // bounds error (the loop's own bound, 2 x ops + 3, applies as well);
+    // lowered only by tests, to see the guard fire and the context survive.
+    uint32_t wave_limit = 0xffffffffu;
 };
 constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list
 constexpr uint32_t PWCAP = 64;         // nonzero words kept per pivot row
@@ -239,6 +244,11 @@ struct KernelProf {
     void end(Rec &r, cudaStream_t s, double bytes);
     int collect();                            // synchronizes pending events
 };
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per (slot,
+// current device): the attribute is per device, and contexts on several
+// devices or host threads launch the same kernels.  Allocates nothing.
+void smem_attr_once(int slot, const void *func, int bytes);
 
 size_t batch_bytes(uint32_t n, uint32_t count);
 int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err);

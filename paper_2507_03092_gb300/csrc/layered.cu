@@ -980,9 +980,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // cleared and it restarts.
     uint32_t wave = 0;
     // every wave resolves at least one op (the first pending random op always
-    // qualifies), so 2*count+2 waves bound the loop; exceeding it is a bug
+    // qualifies), so 2*count+3 passes bound the loop; exceeding it is a bug
+    const uint32_t glimit = min(2 * M.count + 3, a.caps.wave_limit);
     for (uint32_t guard = 0;; guard++) {
-        if (guard > 2 * M.count + 2) {
+        if (guard >= glimit) {
             if (threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
             break;
         }
@@ -1748,7 +1749,6 @@ cudaError_t layered_commute(Batch &b, uint32_t index, const unsigned long long *
     return cudaGetLastError();
 }
 
-static bool g_attr_set = false;
 WaveCaps g_caps;
 
 void set_wave_caps(const WaveCaps &c) {
@@ -1758,6 +1758,7 @@ void set_wave_caps(const WaveCaps &c) {
     g_caps.jcap = std::min(c.jcap, WaveCaps::JCAP_MAX);
     g_caps.mark_budget = c.mark_budget;
     g_caps.window = std::max(1u, c.window);
+    g_caps.wave_limit = std::max(1u, c.wave_limit);
 }
 
 static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, int *d_err,
@@ -1796,16 +1797,12 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
                         unsigned long long *d_stats, GraphSlot *gsl) {
-    if (!g_attr_set) {
-        cudaFuncSetAttribute(k_gate_run, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(lc.smem_optin - 1024));
-        cudaFuncSetAttribute(k_meas_det, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(lc.smem_optin - 1024));
-        cudaFuncSetAttribute(k_meas_late, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(lc.smem_optin - 1024));
-        cudaFuncSetAttribute(k_meas_rand, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(lc.smem_optin - 1024));
-        g_attr_set = true;
+    {
+        const int lim = (int)(lc.smem_optin - 1024);
+        smem_attr_once(0, (const void *)k_gate_run, lim);
+        smem_attr_once(1, (const void *)k_meas_det, lim);
+        smem_attr_once(2, (const void *)k_meas_late, lim);
+        smem_attr_once(3, (const void *)k_meas_rand, lim);
     }
     // this call's inputs, read by the kernels from device memory (a pageable
     // source is staged before cudaMemcpyAsync returns)

@@ -13,6 +13,7 @@
 #include "ctx.h"
 
 #include <algorithm>
+#include <cstring>
 
 namespace stab {
 
@@ -463,15 +464,11 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, 
     const size_t gw = res_words(max_n);
     const size_t smem = 4 * gw * tpc;
     if (!resident_shape_ok(max_n, tune, lc)) return cudaErrorInvalidConfiguration;
-    static bool attr[5] = {false, false, false, false, false};
     cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), s);
     int occ = 0;
     cudaError_t e = cudaSuccess;
     auto launch = [&](auto kern, int slot) {
-        if (!attr[slot]) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lc.smem_optin);
-            attr[slot] = true;
-        }
+        smem_attr_once(8 + slot, (const void *)kern, (int)lc.smem_optin);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)(G * tpc), smem);
         if (occ < 1) occ = 1;
         uint32_t groups_needed = (n_jobs + tpc - 1) / tpc;
@@ -500,7 +497,10 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n, 
 // The resident engine's global scratch is its job table and its work counter.
 // stab_sample_batch_noalloc keeps both in this file-scope device array instead
 // of memory obtained from cudaMalloc.  Every GPU that loads the library holds
-// the array until the process exits; all calls share it.
+// the array until the process exits; all calls share it.  The job table is
+// written on the device by k_noalloc_jobs from a by-value table of the call's
+// groups (a kernel parameter), so no host staging buffer and no host-to-device
+// copy is involved.
 namespace stab {
 
 constexpr uint32_t NOALLOC_MAX_SHOTS = 8192;
@@ -510,8 +510,35 @@ constexpr size_t NOALLOC_BYTES = NOALLOC_JOBS_OFF + (size_t)NOALLOC_MAX_SHOTS * 
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-// host staging for the job table (shared by all calls, like the device array)
-static ResJob g_noalloc_jobs[NOALLOC_MAX_SHOTS];
+struct NoallocGroup {           // one group with at least one shot
+    const DevProg *prog;
+    DevStreams st;
+    unsigned long long *record;
+    unsigned long long rec_stride;
+    uint32_t first_job, shots;
+};
+struct NoallocTable {
+    uint32_t n_groups, n_jobs;
+    NoallocGroup g[NOALLOC_MAX_GROUPS];
+};
+static_assert(sizeof(NoallocTable) < 32000, "the group table must fit the kernel parameter space");
+
+// Job k of the table: shot (k - first_job) of the group whose range holds k.
+__global__ void k_noalloc_jobs(ResJob *jobs, const __grid_constant__ NoallocTable tab) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < tab.n_jobs; k += gridDim.x * blockDim.x) {
+        uint32_t gi = 0;
+        while (gi + 1 < tab.n_groups && tab.g[gi + 1].first_job <= k) gi++;
+        const NoallocGroup &G = tab.g[gi];
+        ResJob j;
+        j.prog = G.prog;
+        j.st = G.st;
+        j.record = G.record;
+        j.rec_stride = G.rec_stride;
+        j.shot = k - G.first_job;
+        j.pad = 0;
+        jobs[k] = j;
+    }
+}
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static void *g_noalloc_dev[NOALLOC_MAX_DEVICES];   // device address of the array, per device
@@ -562,7 +589,7 @@ extern "C" int stab_sample_batch_noalloc(stab_ctx *ctx, const stab_job_group *gr
                                               std::to_string(NOALLOC_MAX_SHOTS) + " shots per call (got " +
                                               std::to_string(total) + ")");
     if (!total) return STAB_OK;
-    // job table: groups in decreasing cost order (longest shots first)
+    // group table in decreasing cost order (longest shots first), on the stack
     uint32_t order[NOALLOC_MAX_GROUPS];
     uint64_t cost[NOALLOC_MAX_GROUPS];
     for (size_t gi = 0; gi < n_groups; gi++) {          // insertion sort: no temporary buffers
@@ -576,31 +603,29 @@ extern "C" int stab_sample_batch_noalloc(stab_ctx *ctx, const stab_job_group *gr
         order[j] = (uint32_t)gi;
         cost[j] = c;
     }
-    uint32_t k = 0;
+    NoallocTable tab;
+    memset(static_cast<void *>(&tab), 0, sizeof tab);
     for (size_t oi = 0; oi < n_groups; oi++) {
         const stab_job_group &G = groups[order[oi]];
-        const HostProg *p = find_prog(ctx, G.circuit_id);
-        for (uint32_t sh = 0; sh < G.shots; sh++) {
-            ResJob &j = g_noalloc_jobs[k++];
-            j.prog = prog_desc(*p);
-            j.st = to_dev(G.streams);
-            j.record = (unsigned long long *)G.d_record;
-            j.rec_stride = G.record_words;
-            j.shot = sh;
-            j.pad = 0;
-        }
-        if (G.shots) {
-            e = cudaMemsetAsync(G.d_record, 0, (size_t)G.shots * G.record_words * 8, ctx->stream);
-            if (e) return cuda_fail(e, "clearing records");
-        }
+        if (!G.shots) continue;
+        NoallocGroup &T = tab.g[tab.n_groups++];
+        T.prog = prog_desc(*find_prog(ctx, G.circuit_id));
+        T.st = to_dev(G.streams);
+        T.record = (unsigned long long *)G.d_record;
+        T.rec_stride = G.record_words;
+        T.first_job = tab.n_jobs;
+        T.shots = G.shots;
+        tab.n_jobs += G.shots;
+        e = cudaMemsetAsync(G.d_record, 0, (size_t)G.shots * G.record_words * 8, ctx->stream);
+        if (e) return cuda_fail(e, "clearing records");
     }
-    e = cudaMemcpyAsync(base + NOALLOC_JOBS_OFF, g_noalloc_jobs, (size_t)total * sizeof(ResJob),
-                        cudaMemcpyHostToDevice, ctx->stream);
-    if (e) return cuda_fail(e, "copying the job table");
+    ResJob *jobs = (ResJob *)(base + NOALLOC_JOBS_OFF);
+    k_noalloc_jobs<<<(tab.n_jobs + 255) / 256, 256, 0, ctx->stream>>>(jobs, tab);
+    e = cudaGetLastError();
+    if (e) return cuda_fail(e, "writing the job table");
     const stab_tune t = lookup_tune(ctx, max_n);
     // resident_run zeroes the counter (first word of the array) before the launch
-    e = resident_run((const ResJob *)(base + NOALLOC_JOBS_OFF), (uint32_t)total, max_n, t,
-                     (unsigned int *)base, ctx->d_err, ctx->lc, ctx->stream, nullptr);
+    e = resident_run(jobs, tab.n_jobs, max_n, t, (unsigned int *)base, ctx->d_err, ctx->lc, ctx->stream, nullptr);
     if (e) return cuda_fail(e, "resident launch");
     return STAB_OK;
 }

@@ -52,6 +52,89 @@ def test_config2_random_clifford_n1000_200_layers(sim):
     assert st["n_meas_random"] > 10000          # the workload is dominated by random outcomes
 
 
+def _golden(name):
+    import json
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", name)) as fh:
+        return json.load(fh)
+
+
+def _digest(words):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(words, "<u8").tobytes()).hexdigest()
+
+
+def test_config3_d71_noiseless_full_record_matches_golden(sim):
+    """All 362 881 outcomes of the noiseless d=71 circuit, shot 0 of seeds 0
+    and 1 (device-generated seeded streams), against the oracle's records
+    stored as digests by tests/golden/make_golden.py (oracle only)."""
+    circ = C.surface_code_memory(71)
+    cid = sim.compile(circ)
+    for seed in (0, 1):
+        gold = _golden(f"d71_noiseless_seed{seed}.json")
+        rec = B.records_to_numpy(sim.sample(cid, circ, 1, seed=seed, engine=B.ENGINE_LAYERED))
+        sim.sync()
+        assert rec.shape[1] == gold["record_words"]
+        bits = oracle.record_bits(rec, circ.n_meas)[0]
+        assert int(bits.sum()) == gold["ones"], seed
+        assert gold["detectors_fired"] == 0
+        assert _digest(rec[0]) == gold["record_sha256"], seed
+
+
+def _check_serve_golden(recs, gold):
+    for got, req in zip(recs, gold["requests"]):
+        assert got.shape == (req["shots"], req["record_words"]), req["d"]
+        bad = [s for s in range(req["shots"]) if _digest(got[s])[:32] != req["shot_sha256"][s]]
+        assert not bad, (req["d"], bad[:10])
+
+
+def test_config5_largest_requests_match_oracle_alone_and_served(sim):
+    """The largest requests of the serving workload -- d=31 with 256 shots and
+    d=29 with 200 shots, DEPOLARIZE p=1e-3, seeded streams keyed by (request
+    seed, shot) -- through stab_sample and through the serving loop (mixed
+    with smaller requests), every shot's record against the oracle's (digests
+    written by tests/golden/make_golden.py)."""
+    gold = _golden("serve_largest.json")
+    circs = {}
+    for req in gold["requests"]:
+        c = C.surface_code_memory(req["d"], p=1e-3)
+        circs[req["d"]] = (c, sim.compile(c))
+    alone = []
+    for req in gold["requests"]:
+        c, cid = circs[req["d"]]
+        alone.append(B.records_to_numpy(sim.sample(cid, c, req["shots"], seed=req["seed"])))
+        sim.sync()
+    _check_serve_golden(alone, gold)
+    # served: the two largest requests among smaller ones of other distances
+    small = {d: (c := C.surface_code_memory(d, p=1e-3), sim.compile(c)) for d in (3, 9, 17)}
+    bufs, ids, order = [], [], []
+    B.stab_serve_start(sim.ctx, 16 << 30, max_inflight=16, n_streams=4, max_batch_requests=8)
+    try:
+        for k, (d, sh) in enumerate([(3, 40), (9, 17), (17, 5), (3, 100)]):
+            c, cid = small[d]
+            buf = sim.record_buffer(sh, c.record_words)
+            ids.append(B.stab_serve_submit(sim.ctx, cid, sh, 70 + k, 0, buf))
+            bufs.append(buf)
+            order.append(None)
+            if k == 1:
+                for j, req in enumerate(gold["requests"]):
+                    c, cid = circs[req["d"]]
+                    buf = sim.record_buffer(req["shots"], c.record_words)
+                    ids.append(B.stab_serve_submit(sim.ctx, cid, req["shots"], req["seed"], 0, buf))
+                    bufs.append(buf)
+                    order.append(j)
+        B.stab_serve_drain(sim.ctx, timeout_s=600)
+        st = {x["req_id"]: x for x in B.stab_serve_poll(sim.ctx)}
+    finally:
+        B.stab_serve_stop(sim.ctx)
+    assert set(st) == set(ids) and all(x["status"] == 0 for x in st.values())
+    served = [None] * len(gold["requests"])
+    for buf, j in zip(bufs, order):
+        if j is not None:
+            served[j] = B.records_to_numpy(buf)
+    _check_serve_golden(served, gold)
+
+
 def test_config3_d71_noiseless_detectors_all_zero(sim):
     circ = C.surface_code_memory(71)
     cid = sim.compile(circ)

@@ -261,6 +261,61 @@ def test_wave_list_overflow_fallbacks_match_oracle():
         assert r.returncode == 0 and "ok" in r.stdout, (caps, r.stdout[-2000:], r.stderr[-4000:])
 
 
+_GUARD_CODE = """
+import numpy as np
+import oracle
+from paper_2507_03092_gb300 import binding as B
+from paper_2507_03092_gb300 import circuit as C
+from paper_2507_03092_gb300 import streams as S
+s = B.Simulator(0)
+# a layer with random outcomes needs at least two passes of the wave loop (one
+# applying a wave, one finding nothing left), so a limit of one pass trips the
+# guard: the kernel records a bounds error and returns
+g = C.ghz(8)
+cid = s.compile(g)
+s.sample(cid, g, 4, seed=3, engine=B.ENGINE_LAYERED)
+try:
+    s.sync()
+    print("no error")
+except B.StabError as e:
+    print("guard", e.code, str(e))
+# the context stays usable: a circuit with deterministic outcomes only never
+# enters the wave loop and matches the oracle, and the flag was cleared
+b = C.Builder(6)
+for q in (0, 2, 3):
+    b.gate1(C.X, q)
+for q in range(6):
+    b.measure(q)
+det = b.build()
+cid2 = s.compile(det)
+coins, noise = S.streams_for(det, 1, range(4))
+got = B.records_to_numpy(s.sample(cid2, det, 4, coins, noise, engine=B.ENGINE_LAYERED))
+s.sync()
+want, _ = oracle.sample(det, coins, noise)
+print("after", bool(np.array_equal(got, want)))
+s.close()
+"""
+
+
+def test_wave_loop_guard_reports_an_error_and_the_context_survives():
+    """The wave loop's bound (lowered through STAB_WAVE_CAPS' seventh field)
+    fires as a device bounds error that stab_sync reports as
+    STAB_ERR_INTERNAL; the kernel returns instead of spinning, and the next
+    call on the same context runs normally."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, STAB_WAVE_CAPS="4096,1024,2048,2048,2048,128,1")
+    r = subprocess.run([sys.executable, "-c", _GUARD_CODE], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-4000:]
+    lines = r.stdout.splitlines()
+    guard = [ln for ln in lines if ln.startswith("guard ")]
+    assert guard and guard[0].split()[1] == str(B.ERR_INTERNAL) and "bounds" in guard[0], r.stdout
+    assert "after True" in lines, r.stdout
+
+
 def test_layered_wide_layer_item_state_in_global_memory(sim):
     """n = 16 400 > 16 384: the wave kernel keeps the layer's qubit map, item
     status and stale flags in global memory instead of shared memory, and the

@@ -59,7 +59,7 @@ MUTANTS = {
                                          "s->r[p - n] = 0;\n        memcpy(XR(s, p), XR(s, pr)"),
     "mpp_y_factor_without_z": ("if (c == 2 || c == 3) setb(ZR(s, pr), q, 1);",
                                "if (c == 3) setb(ZR(s, pr), q, 1);"),
-    # Sec. 2.6 noise channels, Sec. 4.2 composite channel
+    # Sec. 2.7 noise channels, Sec. 4.2 composite channel
     "threshold_off_by_one": ("return (uint64_t)(p * 4294967296.0);", "return (uint64_t)(p * 4294967296.0) + 1;"),
     "dep1_pauli_order": ("apply_pauli(s, a, (int)((u * 3) / T) + 1);", "apply_pauli(s, a, 3 - (int)((u * 3) / T));"),
     "dep2_qubits_swapped": ("if (m / 4) apply_pauli(s, a, m / 4);\n                        if (m % 4) apply_pauli(s, b, m % 4);",

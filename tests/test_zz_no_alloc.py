@@ -64,7 +64,9 @@ def test_noalloc_batch_matches_allocating_batch_twice(sim):
 def test_noalloc_rejects_batches_beyond_its_fixed_size(sim):
     circ = C.ghz(4)
     cid = sim.compile(circ)
-    rec = sim.record_buffer(1, circ.record_words)
+    # sized for every requested shot, so that a regression of the host-side
+    # limit check fails on the assertion below instead of writing past a buffer
+    rec = sim.record_buffer(8193, circ.record_words)
     g = B.JobGroup()
     g.circuit_id, g.shots = cid, 8193
     g.streams = B.make_streams(B.STREAM_SEEDED, seed=1)
