@@ -80,6 +80,38 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def l2_sweep(sim, B, torch):
+    """Measured L2 read + write bandwidth: the library's copy probe over
+    working sets of 8..64 MB (two buffers of half the size each, well below
+    the L2 size), many passes in one launch; the best size is the L2 peak.
+    One size far above L2 (2 GiB) gives the same probe's HBM figure for
+    comparison with the measured copy peak."""
+    props = torch.cuda.get_device_properties(sim.device)
+    l2_bytes = int(getattr(props, "L2_cache_size", 0) or 0)
+    per = {}
+    for mb in (8, 16, 32, 48, 64):
+        per[mb] = B.stab_probe_copy(sim.ctx, mb << 20, 200)
+    best_mb = max(per, key=per.get)
+    hbm_probe = B.stab_probe_copy(sim.ctx, 2 << 30, 5)
+    return {"l2_gbs": per[best_mb], "best_working_set_mb": best_mb,
+            "per_working_set_gbs": {str(k): round(v, 1) for k, v in per.items()},
+            "l2_cache_bytes": l2_bytes, "hbm_gbs_same_probe": hbm_probe,
+            "method": "stab_probe_copy: 16-byte ld/st.cg copy, 200 passes in one launch over "
+                      "two buffers of half the working set, CUDA events; read + write bytes"}
+
+
+def roof_bound(working_set_bytes, l2_bytes):
+    """'l2' when one launch's working set fits the L2 cache, else 'hbm'."""
+    return "l2" if l2_bytes and working_set_bytes <= l2_bytes else "hbm"
+
+
+def tableau_bytes(n):
+    """(column-packed copy, row-packed copy) bytes of one n-qubit tableau."""
+    H = (n + 31) // 32
+    Hr = (H + 3) // 4 * 4
+    return 8 * 2 * H * n, 4 * 64 * H * 2 * Hr
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -440,10 +472,19 @@ def main():
             raise AssertionError("host-buffer call gave a different record than the device-buffer call")
     e2e_val = ops_per_step * world / float(np.mean(e2e_t)) if e2e_t else None
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel, against HBM or L2 by working set
     dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
     ds = kstats[dom]
     hbm, src = peaks()
+    l2 = l2_sweep(sim, B, torch)
+    l2_gbs, l2_size = l2["l2_gbs"], l2["l2_cache_bytes"]
+    qm_b, rm_b = tableau_bytes(circ.n)
+    # one launch's working set: a gate run reads and writes the column-packed
+    # copy and writes the row-packed stabilizer half; the random-measurement
+    # kernel works on the row-packed copy and the layer's measured columns
+    max_layer = int(info.get("max_layer_meas", 0))
+    ws = {"k_gate_run": qm_b + rm_b // 2,
+          "k_meas_rand": rm_b + 4 * max_layer * 2 * ((circ.n + 31) // 32)}
     row_bytes = 2 * circ.n / 8.0          # a tableau row (x and z) or column (2n rows), in bytes
     alg = ds["alg_bytes"]
     model = "library model" if alg > 0 else None
@@ -457,8 +498,11 @@ def main():
     if ds["launches"] and alg > 0:
         ach = alg / (ds["total_ms"] / 1e3) / 1e9
         tr, tr_tag = ncu_traffic(dom)
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_source": src,
+        bnd = roof_bound(ws.get(dom, float("inf")), l2_size)
+        pk = l2_gbs if bnd == "l2" else hbm
+        roof = {"bound": bnd, "kernel": dom, "achieved": ach, "peak": pk, "unit": "GB/s",
+                "frac": ach / pk, "peak_source": "measured (L2 copy probe, this run)" if bnd == "l2" else src,
+                "frac_hbm": ach / hbm, "frac_l2": ach / l2_gbs, "working_set_bytes": ws.get(dom),
                 "traffic": tr, "traffic_source": tr_tag,
                 "alg_bytes_per_launch": alg / ds["launches"], "alg_model": model,
                 "avg_launch_us": 1e3 * ds["total_ms"] / ds["launches"]}
@@ -471,7 +515,10 @@ def main():
     if gr and gr["launches"]:
         ach = gr["alg_bytes"] / (gr["total_ms"] / 1e3) / 1e9
         tr, tr_tag = ncu_traffic("k_gate_run")
-        gate_roof = {"kernel": "k_gate_run", "achieved": ach, "peak": hbm, "frac": ach / hbm,
+        bnd = roof_bound(ws["k_gate_run"], l2_size)
+        pk = l2_gbs if bnd == "l2" else hbm
+        gate_roof = {"kernel": "k_gate_run", "bound": bnd, "achieved": ach, "peak": pk, "frac": ach / pk,
+                     "frac_hbm": ach / hbm, "frac_l2": ach / l2_gbs, "working_set_bytes": ws["k_gate_run"],
                      "unit": "GB/s", "launches": gr["launches"],
                      "alg_bytes_per_launch": gr["alg_bytes"] / gr["launches"],
                      "traffic": tr, "traffic_source": tr_tag,
@@ -503,6 +550,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
+        "l2": l2,
         "roofline_gate_run": gate_roof,
         "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in kstats.items()},
         "engine_counters_per_step": {k: v / K for k, v in counters_prof.items()},

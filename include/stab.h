@@ -352,6 +352,16 @@ int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
  * rowsums, column updates, row copies, other).  n <= 24 entries are written. */
 int stab_engine_counters(stab_ctx *ctx, uint64_t *out, size_t n, int reset);
 
+/* Read + write copy bandwidth of the context's device, for roofline
+ * denominators: two buffers of bytes/2 each (allocated and freed inside the
+ * call), one warm-up pass, then `passes` passes of a 16-byte-vector copy in
+ * ONE launch, loads and stores through L2 only (ld/st .cg), timed with CUDA
+ * events.  With bytes well below the L2 size every timed pass hits L2 (an L2
+ * bandwidth figure); with bytes far above it every pass goes to HBM.
+ * *gbs = 2 x (bytes/2) x passes / elapsed, in GB/s.  Synchronizes.  Errors:
+ * STAB_ERR_ARG (bytes < 4096, passes = 0, gbs NULL), STAB_ERR_OOM. */
+int stab_probe_copy(stab_ctx *ctx, uint64_t bytes, uint32_t passes, double *gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,7 @@ _SIGS = {
     "stab_profile_read": (I32, [P, U32, ctypes.POINTER(KernelStats), I32]),
     "stab_launch_count": (I32, [P, PU64, I32]),
     "stab_engine_counters": (I32, [P, PU64, SZ, I32]),
+    "stab_probe_copy": (I32, [P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -366,6 +367,13 @@ def stab_engine_counters(ctx, reset=True) -> dict:
     arr = (ctypes.c_uint64 * 24)()
     _check(lib().stab_engine_counters(ctx, arr, 24, 1 if reset else 0))
     return {k: int(v) for k, v in zip(COUNTER_NAMES, arr)}
+
+
+def stab_probe_copy(ctx, nbytes, passes) -> float:
+    """Read + write copy bandwidth (GB/s) over two buffers of nbytes/2 each."""
+    out = ctypes.c_double(0.0)
+    _check(lib().stab_probe_copy(ctx, int(nbytes), int(passes), ctypes.byref(out)))
+    return float(out.value)
 
 
 # ---------------------------------------------------------------- convenience

@@ -373,6 +373,25 @@ static uint32_t pick_engine(const stab_ctx *ctx, const HostProg &p, uint32_t eng
     return prefer_resident(ctx, p.n, shots) ? STAB_ENGINE_RESIDENT : STAB_ENGINE_LAYERED;
 }
 
+// Copy-bandwidth probe: `passes` passes of dst[i] = src[i] over n 16-byte
+// words in one launch, loads and stores through L2 only (ld/st .cg), each
+// thread keeping the same words on every pass.  With the two buffers smaller
+// than L2 every pass after the first hits L2, so the launch measures L2
+// read + write bandwidth without launch gaps between passes.
+__global__ void __launch_bounds__(512) k_probe_copy(const uint4 *src, uint4 *dst, size_t n, uint32_t passes) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (uint32_t p = 0; p < passes; p++)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (i + k * stride < n) v[k] = __ldcg(src + i + k * stride);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (i + k * stride < n) __stcg(dst + i + k * stride, v[k]);
+        }
+}
+
 }  // namespace stab
 
 using namespace stab;
@@ -834,6 +853,40 @@ int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset) {
     if (!count) return fail(STAB_ERR_ARG, "count is NULL");
     *count = ctx->prof.launches;
     if (reset) ctx->prof.launches = 0;
+    return STAB_OK;
+}
+
+int stab_probe_copy(stab_ctx *ctx, uint64_t bytes, uint32_t passes, double *gbs) {
+    CTX_GUARD;
+    if (!gbs || passes == 0 || bytes < 4096) return fail(STAB_ERR_ARG, "bad probe arguments");
+    const size_t half = (size_t)(bytes / 2) & ~(size_t)15;
+    void *a = nullptr, *b = nullptr;
+    if (cudaMalloc(&a, half) != cudaSuccess || cudaMalloc(&b, half) != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaFree(a);
+        return fail(STAB_ERR_OOM, "cudaMalloc for the probe buffers failed");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(a, 1, half, ctx->stream);
+    if (!e) e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    const uint32_t grid = 4u * (uint32_t)ctx->lc.sm_count;
+    const size_t n = half / 16;
+    float ms = 0.f;
+    if (!e) {
+        k_probe_copy<<<grid, 512, 0, ctx->stream>>>((const uint4 *)a, (uint4 *)b, n, 1);   // warm-up pass
+        cudaEventRecord(e0, ctx->stream);
+        k_probe_copy<<<grid, 512, 0, ctx->stream>>>((const uint4 *)a, (uint4 *)b, n, passes);
+        cudaEventRecord(e1, ctx->stream);
+        e = cudaEventSynchronize(e1);
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(a);
+    cudaFree(b);
+    if (e) return cuda_fail(e, "copy probe");
+    *gbs = 2.0 * (double)(n * 16) * passes / (ms * 1e-3) / 1e9;
     return STAB_OK;
 }
 
