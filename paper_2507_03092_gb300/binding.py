@@ -359,8 +359,8 @@ def stab_launch_count(ctx, reset=True) -> int:
 
 COUNTER_NAMES = ("waves", "wave_ops", "det_in_wave_kernel", "det", "sum_K", "sum_A",
                  "pivot_recomputes", "rowsum_passes",
-                 "cyc_pending", "cyc_pivots", "cyc_det_now", "cyc_window", "cyc_mark", "cyc_select",
-                 "cyc_lists", "cyc_rowsums", "cyc_colupd", "cyc_copies", "cyc_other")
+                 "cyc_pending", "cyc_refresh", "cyc_select", "cyc_lists", "cyc_apply", "cyc_signs",
+                 "unused14", "unused15", "unused16", "unused17", "unused18", "xsupport_recomputes")
 
 
 def stab_engine_counters(ctx, reset=True) -> dict:

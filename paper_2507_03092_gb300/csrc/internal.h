@@ -172,7 +172,10 @@ struct MeasScratch {
     uint32_t *cols = nullptr;     // [count][max_meas][CW]
     uint8_t *stat = nullptr;      // [count][max_meas]
     uint8_t *out = nullptr;       // [count][max_meas]
-    int *first = nullptr;         // [count][3][64H] wave marking: column rows, pivots, row claims
+    uint16_t *mxs = nullptr;      // [count][max_meas][XSCAP] layer items j with X on q_j in the op's pivot row
+    uint8_t *mxn = nullptr;       // [count][max_meas] entries of mxs (XS_OVER: more than XSCAP, XS_UNKNOWN: not computed)
+    uint32_t *mxver = nullptr;    // [count][max_meas] version of the pivot row when mxs was computed
+    uint32_t *rowver = nullptr;   // [count][32H] stabilizer-row versions (bumped whenever a row changes)
     uint16_t *qmap = nullptr;     // [count][n] qubit -> item of the current layer (0xffff: none)
     uint32_t *mpiv = nullptr;     // [count][max_meas] cached pivot (slot - 32H) or ~0
     uint32_t *mbsz = nullptr;     // [count][max_meas] cached |x-column support|
@@ -207,18 +210,16 @@ struct LaunchCfg {
 // to exercise them.
 struct WaveCaps {
     // Maxima size k_meas_rand's shared memory, which shares each SM's 256 KB
-    // with its L1 cache: smaller lists leave more L1 for the kernel's global
-    // data (measured on GB300, d = 71: 8192/4096/4096 -> 4096/2048/2048 entries
-    // is 3 % faster per step).  A wave's rowsum pairs are bounded by the mark
-    // budget below, so PAIRCAP_MAX = mark_budget loses nothing; larger lists
-    // only fall back to slower loops when they overflow.
-    static constexpr uint32_t PCAP_MAX = 4096, WCAP_MAX = 1024, PAIRCAP_MAX = 2048, JCAP_MAX = 2048;
+    // with its L1 cache; larger lists only fall back to slower loops when
+    // they overflow.  The window (pending measurements examined per wave) is
+    // at most WCAP_MAX, so every selected measurement fits the wave.
+    static constexpr uint32_t PCAP_MAX = 4096, WCAP_MAX = 512, PAIRCAP_MAX = 2048, JCAP_MAX = 2048;
     uint32_t pcap = PCAP_MAX;          // pending measurements considered per wave
     uint32_t wcap = WCAP_MAX;          // measurements applied per wave
     uint32_t paircap = PAIRCAP_MAX;    // (row, pivot) rowsum pairs listed per wave
     uint32_t jcap = JCAP_MAX;          // measured-column updates listed per wave
-    uint32_t mark_budget = 2048;       // rows marked per wave (bounds the window)
-    uint32_t window = 128;             // pending measurements examined per wave
+    uint32_t mark_budget = 0;          // unused (kept so that the test variable keeps its fields)
+    uint32_t window = WCAP_MAX;        // pending measurements examined per wave
     // Waves allowed per measurement layer before the kernel gives up with a
     // bounds error (the loop's own bound, 2 x ops + 3, applies as well);
     // lowered only by tests, to see the guard fire and the context survive.
@@ -226,6 +227,8 @@ struct WaveCaps {
 };
 constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list
 constexpr uint32_t PWCAP = 64;         // nonzero words kept per pivot row
+constexpr uint32_t XSCAP = 32;         // layer items kept per pivot-row X support
+constexpr uint8_t XS_OVER = 0xff, XS_UNKNOWN = 0xfe;
 void set_wave_caps(const WaveCaps &c);
 
 // Launch accounting and optional per-kernel CUDA-event timing.
@@ -294,8 +297,12 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
                          const LaunchCfg &lc, cudaStream_t s, KernelProf *kp);
 
 // device counters (unsigned long long) kept next to the error flag
+// DC_PHASE0 + k: SM cycles of k_meas_rand's per-wave phase k (0 pending list,
+// 1 pivot and X-support refresh, 2 selection, 3 work lists, 4 rowsums +
+// column updates + row copies, 5 chain signs)
 enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
-             DC_PIV_RECOMP = 6, DC_ROWSUM_PASSES = 7, DC_PHASE0 = 8, DC_N_PHASES = 11, DC_N = 24 };
+             DC_PIV_RECOMP = 6, DC_ROWSUM_PASSES = 7, DC_PHASE0 = 8, DC_N_PHASES = 11,
+             DC_XS_RECOMP = 19, DC_N = 24 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

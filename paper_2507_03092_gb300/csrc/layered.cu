@@ -69,7 +69,10 @@ struct LArgs {
     unsigned long long cols_stride;  // words per tableau
     uint8_t *mstat, *mout;
     unsigned long long m_stride;     // items per tableau
-    int *first;                      // [B][3][64H]
+    uint16_t *mxs;                   // [B][max_meas][XSCAP] pivot-row X support over the layer's items
+    uint8_t *mxn;                    // [B][max_meas] its length, XS_OVER or XS_UNKNOWN
+    uint32_t *mxver;                 // [B][max_meas] pivot-row version it was computed at
+    uint32_t *rowver;                // [B][32H] stabilizer-row versions
     uint16_t *qmap;                  // [B][n]
     uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
     uint32_t *mpiv, *mbsz;           // [B][max_meas] cached pivot / column size
@@ -723,6 +726,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
             a.mpiv[ci] = pv;
             a.mbsz[ci] = csize;
             a.mstale[ci] = 0;
+            a.mxn[ci] = XS_UNKNOWN;
         }
         return;
     }
@@ -850,23 +854,57 @@ constexpr uint32_t PCAP = WaveCaps::PCAP_MAX;
 constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;
 constexpr uint32_t PAIRCAP = WaveCaps::PAIRCAP_MAX;
 constexpr uint32_t JCAP = WaveCaps::JCAP_MAX;
+constexpr uint32_t HT = 4096;                 // chain hash slots (> PAIRCAP: never full)
+constexpr uint32_t PWS = 4;                   // pivot words staged in shared memory per wave op
 constexpr uint16_t NOPIV = 0xffffu;
-constexpr uint32_t QMAP_SMEM_MAX = 16384;   // qubits whose item map fits shared memory
+constexpr uint16_t HEMPTY = 0xffffu;
+constexpr uint32_t QMAP_SMEM_MAX = 16384;     // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
+static_assert(WCAP <= RAND_THREADS, "one thread per window op");
+static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "chain hash larger than the pair list, power of two");
 
-// k_meas_rand's dynamic shared memory: lists, the layer's per-item state when
-// n is small enough (qubit -> item map as 16-bit indices, item status and
-// stale-column flags as bytes; a layer has at most n items) and, last, the
-// sign column (CW words, 16-byte aligned).
-__host__ __device__ __forceinline__ uint32_t rand_item_words(uint32_t n) {
-    return n <= QMAP_SMEM_MAX ? (n + 1) / 2 + 2 * ((n + 3) / 4) : 0u;
+// k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
+struct RandLayout {
+    uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, pacc, hkey, htail, dlist, ents, spc, spx,
+        spz, qmask, blocked, qmap, stat, stale, r, total;
+};
+__host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
+    const uint32_t at = o;
+    o = (o + bytes + 15u) & ~15u;
+    return at;
 }
-__host__ __device__ __forceinline__ size_t rand_r_offset(uint32_t n, uint32_t H) {
-    const size_t bytes = (size_t)PCAP * 6 + WCAP * 2 + PAIRCAP * 4 + JCAP * 4 + 8 * (size_t)H +
-                         4 * (size_t)rand_item_words(n) + 2 * WCAP + 12 * (size_t)PAIRCAP;
-    return ((bytes + 15) & ~(size_t)15) / 4;           // in words
+__host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t H) {
+    RandLayout L;
+    uint32_t o = 0;
+    const bool item_smem = n <= QMAP_SMEM_MAX;
+    L.pend = rl_take(o, 2 * PCAP);
+    L.wpiv = rl_take(o, 2 * WCAP);
+    L.wbsz = rl_take(o, 2 * WCAP);
+    L.wxn = rl_take(o, WCAP);
+    L.sel = rl_take(o, 2 * WCAP);
+    L.sr = rl_take(o, WCAP);
+    L.pwn = rl_take(o, 2 * WCAP);
+    L.pairs = rl_take(o, 4 * PAIRCAP);
+    L.nxt = rl_take(o, 2 * PAIRCAP);
+    L.hslot = rl_take(o, 2 * PAIRCAP);
+    L.pacc = rl_take(o, 4 * PAIRCAP);
+    L.hkey = rl_take(o, 2 * HT);
+    L.htail = rl_take(o, 4 * HT);
+    L.dlist = rl_take(o, 2 * PAIRCAP);
+    L.ents = rl_take(o, 4 * JCAP);
+    L.spc = rl_take(o, 2 * WCAP * PWS);
+    L.spx = rl_take(o, 4 * WCAP * PWS);
+    L.spz = rl_take(o, 4 * WCAP * PWS);
+    L.qmask = rl_take(o, 8 * H);
+    L.blocked = rl_take(o, 4 * H);
+    L.qmap = rl_take(o, item_smem ? 2 * n : 0u);
+    L.stat = rl_take(o, item_smem ? n : 0u);
+    L.stale = rl_take(o, item_smem ? n : 0u);
+    L.r = rl_take(o, 8 * H);
+    L.total = o;
+    return L;
 }
-size_t rand_smem(uint32_t n, uint32_t H) { return 4 * rand_r_offset(n, H) + 8 * (size_t)H + 64; }
+size_t rand_smem(uint32_t n, uint32_t H) { return rand_layout(n, H).total; }
 
 // Block-wide exclusive scan of one value per thread (1024 threads).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t *total) {
@@ -894,52 +932,83 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
     return res;
 }
 
+// The random measurements of one measurement layer of one tableau (one CTA),
+// in waves.  Sequential CHP applies them one by one in circuit order (Sec. 2.4:
+// pivot, rowsum of the pivot into every other row with an X or Y on the
+// measured qubit, destabilizer copy, +-Z_a with a random sign).  Two of them,
+// j before k, commute bit for bit as tableau operations when neither pivot row
+// has an X or Y on the other's qubit; a wave applies at once every pending op
+// that commutes in this sense with every earlier pending op.  Conflicts are
+// read from each pending op's cached pivot-row X support over the layer's
+// items (mxs), recomputed only when the op's measured column changed (mstale)
+// or its pivot row did (row versions), so selection needs no pass over
+// columns and a window of up to WCAP pending ops costs the same as a small one.
+//
+// Per wave: (1) ordered list of pending random ops; (2) refresh of stale
+// pivots and X supports of the window; (3) selection: an op is blocked when an
+// earlier window op conflicts with it; (4) work lists: the rowsum pairs
+// (rows of the op's measured column, except its pivot and the destabilizer
+// partners of the wave's pivots, which end as copies of their pivot rows) are
+// linked per row through a shared-memory hash, the pivots' nonzero words are
+// staged in shared memory, and the pending ops whose measured column changes
+// are listed; (5) rowsums (a thread per pair: for each pivot word no earlier
+// pair of its row's chain holds, load the row word once and apply every pivot
+// of the chain holding that word, adding the powers of i), column updates and
+// row copies, which touch disjoint data, in one phase; (6) each row's sign
+// from 2 r + sum 2 r_p + the powers of i, applied at the start of the next
+// wave.  A chain holding a pivot with more than PWS nonzero words is applied
+// by one warp with full or word-listed rowsums before the copies.
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
-    extern __shared__ uint32_t smem[];
-    __shared__ uint32_t s_wt[32];
-    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_kend, s_firstrand, s_nrand, s_any, s_nstale;
-    __shared__ uint32_t s_tt;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint32_t s_wt[32], s_wcnt[32];
+    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_firstrand, s_nrand, s_any, s_nstale, s_cut;
+    __shared__ uint32_t s_serial, s_ndense;
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const Layer M = a.P.layers[layer];
-    const uint32_t pcap = a.caps.pcap, wcap = a.caps.wcap, paircap = a.caps.paircap, jcap = a.caps.jcap;
-    const uint32_t budget = a.caps.mark_budget, wmax = max(1u, a.caps.window);
+    const RandLayout Lo = rand_layout(n, H);
+    const uint32_t pcap = a.caps.pcap, wcap = min(a.caps.wcap, WCAP), paircap = a.caps.paircap,
+                   jcap = a.caps.jcap;
+    const uint32_t wmax = max(1u, min(a.caps.window, WCAP));
     uint8_t *const gstat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
-    uint32_t *cols = a.cols + t * a.cols_stride;
-    uint32_t *rm = a.rm + t * a.rm_stride;
+    uint32_t *const cols = a.cols + t * a.cols_stride;
+    uint32_t *const rm = a.rm + t * a.rm_stride;
     uint32_t *const gr = a.r + (size_t)t * CW;
-    uint8_t *dirty = a.dirty + (size_t)t * CW;
-    uint32_t *first = (uint32_t *)a.first + (size_t)t * 3 * 64 * H;   // earliest window op holding row
-    uint32_t *firstp = first + 64 * H;                                // earliest window op pivoting on row
-    uint32_t *claim = firstp + 64 * H;                                // last rowsum pair linked per row
-    // qubit -> item map, item status and stale flags: shared memory when n is
-    // small enough (status and flags copied in here and back at the end), else
-    // global
-    const bool item_smem = n <= QMAP_SMEM_MAX;
-    uint32_t *const item_w = smem + (PCAP * 6 + WCAP * 2) / 4 + PAIRCAP + JCAP + CW;
-    uint16_t *qmap = item_smem ? (uint16_t *)item_w : a.qmap + (size_t)t * n;
-    uint32_t *mpiv = a.mpiv + t * a.m_stride, *mbsz = a.mbsz + t * a.m_stride;
+    uint8_t *const dirty = a.dirty + (size_t)t * CW;
+    uint32_t *const mpiv = a.mpiv + t * a.m_stride, *const mbsz = a.mbsz + t * a.m_stride;
     uint8_t *const gmstale = a.mstale + t * a.m_stride;
-    uint16_t *msup = a.msup + t * a.m_stride * SUPCAP;
-    uint16_t *pend = (uint16_t *)smem;             // pending item indices, circuit order
-    uint16_t *piv = pend + PCAP;                   // their pivot (slot - 32H), NOPIV
-    uint16_t *bsz = piv + PCAP;                    // |x-column support| (saturated)
-    uint16_t *sel = bsz + PCAP;                    // selected pending positions
-    uint32_t *pairs = (uint32_t *)(sel + WCAP);    // row | sel index << 16
-    uint32_t *ents = pairs + PAIRCAP;              // item | sel index << 16 | bp << 31
-    uint32_t *qmask = ents + JCAP;                 // destabilizer partners of the wave [CW]
-    uint16_t *pwn = (uint16_t *)(qmask + CW + rand_item_words(n));   // nonzero words per pivot
-    uint32_t *wl_off = (uint32_t *)(pwn + WCAP);   // task offsets of the round's winning pairs [PAIRCAP]
-    int *pacc = (int *)(wl_off + PAIRCAP);         // their accumulated powers of i [PAIRCAP]
-    uint16_t *wl_e = (uint16_t *)(pacc + PAIRCAP); // chain links of the rowsum pairs [PAIRCAP]
-    uint16_t *phead = wl_e + PAIRCAP;              // each pair's chain head (| 0x8000: dense chain)
-    uint16_t *pwl = a.pwl + (size_t)t * WCAP * PWCAP;
-    // The sign column lives in shared memory for the whole kernel (copied
-    // back at the end).
-    uint32_t *r = smem + rand_r_offset(n, H);
-    uint8_t *stat = item_smem ? (uint8_t *)(item_w + (n + 1) / 2) : gstat;
-    uint8_t *mstale = item_smem ? (uint8_t *)(item_w + (n + 1) / 2 + (n + 3) / 4) : gmstale;
+    uint16_t *const msup = a.msup + t * a.m_stride * SUPCAP;
+    uint16_t *const mxs = a.mxs + t * a.m_stride * XSCAP;
+    uint8_t *const mxn = a.mxn + t * a.m_stride;
+    uint32_t *const mxver = a.mxver + t * a.m_stride;
+    uint32_t *const rowver = a.rowver + (size_t)t * 32 * H;
+    uint16_t *const pwl = a.pwl + (size_t)t * WCAP * PWCAP;
+    const bool item_smem = n <= QMAP_SMEM_MAX;
+    uint16_t *const pend = (uint16_t *)(smraw + Lo.pend);    // pending item indices, circuit order
+    uint16_t *const wpiv = (uint16_t *)(smraw + Lo.wpiv);    // window: pivot (slot - 32H) or NOPIV
+    uint16_t *const wbsz = (uint16_t *)(smraw + Lo.wbsz);    // window: |x-column support| (saturated)
+    uint8_t *const wxn = smraw + Lo.wxn;                     // window: X-support length / XS_OVER
+    uint16_t *const sel = (uint16_t *)(smraw + Lo.sel);      // wave: window positions
+    uint8_t *const sr = smraw + Lo.sr;                       // wave: pivot sign before the wave
+    uint16_t *const pwn = (uint16_t *)(smraw + Lo.pwn);      // wave: nonzero words of the pivot row
+    uint32_t *const pairs = (uint32_t *)(smraw + Lo.pairs);  // row | wave index << 16
+    uint16_t *const nxt = (uint16_t *)(smraw + Lo.nxt);      // next pair of the same row (0xffff ends)
+    uint16_t *const hslot = (uint16_t *)(smraw + Lo.hslot);  // hash slot of the pair's row
+    int *const pacc = (int *)(smraw + Lo.pacc);              // powers of i summed per chain (at its first pair)
+    uint16_t *const hkey = (uint16_t *)(smraw + Lo.hkey);    // hash: row
+    uint32_t *const htail = (uint32_t *)(smraw + Lo.htail);  // hash: first pair of the row's chain
+    uint16_t *const dlist = (uint16_t *)(smraw + Lo.dlist);  // chains applied by warps
+    uint32_t *const ents = (uint32_t *)(smraw + Lo.ents);    // item | wave index << 16 | bp << 31
+    uint16_t *const spc = (uint16_t *)(smraw + Lo.spc);      // wave pivots' nonzero words: index,
+    uint32_t *const spx = (uint32_t *)(smraw + Lo.spx);      //   x word
+    uint32_t *const spz = (uint32_t *)(smraw + Lo.spz);      //   z word
+    uint32_t *const qmask = (uint32_t *)(smraw + Lo.qmask);  // destabilizer partners of the wave's pivots
+    uint32_t *const blocked = (uint32_t *)(smraw + Lo.blocked);   // per item: an earlier window op conflicts
+    uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
+    uint8_t *const stat = item_smem ? smraw + Lo.stat : gstat;
+    uint8_t *const mstale = item_smem ? smraw + Lo.stale : gmstale;
+    uint32_t *const r = (uint32_t *)(smraw + Lo.r);          // sign column, copied back at the end
 
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -958,13 +1027,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             stat[i] = gstat[i];
             mstale[i] = gmstale[i];
         }
-    for (uint32_t s = threadIdx.x; s < 3 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
+    for (uint32_t h = threadIdx.x; h < HT; h += blockDim.x) {
+        hkey[h] = HEMPTY;
+        htail[h] = 0xffffffffu;
+    }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
     __syncthreads();
 
-    // first[row] holds stamp(wave) | k for the earliest op k of the wave's window
-    // whose column holds row; stamps decrease, so stale entries never win atomicMin.
     unsigned long long tlast = clock64();
 #define PHASE(k)                                                              \
     do {                                                                      \
@@ -974,26 +1044,52 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             tlast = now_;                                                     \
         }                                                                     \
     } while (0)
+    // the chain of pair e, from its first pair
+    auto chain_first = [&](uint32_t e) { return htail[hslot[e]]; };
+    auto pivot_has = [&](uint32_t x, uint32_t c, uint32_t &px, uint32_t &pz) {
+        const uint32_t m = pwn[x];
+        for (uint32_t w = 0; w < m && w < PWS; w++)
+            if (spc[x * PWS + w] == c) {
+                px = spx[x * PWS + w];
+                pz = spz[x * PWS + w];
+                return true;
+            }
+        return false;
+    };
+    // (6) signs of the previous wave's word-task chains: 2 r + sum 2 r_p + the
+    // powers of i, set once per row by the thread of the chain's first pair
+    uint32_t prev_npair = 0;
+    bool signs_pending = false;          // block-uniform
+    auto chain_signs = [&]() {
+        for (uint32_t e = threadIdx.x; e < prev_npair; e += blockDim.x) {
+            if (chain_first(e) != e) continue;
+            bool dense = false;
+            for (uint32_t f = e; f != 0xffffu; f = nxt[f]) dense |= pwn[pairs[f] >> 16] > PWS;
+            if (dense) continue;                       // its warp has set the sign
+            const uint32_t row = pairs[e] & 0xffffu;
+            const uint32_t r_s = rbit(r, row);
+            int ev = (int)(2 * r_s) + pacc[e];
+            for (uint32_t f = e; f != 0xffffu; f = nxt[f]) ev += 2 * (int)sr[pairs[f] >> 16];
+            if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
+            if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
+            if (row >= 32 * H) rowver[row - 32 * H]++;
+        }
+    };
+
     bool full_scan = true;          // pending list rebuilt from all items (first wave, or overflow)
-    // Stamps only decrease (marks per wave), so entries left from earlier
-    // waves never win an atomicMin; when the counter runs out the arrays are
-    // cleared and it restarts.
-    uint32_t wave = 0;
     // every wave resolves at least one op (the first pending random op always
     // qualifies), so 2*count+3 passes bound the loop; exceeding it is a bug
     const uint32_t glimit = min(2 * M.count + 3, a.caps.wave_limit);
     for (uint32_t guard = 0;; guard++) {
+        if (signs_pending) {
+            chain_signs();
+            signs_pending = false;
+        }
+        PHASE(5);
         if (guard >= glimit) {
             if (threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
             break;
         }
-        if (wave >= 0xfff0u) {
-            for (uint32_t s = threadIdx.x; s < 2 * 64 * H; s += blockDim.x) first[s] = 0xffffffffu;
-            wave = 0;
-            __syncthreads();
-        }
-        const uint32_t stamp = (0xfffeu - wave) << 16;
-        wave++;
         // ---- (1) ordered list of pending random measurements (first pcap):
         // from all items on the first wave or after an overflow, else by
         // compacting the previous list (ops only ever leave it)
@@ -1030,466 +1126,416 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 for (uint32_t d = 0; d < 8; d++)
                     if (d < cnt) pend[off + d] = keep[d];
             }
+            // the previous wave's chain hash is no longer read (its signs were
+            // applied before the scan's barriers)
+            for (uint32_t h = threadIdx.x; h < HT; h += blockDim.x) {
+                hkey[h] = HEMPTY;
+                htail[h] = 0xffffffffu;
+            }
+            for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
             __syncthreads();
             if (threadIdx.x == 0) {
                 s_np = min(s_tot, pcap);
-                s_nsel = 0; s_npair = 0; s_nent = 0;
-                s_firstrand = 0xffffffffu; s_nrand = 0;
+                s_nsel = 0; s_npair = 0; s_nent = 0; s_nstale = 0;
+                s_firstrand = 0xffffffffu; s_nrand = 0; s_cut = 0xffffffffu;
+                s_serial = 0; s_ndense = 0;
             }
-            for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
             __syncthreads();
         }
         PHASE(0);
         const uint32_t np = s_np;
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
-        // ---- (2) pivots and supports of the examined ops (cached; recomputed
-        // for ops whose column an earlier wave changed).  Cached ones are read
-        // a thread per op and the stale ones listed (in `pairs`, unused until
-        // the lists below); the warps then share out the rescans.
-        auto take_pivot = [&](uint32_t k, uint32_t pv, uint32_t bs) {
-            piv[k] = pv == 0xffffffffu ? NOPIV : (uint16_t)pv;
-            bsz[k] = (uint16_t)min(bs, 65535u);
-            if (pv != 0xffffffffu) { atomicMin(&s_firstrand, k); atomicAdd(&s_nrand, 1u); }
-        };
-        if (nlook <= PAIRCAP) {
-            if (threadIdx.x == 0) s_nstale = 0;
-            __syncthreads();
-            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
-                const uint32_t i = pend[k];
-                if (mstale[i]) pairs[atomicAdd(&s_nstale, 1u)] = k;
-                else take_pivot(k, mpiv[i], mbsz[i]);
+        const uint32_t wfirst = pend[0], wlast = pend[nlook - 1];
+        // ---- (2) window: cached pivots and X supports; stale ones listed in
+        // `pairs` (free until the work lists), bit 31 = column rescan
+        for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+            const uint32_t i = pend[k];
+            if (mstale[i]) {
+                pairs[atomicAdd(&s_nstale, 1u)] = k | 0x80000000u;
+                continue;
             }
-            __syncthreads();
+            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
+            wpiv[k] = (uint16_t)pv;
+            wbsz[k] = (uint16_t)min(bs, 65535u);
+            wxn[k] = (uint8_t)xn;
+            if (xn == XS_UNKNOWN || rowver[pv] != xv) pairs[atomicAdd(&s_nstale, 1u)] = k;
+        }
+        for (uint32_t w = (wfirst >> 5) + threadIdx.x; w <= (wlast >> 5); w += blockDim.x) blocked[w] = 0u;
+        if (lane == 0) s_wcnt[warp] = 0;
+        __syncthreads();
+        {
             const uint32_t nst = s_nstale;
             for (uint32_t x = (uint32_t)warp; x < nst; x += (uint32_t)nw) {
-                const uint32_t k = pairs[x], i = pend[k];
-                uint32_t pv, bs;
-                warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
-                if (lane == 0) {
-                    mpiv[i] = pv;
-                    mbsz[i] = bs;
-                    mstale[i] = 0;
-                    count(a, DC_PIV_RECOMP, 1);
-                    take_pivot(k, pv, bs);
-                }
-            }
-        } else {
-            for (uint32_t k = (uint32_t)warp; k < nlook; k += (uint32_t)nw) {
-                const uint32_t i = pend[k];
-                uint32_t pv, bs;
-                if (!mstale[i]) {
-                    pv = mpiv[i];
-                    bs = mbsz[i];
-                } else {
+                const uint32_t ent = pairs[x], k = ent & 0x7fffffffu, i = pend[k];
+                uint32_t pv;
+                if (ent >> 31) {
+                    uint32_t bs;
                     warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
                     if (lane == 0) {
                         mpiv[i] = pv;
                         mbsz[i] = bs;
                         mstale[i] = 0;
                         count(a, DC_PIV_RECOMP, 1);
+                        wbsz[k] = (uint16_t)min(bs, 65535u);
+                    }
+                    if (pv == 0xffffffffu) {             // became deterministic (warp-uniform)
+                        if (lane == 0) {
+                            wpiv[k] = NOPIV;
+                            stat[i] = MS_DETLATE;
+                            count(a, DC_DET_NOW, 1);
+                        }
+                        continue;
+                    }
+                    if (lane == 0) wpiv[k] = (uint16_t)pv;
+                } else {
+                    pv = wpiv[k];
+                }
+                // X support of the pivot row over the layer's items
+                const uint32_t ver = rowver[pv];
+                const uint32_t *__restrict__ prow = rm + (size_t)(32 * H + pv) * RS;
+                if (lane == 0) s_wcnt[warp] = 0;
+                __syncwarp();
+                for (uint32_t c0 = 0; c0 < H; c0 += 32 * 8) {
+                    uint32_t v[8];
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk++) {
+                        const uint32_t c = c0 + 32 * kk + lane;
+                        v[kk] = c < H ? prow[c] : 0u;
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk++) {
+                        uint32_t m = v[kk];
+                        const uint32_t c = c0 + 32 * kk + lane;
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t u = 32 * c + b;
+                            const uint32_t j = u < n ? qmap[u] : 0xffffu;
+                            if (j == 0xffffu) continue;
+                            const uint32_t pos = atomicAdd(&s_wcnt[warp], 1u);
+                            if (pos < XSCAP) mxs[(size_t)i * XSCAP + pos] = (uint16_t)j;
+                        }
                     }
                 }
-                if (lane == 0) take_pivot(k, pv, bs);
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t cnt = s_wcnt[warp];
+                    const uint8_t xn = cnt <= XSCAP ? (uint8_t)cnt : XS_OVER;
+                    mxn[i] = xn;
+                    mxver[i] = ver;
+                    wxn[k] = xn;
+                    count(a, DC_XS_RECOMP, 1);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
         PHASE(1);
-        // ---- (3) ops that became deterministic: resolved by k_meas_late
+        // ---- (3) selection: for every conflicting pair of window ops the
+        // later one is blocked; an op whose X support overflowed its list
+        // blocks every later op (and itself, unless it is the first)
         for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
-            if (piv[k] != NOPIV) continue;
-            stat[pend[k]] = MS_DETLATE;
-            count(a, DC_DET_NOW, 1);
+            if (wpiv[k] == NOPIV) continue;
+            atomicMin(&s_firstrand, k);
+            atomicAdd(&s_nrand, 1u);
+            const uint32_t i = pend[k], xn = wxn[k];
+            if (xn == XS_OVER) {
+                atomicMin(&s_cut, k);
+                continue;
+            }
+            const uint16_t *xl = mxs + (size_t)i * XSCAP;
+            for (uint32_t e = 0; e < xn; e++) {
+                const uint32_t j = xl[e];
+                if (j == i || j < wfirst || j > wlast || stat[j] != MS_RANDOM) continue;
+                const uint32_t late = max(i, j);
+                atomicOr(&blocked[late >> 5], 1u << (late & 31));
+            }
         }
-        if (s_nrand == 0) {          // block-uniform
-            __syncthreads();
+        __syncthreads();
+        if (s_nrand == 0) {             // block-uniform: the window became deterministic
             PHASE(2);
             continue;
         }
-        // ---- (4) window: leading examined ops whose columns total <= budget rows
-        if (warp == 0) {
-            uint32_t base = 0, kend = 0;
-            for (uint32_t k0 = 0; k0 < nlook; k0 += 32) {
-                const uint32_t k = k0 + lane;
-                const uint32_t v = (k < nlook && piv[k] != NOPIV) ? bsz[k] : 0u;
-                uint32_t x = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
-                    if (lane >= o) x += y;
-                }
-                const uint32_t ok = __ballot_sync(FULL_MASK, k < nlook && base + x <= budget);
-                kend = ok ? k0 + 32 - __clz(ok) : kend;        // highest lane within budget
-                base += __shfl_sync(FULL_MASK, x, 31);
-                if (base > budget) break;
-            }
-            if (lane == 0) s_kend = max(kend, s_firstrand + 1);
-        }
-        __syncthreads();
-        PHASE(3);
-        const uint32_t kend = s_kend;
-        // ---- (5) mark rows with the earliest window op holding them in its
-        // column, and pivot rows with the earliest window op pivoting on them.
-        // Ops with a listed support (<= SUPCAP rows) go 4 to a warp, 8 lanes
-        // each; larger columns take a whole warp.
         {
-            const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
-            for (uint32_t k0 = (uint32_t)warp * 4; k0 < kend; k0 += (uint32_t)nw * 4) {
-                const uint32_t k = k0 + sub;
-                if (k >= kend || piv[k] == NOPIV || bsz[k] > SUPCAP) continue;
+            const uint32_t cut = s_cut, fr = s_firstrand;
+            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
                 const uint32_t i = pend[k];
-                if (sl == 0) atomicMin(&firstp[32 * H + piv[k]], stamp | k);
-                const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                for (uint32_t e = sl; e < bsz[k]; e += 8) atomicMin(&first[sp[e]], stamp | k);
-            }
-        }
-        for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
-            if (piv[k] == NOPIV || bsz[k] <= SUPCAP) continue;
-            const uint32_t i = pend[k];
-            if (lane == 0) atomicMin(&firstp[32 * H + piv[k]], stamp | k);
-            const uint32_t *col = cols + (size_t)i * CW;
-            for (uint32_t w = lane; w < CW; w += 32) {
-                uint32_t m = col[w];
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    atomicMin(&first[32 * w + b], stamp | k);
-                }
-            }
-        }
-        __syncthreads();
-        PHASE(4);
-        // ---- (6) select op k when no earlier window op pivots on a row of its
-        // column and no earlier window op's column holds its pivot row (same
-        // split: 8 lanes per listed-support op, a warp per larger column)
-        {
-            const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
-            for (uint32_t k0 = (uint32_t)warp * 4; k0 < kend; k0 += (uint32_t)nw * 4) {   // warp-uniform
-                const uint32_t k = k0 + sub;
-                const bool active = k < kend && piv[k] != NOPIV && bsz[k] <= SUPCAP;
-                bool ok = true;
-                uint32_t i = 0;
-                if (active) {
-                    i = pend[k];
-                    const uint32_t me = stamp | k;
-                    const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                    for (uint32_t e = sl; e < bsz[k]; e += 8) ok &= firstp[sp[e]] >= me;
-                    if (sl == 0) ok &= first[32 * H + piv[k]] == me;
-                }
-                const uint32_t bal = __ballot_sync(FULL_MASK, ok);
-                if (active && sl == 0 && ((bal >> (8 * sub)) & 0xffu) == 0xffu) {
-                    const uint32_t idx = atomicAdd(&s_nsel, 1u);
-                    if (idx < wcap) {
-                        sel[idx] = (uint16_t)k;
-                        stat[i] = MS_WAVE;
-                    }
-                }
-            }
-        }
-        for (uint32_t k = (uint32_t)warp; k < kend; k += (uint32_t)nw) {
-            if (piv[k] == NOPIV || bsz[k] <= SUPCAP) continue;
-            const uint32_t i = pend[k], me = stamp | k;
-            bool ok = true;
-            const uint32_t *col = cols + (size_t)i * CW;
-            for (uint32_t w = lane; w < CW; w += 32) {
-                uint32_t m = col[w];
-                while (m && ok) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    ok = firstp[32 * w + b] >= me;
-                }
-            }
-            if (lane == 0) ok &= first[32 * H + piv[k]] == me;
-            if (__all_sync(FULL_MASK, ok) && lane == 0) {
+                if (wpiv[k] == NOPIV || ((blocked[i >> 5] >> (i & 31)) & 1u)) continue;
+                if (k > cut || (k == cut && k != fr)) continue;
                 const uint32_t idx = atomicAdd(&s_nsel, 1u);
                 if (idx < wcap) {
                     sel[idx] = (uint16_t)k;
                     stat[i] = MS_WAVE;
+                    atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
                 }
             }
         }
         __syncthreads();
-        PHASE(5);
-        // ---- (7) list rowsum pairs and measured-column updates
+        PHASE(2);
+        // ---- (4) work lists, one warp per wave op
         const uint32_t nsel = min(s_nsel, wcap);
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
             const uint32_t k = sel[x], i = pend[k];
-            const uint32_t q = piv[k], p = 32 * H + q;
-            if (bsz[k] <= SUPCAP) {
-                const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                for (uint32_t e = lane; e < bsz[k]; e += 32) {
-                    const uint32_t row = sp[e];
-                    dirty[row >> 5] = 1;
-                    if (row == p || row == q) continue;
-                    const uint32_t f = atomicAdd(&s_npair, 1u);
-                    if (f < paircap) pairs[f] = row | (x << 16);
+            const uint32_t q = wpiv[k], p = 32 * H + q;
+            // rowsum pairs: rows of the measured column except the pivot and
+            // the wave's destabilizer partners, linked per row
+            auto add_pair = [&](uint32_t row) {
+                dirty[row >> 5] = 1;
+                if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) return;
+                const uint32_t f = atomicAdd(&s_npair, 1u);
+                if (f >= paircap) return;
+                pairs[f] = row | (x << 16);
+                pacc[f] = 0;
+                uint32_t h = (row * 2654435761u) >> 20;       // HT = 4096 slots
+                uint32_t probe = 0;
+                for (; probe < HT; probe++) {
+                    const uint16_t old = atomicCAS(&hkey[h], HEMPTY, (uint16_t)row);
+                    if (old == HEMPTY || old == (uint16_t)row) break;
+                    h = (h + 1) & (HT - 1);
                 }
+                if (probe == HT) {                   // cannot happen: HT > paircap
+                    set_err(a.err, DERR_BOUNDS);
+                    nxt[f] = 0xffffu;
+                    hslot[f] = 0;
+                    return;
+                }
+                const uint32_t prev = atomicExch(&htail[h], f);
+                nxt[f] = prev == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)prev;
+                hslot[f] = (uint16_t)h;
+            };
+            if (wbsz[k] <= SUPCAP) {
+                const uint16_t *sp = msup + (size_t)i * SUPCAP;
+                for (uint32_t e = lane; e < wbsz[k]; e += 32) add_pair(sp[e]);
             } else {
                 const uint32_t *col = cols + (size_t)i * CW;
                 for (uint32_t w = lane; w < CW; w += 32) {
                     uint32_t m = col[w];
-                    if (m) dirty[w] = 1;
-                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
-                    if (w == (q >> 5)) m &= ~(1u << (q & 31));
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        const uint32_t f = atomicAdd(&s_npair, 1u);
-                        if (f < paircap) pairs[f] = (32 * w + b) | (x << 16);
+                        add_pair(32 * w + b);
                     }
                 }
             }
-            // remaining pending ops whose qubit has X or Y in row p or row q, and
-            // the nonzero words of row p (for the sparse rowsums); each lane
-            // loads 6 words of both rows before using them
+            // pending ops whose qubit has X or Y in row p or row q (their
+            // measured columns change), and the nonzero words of row p
             const uint32_t *__restrict__ rp_ = rm + (size_t)p * RS;
             const uint32_t *__restrict__ rq_ = rm + (size_t)q * RS;
             uint32_t nzcnt = 0;
             for (uint32_t c0 = 0; c0 < H; c0 += 32 * 6) {
                 uint32_t xp[6], zp[6], xq[6];
 #pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const uint32_t c = c0 + 32 * k + lane;
-                    xp[k] = c < H ? rp_[c] : 0u;
-                    zp[k] = c < H ? rp_[Hr + c] : 0u;
-                    xq[k] = c < H ? rq_[c] : 0u;
+                for (int kk = 0; kk < 6; kk++) {
+                    const uint32_t c = c0 + 32 * kk + lane;
+                    xp[kk] = c < H ? rp_[c] : 0u;
+                    zp[kk] = c < H ? rp_[Hr + c] : 0u;
+                    xq[kk] = c < H ? rq_[c] : 0u;
                 }
 #pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const uint32_t c = c0 + 32 * k + lane;
-                    uint32_t mm = xp[k] | xq[k];
+                for (int kk = 0; kk < 6; kk++) {
+                    const uint32_t c = c0 + 32 * kk + lane;
+                    uint32_t mm = xp[kk] | xq[kk];
                     while (mm) {
                         const int b = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const uint32_t j = qmap[32 * c + b];
+                        const uint32_t u = 32 * c + b;
+                        const uint32_t j = u < n ? qmap[u] : 0xffffu;
                         if (j != 0xffffu && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
                             const uint32_t f = atomicAdd(&s_nent, 1u);
-                            if (f < jcap) ents[f] = j | (x << 16) | (((xp[k] >> b) & 1u) << 31);
+                            if (f < jcap) ents[f] = j | (x << 16) | (((xp[kk] >> b) & 1u) << 31);
                         }
                     }
-                    const bool nzw = (xp[k] | zp[k]) != 0u;
+                    const bool nzw = (xp[kk] | zp[kk]) != 0u;
                     const uint32_t m = __ballot_sync(FULL_MASK, nzw);
                     const uint32_t pos = nzcnt + __popc(m & ((1u << lane) - 1u));
                     if (nzw && pos < PWCAP) pwl[x * PWCAP + pos] = (uint16_t)c;
+                    if (nzw && pos < PWS) {
+                        spc[x * PWS + pos] = (uint16_t)c;
+                        spx[x * PWS + pos] = xp[kk];
+                        spz[x * PWS + pos] = zp[kk];
+                    }
                     nzcnt += __popc(m);
                 }
             }
-            if (lane == 0) pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
             if (lane == 0) {
+                pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
+                sr[x] = (uint8_t)rbit(r, p);
+                if (nzcnt > PWS) s_serial = 1;
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
-                atomicOr(&qmask[q >> 5], 1u << (q & 31));
             }
         }
         __syncthreads();
-        PHASE(6);
+        PHASE(3);
         const uint32_t npair = s_npair, nent = s_nent;
         if (threadIdx.x == 0) {
             count(a, DC_WAVES, 1);
             count(a, DC_WAVE_OPS, nsel);
             count(a, DC_SUM_A, npair);
+            count(a, DC_ROWSUM_PASSES, 1);
         }
-        // ---- (8) rowsums of the wave.  A row in the columns of several wave
-        // ops receives the product of their pivots; the pivots are commuting
-        // stabilizers, so that product -- and the row's final sign -- does not
-        // depend on the order in which they are applied.  The pairs of each
-        // row are linked into a chain; a task is one (pair, nonzero pivot
-        // word): it runs only if no earlier pair of its chain has that word
-        // nonzero, and applies its pivot and every later pivot of the chain to
-        // that word in chain order.  The powers of i add up per row and the
-        // sign is set once from 2 r_s + sum 2 r_p + sum of the powers.  Chains
-        // holding a pivot with more than PWCAP nonzero words go to one warp,
-        // which applies them in the same order with the warp rowsums.
+        // serial: a dense pivot, or an overflowed list whose fallback reads
+        // pivot rows from the tableau -- the row copies wait for them
+        const bool serial = s_serial || npair > paircap || nent > jcap;
+        // ---- (5a) rowsums of chains whose pivots are all staged: a thread per pair
         if (npair <= paircap) {
-            uint32_t *head = claim;                    // [64H] last pair linked for each row, or ~0
-            uint16_t *nxt = wl_e;                      // next pair of the same row, 0xffff ends
             for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
-                const uint32_t old = atomicExch(&head[pairs[e] & 0xffffu], e);
-                nxt[e] = old == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)old;
-                phead[e] = 0xffffu;
-            }
-            __syncthreads();
-            // the chain heads are the pairs no other pair links to; each head
-            // then gives every pair of its chain the head's index, with bit 15
-            // set when a pivot of the chain is dense (shared memory from here
-            // on: no pass below reads the global head words)
-            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x)
-                if (nxt[e] != 0xffffu) phead[nxt[e]] = 0xfffeu;
-            __syncthreads();
-            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
-                if (phead[e] != 0xffffu) continue;
+                const uint32_t f0 = chain_first(e);
                 bool dense = false;
-                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) dense |= pwn[(pairs[f] >> 16) & 0x7fffu] > PWCAP;
-                const uint16_t hv = (uint16_t)(e | (dense ? 0x8000u : 0u));
-                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) phead[f] = hv;
-            }
-            __syncthreads();
-            // task offsets: pairs in contiguous chunks per thread
-            const uint32_t per = (npair + blockDim.x - 1) / blockDim.x;
-            const uint32_t e0 = threadIdx.x * per, e1 = min(npair, e0 + per);
-            uint32_t ntask = 0;
-            for (uint32_t e = e0; e < e1; e++) {
-                pacc[e] = 0;
-                if (phead[e] >> 15) continue;
-                ntask += pwn[(pairs[e] >> 16) & 0x7fffu];
-            }
-            uint32_t kt = block_excl_scan(ntask, s_wt, &s_tt);
-            for (uint32_t e = e0; e < e1; e++) {
-                wl_off[e] = kt;
-                if (!(phead[e] >> 15)) kt += pwn[(pairs[e] >> 16) & 0x7fffu];
-            }
-            __syncthreads();
-            const uint32_t tott = s_tt;
-            for (uint32_t tk = threadIdx.x; tk < tott; tk += blockDim.x) {
-                uint32_t lo = 0, hi = npair;                // upper bound of tk in wl_off
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (wl_off[mid] <= tk) lo = mid + 1; else hi = mid;
+                for (uint32_t f = f0; f != 0xffffu; f = nxt[f]) dense |= pwn[pairs[f] >> 16] > PWS;
+                if (dense) {
+                    if (f0 == e) dlist[atomicAdd(&s_ndense, 1u)] = (uint16_t)e;
+                    continue;
                 }
-                const uint32_t e = lo - 1;                  // wl_off[0] = 0 <= tk, so lo >= 1
-                const uint32_t pe = pairs[e], row = pe & 0xffffu, x = (pe >> 16) & 0x7fffu;
-                const uint32_t c = pwl[x * PWCAP + (tk - wl_off[e])];
-                const uint32_t hd = phead[e];             // not dense: dense chains have no tasks
-                bool first_here = true;
-                for (uint32_t f = hd; f != e; f = nxt[f]) {
-                    const uint32_t pf = 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]];
-                    if ((rm[(size_t)pf * RS + c] | rm[(size_t)pf * RS + Hr + c]) != 0u) { first_here = false; break; }
-                }
-                if (!first_here) continue;
-                uint32_t *rs = rm + (size_t)row * RS;
-                uint32_t xs = rs[c], zs = rs[Hr + c];
-                int acc = 0;
-                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
-                    const uint32_t pf = 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]];
-                    const uint32_t xp = rm[(size_t)pf * RS + c], zp = rm[(size_t)pf * RS + Hr + c];
-                    acc += phase_word(xp, zp, xs, zs);
-                    xs ^= xp;
-                    zs ^= zp;
-                }
-                rs[c] = xs;
-                rs[Hr + c] = zs;
-                if (acc) atomicAdd(&pacc[hd], acc);
-            }
-            __syncthreads();
-            // signs of the sparse chains (head thread); dense chains by warps
-            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
-                if (phead[e] != e) continue;
-                const uint32_t row = pairs[e] & 0xffffu;
-                const uint32_t r_s = rbit(r, row);
-                int ev = (int)(2 * r_s) + pacc[e];
-                for (uint32_t f = e; f != 0xffffu; f = nxt[f])
-                    ev += (int)(2 * rbit(r, 32 * H + piv[sel[(pairs[f] >> 16) & 0x7fffu]]));
-                if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
-                if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
-            }
-            for (uint32_t e = (uint32_t)warp; e < npair; e += (uint32_t)nw) {
-                if (phead[e] != (e | 0x8000u)) continue;
-                const uint32_t row = pairs[e] & 0xffffu;
-                for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
-                    const uint32_t x = (pairs[f] >> 16) & 0x7fffu, p = 32 * H + piv[sel[x]];
-                    if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
-                    else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) head[pairs[e] & 0xffffu] = 0xffffffffu;
-            if (threadIdx.x == 0) count(a, DC_ROWSUM_PASSES, 1);
-            PHASE(7);
-        } else {
-            // list overflow: one warp applies the pivots row by row, in wave order
-            for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
-                for (uint32_t x = 0; x < nsel; x++) {
-                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
-                    uint32_t m = cols[(size_t)pend[k] * CW + w];
-                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
-                    if (w == (q >> 5)) m &= ~(1u << (q & 31));
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        rowsum_warp(rm, RS, Hr, H, r, 32 * w + b, p, a.err);
+                const uint32_t row = pairs[e] & 0xffffu, x = pairs[e] >> 16;
+                const uint32_t nwd = pwn[x];
+                // the words of this pair's pivot that no earlier pair of the chain holds
+                uint32_t own = 0;
+                for (uint32_t w = 0; w < nwd; w++) {
+                    const uint32_t c = spc[x * PWS + w];
+                    bool first = true;
+                    for (uint32_t f = f0; f != e; f = nxt[f]) {
+                        uint32_t px_, pz_;
+                        if (pivot_has(pairs[f] >> 16, c, px_, pz_)) { first = false; break; }
                     }
+                    if (first) own |= 1u << w;
                 }
+                if (!own) continue;
+                uint32_t *rs = rm + (size_t)row * RS;
+                uint32_t xs[PWS], zs[PWS];
+#pragma unroll
+                for (uint32_t w = 0; w < PWS; w++) {
+                    const bool o = (own >> w) & 1u;
+                    const uint32_t c = o ? spc[x * PWS + w] : 0u;
+                    xs[w] = o ? rs[c] : 0u;
+                    zs[w] = o ? rs[Hr + c] : 0u;
+                }
+                int acc = 0;
+#pragma unroll
+                for (uint32_t w = 0; w < PWS; w++) {
+                    if (!((own >> w) & 1u)) continue;
+                    const uint32_t c = spc[x * PWS + w];
+                    uint32_t xv = xs[w], zv = zs[w];
+                    for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
+                        uint32_t px_, pz_;
+                        if (!pivot_has(pairs[f] >> 16, c, px_, pz_)) continue;
+                        acc += phase_word(px_, pz_, xv, zv);
+                        xv ^= px_;
+                        zv ^= pz_;
+                    }
+                    rs[c] = xv;
+                    rs[Hr + c] = zv;
+                }
+                if (acc) atomicAdd(&pacc[f0], acc);
             }
         }
-        // ---- (9) measured columns of remaining ops: x ^= x_{p,b} on A rows.
-        // Rows that are destabilizer partners of this wave's pivots are left
-        // out: each ends as a copy of its pivot row, so its bit is set in (10).
+        // ---- (5b) measured columns of the remaining ops: x ^= x_{p,b} on the
+        // pivot's column rows (not the pivot, not the wave's destabilizer
+        // partners, which end as copies of their pivots); then row q's bit is
+        // x_{p,b} and row p's is 0.  Touches no bit of another wave op's p or q.
         if (nent <= jcap) {
             for (uint32_t e = (uint32_t)warp; e < nent; e += (uint32_t)nw) {
-                if (!(ents[e] >> 31)) continue;
-                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu;
-                const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
-                uint32_t *cj = cols + (size_t)j * CW;
-                if (bsz[k] <= SUPCAP) {
-                    const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
-                    for (uint32_t f = lane; f < bsz[k]; f += 32) {
-                        const uint32_t row = sp[f];
-                        if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
-                        atomicXor(&cj[row >> 5], 1u << (row & 31));
-                    }
-                } else {
-                    const uint32_t *col = cols + (size_t)pend[k] * CW;
-                    for (uint32_t w = lane; w < CW; w += 32) {
-                        uint32_t v = col[w] & ~qmask[w];
-                        if (w == (p >> 5)) v &= ~(1u << (p & 31));
-                        if (v) atomicXor(&cj[w], v);
-                    }
-                }
-            }
-        } else {
-            for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
-                if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
-                uint32_t *cj = cols + (size_t)j * CW;
-                for (uint32_t x = 0; x < nsel; x++) {
-                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
-                    if (!((cj[p >> 5] >> (p & 31)) & 1u)) continue;
-                    const uint32_t *col = cols + (size_t)pend[k] * CW;
-                    for (uint32_t w = lane; w < CW; w += 32) {
-                        uint32_t v = col[w] & ~qmask[w];
-                        if (w == (p >> 5)) v &= ~(1u << (p & 31));
-                        cj[w] ^= v;
-                    }
-                    __syncwarp();
-                }
-            }
-        }
-        __syncthreads();
-        PHASE(8);
-        // ---- (10) bit fixes (row q gets x_{p,b}, row p gets 0), row copies
-        if (nent <= jcap) {
-            for (uint32_t e = threadIdx.x; e < nent; e += blockDim.x) {
                 const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
-                const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
                 uint32_t *cj = cols + (size_t)j * CW;
-                if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
-                else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
-                atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
-                mstale[j] = 1;
+                if (bp) {
+                    if (wbsz[k] <= SUPCAP) {
+                        const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
+                        for (uint32_t f = lane; f < wbsz[k]; f += 32) {
+                            const uint32_t row = sp[f];
+                            if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
+                            atomicXor(&cj[row >> 5], 1u << (row & 31));
+                        }
+                    } else {
+                        const uint32_t *col = cols + (size_t)pend[k] * CW;
+                        for (uint32_t w = lane; w < CW; w += 32) {
+                            uint32_t v = col[w] & ~qmask[w];
+                            if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                            if (v) atomicXor(&cj[w], v);
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
+                    else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                    atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                    mstale[j] = 1;
+                }
             }
         } else {
-            // fallback: recompute bits from the untouched pivot rows
+            // list overflow: every remaining op's column from the wave's columns
+            // and the (not yet overwritten) pivot rows
             for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
                 if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
                 uint32_t *cj = cols + (size_t)j * CW;
                 const uint32_t qb = a.P.mitems[M.first + j].q;
-                if (lane == 0) mstale[j] = 1;
-                for (uint32_t x = lane; x < nsel; x += 32) {
-                    const uint32_t k = sel[x], q = piv[k], p = 32 * H + q;
+                for (uint32_t x = 0; x < nsel; x++) {
+                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
                     const uint32_t bp = (rm[(size_t)p * RS + (qb >> 5)] >> (qb & 31)) & 1u;
-                    if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
-                    else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
-                    atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                    if (bp) {
+                        const uint32_t *col = cols + (size_t)pend[k] * CW;
+                        for (uint32_t w = lane; w < CW; w += 32) {
+                            uint32_t v = col[w] & ~qmask[w];
+                            if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                            cj[w] ^= v;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        const uint32_t bq = (cj[q >> 5] >> (q & 31)) & 1u;
+                        if (bp != bq) cj[q >> 5] ^= 1u << (q & 31);
+                        cj[p >> 5] &= ~(1u << (p & 31));
+                    }
+                    __syncwarp();
+                }
+                if (lane == 0) mstale[j] = 1;
+            }
+        }
+        if (serial) {
+            __syncthreads();
+            // chains holding a dense pivot: one warp per chain, pivots in chain
+            // order (pivot signs still unchanged: the copies come after)
+            if (npair <= paircap) {
+                const uint32_t nd = s_ndense;
+                for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) {
+                    const uint32_t e = dlist[d], row = pairs[e] & 0xffffu;
+                    for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
+                        const uint32_t x = pairs[f] >> 16, p = 32 * H + wpiv[sel[x]];
+                        if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
+                        else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                        __syncwarp();
+                    }
+                    if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+                }
+            } else {
+                // pair-list overflow: one warp applies the pivots row by row, in wave order
+                for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
+                    for (uint32_t x = 0; x < nsel; x++) {
+                        const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                        uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
+                        if (w == (p >> 5)) m &= ~(1u << (p & 31));
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t row = 32 * w + b;
+                            rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                            __syncwarp();
+                            if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+                        }
+                    }
                 }
             }
-            __syncthreads();          // the pivot rows read above are overwritten next
+            __syncthreads();
         }
+        // ---- (5c) row copies: row q <- row p, row p <- +-Z_a (16-byte words
+        // over the Hr-word rows; the words past H are zero in every row), and
+        // the outcome
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
-            const uint32_t k = sel[x], i = pend[k], q = piv[k], p = 32 * H + q;
+            const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
             const MItem m = a.P.mitems[M.first + i];
             const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
                                                            : coin_bit(a.call->st, t, m.coin);
-            // row q <- row p, row p <- Z_a: 16-byte words over the Hr-word rows
-            // (the words past H are zero in every row)
             const uint32_t H4 = Hr >> 2;
             const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
             uint4 *__restrict__ dq = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
@@ -1509,11 +1555,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                                         here && zsub == 2 ? za : 0u, here && zsub == 3 ? za : 0u);
             }
             if (lane == 0) {
-                const uint32_t rp = rbit(r, p);
-                if (rp) atomicOr(&r[q >> 5], 1u << (q & 31));
+                if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
                 else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
                 if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
                 else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
+                rowver[q]++;
                 out[i] = (uint8_t)coin;
                 stat[i] = MS_DONE;
                 write_record(a, t, m.rec, coin);
@@ -1521,9 +1567,12 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         }
         __syncthreads();
-        PHASE(9);
+        PHASE(4);
+        prev_npair = npair <= paircap ? npair : 0u;
+        signs_pending = prev_npair > 0;
     }
 #undef PHASE
+    if (signs_pending) chain_signs();
     __syncthreads();
     for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
     if (item_smem)
@@ -1628,7 +1677,10 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err)
         a.cols_stride = (unsigned long long)std::max<uint32_t>(1, p->dev.max_meas) * b.CW;
         a.mstat = ms->stat; a.mout = ms->out;
         a.m_stride = std::max<uint32_t>(1, p->dev.max_meas);
-        a.first = ms->first;
+        a.mxs = ms->mxs;
+        a.mxn = ms->mxn;
+        a.mxver = ms->mxver;
+        a.rowver = ms->rowver;
         a.qmap = ms->qmap;
         a.ev = ms->ev;
         a.ev_cnt = ms->ev_cnt;
