@@ -320,6 +320,113 @@ def oracle_batched(shots=4096, per_d=64, seed=0, cores=None):
                       f"each distance's time scaled by its share of the shots"}
 
 
+# ------------------------------------------------------------------ per-config rates
+def tick_prefixes(circ):
+    """Op counts at the TICKs of a circuit (whole layers / rounds as prefixes)."""
+    return [int(i) + 1 for i in np.flatnonzero(circ.ops["kind"] == C.TICK)] or [len(circ.ops)]
+
+
+def oracle_prefix_rate(circ, coins, noise, budget_s, prefixes=None):
+    """The oracle, one thread, on the longest whole-round prefix of ``circ``
+    that fits about ``budget_s`` seconds (sized from a one-round probe).
+    Returns (gate+measure ops/s, measurements/s, description)."""
+    import oracle
+    ends = prefixes or tick_prefixes(circ)
+    pre = C.prefix(circ, ends[0])
+    t0 = time.perf_counter()
+    oracle.run(pre, coins, noise)
+    t_one = time.perf_counter() - t0
+    k = int(max(1, min(len(ends), budget_s // max(t_one, 1e-6))))
+    pre = C.prefix(circ, ends[k - 1])
+    t0 = time.perf_counter()
+    oracle.run(pre, coins, noise)
+    dt = time.perf_counter() - t0
+    kinds = pre.ops["kind"]
+    n_meas = int(np.count_nonzero(np.isin(kinds, (C.M, C.R, C.MPP))))
+    ops = C.gate_measure_ops(pre)
+    return ops / dt, n_meas / dt, (f"first {k} of {len(ends)} rounds ({ops} gate+measure ops), "
+                                   f"1 thread, {dt:.2f} s")
+
+
+def gpu_rates(sim, B, torch, circ, shots, flush, reps=3, engine=None, seed=0):
+    """Device-timed shots of ``circ`` through stab_sample (device-resident
+    streams, L2 flushed between reps): shots/s, gates/s, measurements/s,
+    gate+measure ops/s, and the ms per call."""
+    eng = B.ENGINE_AUTO if engine is None else engine
+    cid = sim.compile(circ)
+    coins, noise = S.streams_for(circ, seed, range(shots))
+    dc, dn = sim.to_dev(coins), sim.to_dev(noise)
+    rec = sim.record_buffer(shots, circ.record_words)
+    st = B.make_streams(B.STREAM_BUFFER, coins=dc, noise=dn)
+    B.stab_sample(sim.ctx, cid, shots, st, rec, eng)          # warm-up (allocation, graph capture)
+    sim.sync()
+    ts = []
+    for i in range(reps):
+        flush.fill_(i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.stab_sample(sim.ctx, cid, shots, st, rec, eng)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    sim.sync()
+    t = float(np.median(ts))
+    kinds = circ.ops["kind"]
+    n_g = int(np.count_nonzero(np.isin(kinds, C.ONE_QUBIT_GATES + C.TWO_QUBIT_GATES)))
+    n_m = int(np.count_nonzero(np.isin(kinds, (C.M, C.R, C.MPP))))
+    sim.release(cid)
+    return {"shots_per_s": shots / t, "gates_per_s": n_g * shots / t, "measurements_per_s": n_m * shots / t,
+            "ops_per_s": (n_g + n_m) * shots / t, "ms_per_call": 1e3 * t, "shots": shots}, (coins, noise)
+
+
+def config_suite(sim, B, torch, flush, cpu=True):
+    """The other workloads at their stated sizes, with the oracle beside each:
+    C1 (d=3, 1024 shots; oracle on 1 thread and all host threads), C2
+    (n=1000, 200 random Clifford layers, one tableau), C3 noiseless (d=71,
+    one shot) and the random n-wide, n-round H/S/CX/M/R benchmark (Sec. 4.1)
+    at three widths."""
+    import oracle
+    cores = os.cpu_count() or 1
+    out = {}
+    c1 = C.surface_code_memory(3, p=1e-3)
+    g, (coins, noise) = gpu_rates(sim, B, torch, c1, 1024, flush)
+    if cpu:
+        t0 = time.perf_counter()
+        oracle.sample(c1, coins, noise, threads=1)
+        t1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.sample(c1, coins, noise, threads=cores)
+        tn = time.perf_counter() - t0
+        g["cpu_baseline"] = {"kind": "oracle", "one_core_shots_per_s": 1024 / t1,
+                             "all_cores_shots_per_s": 1024 / tn, "cores": cores, "sample": "all 1024 shots"}
+    out["c1_d3_1024_shots"] = g
+    c2 = C.random_clifford_layers(1000, 200, seed=0)
+    g, (coins, noise) = gpu_rates(sim, B, torch, c2, 1, flush, engine=B.ENGINE_LAYERED)
+    if cpu:
+        ops, meas, desc = oracle_prefix_rate(c2, coins[0], noise[0], 10.0)
+        g["cpu_baseline"] = {"kind": "oracle", "ops_per_s": ops, "measurements_per_s": meas, "cores": 1,
+                             "sample": desc}
+    out["c2_random_clifford_n1000_200_layers"] = g
+    c3 = C.surface_code_memory(71)
+    g, (coins, noise) = gpu_rates(sim, B, torch, c3, 1, flush, engine=B.ENGINE_LAYERED)
+    if cpu:
+        ops, meas, desc = oracle_prefix_rate(c3, coins[0], noise[0], 8.0, c3.meta["round_end"])
+        g["cpu_baseline"] = {"kind": "oracle", "ops_per_s": ops, "measurements_per_s": meas, "cores": 1,
+                             "sample": desc}
+    out["c3_d71_noiseless"] = g
+    wide = {}
+    for n in (256, 1024, 2048):
+        cw = C.random_wide_benchmark(n, n, seed=1)
+        g, (coins, noise) = gpu_rates(sim, B, torch, cw, 1, flush, reps=2, engine=B.ENGINE_LAYERED)
+        if cpu:
+            ops, meas, desc = oracle_prefix_rate(cw, coins[0], noise[0], 4.0)
+            g["cpu_baseline"] = {"kind": "oracle", "ops_per_s": ops, "measurements_per_s": meas, "cores": 1,
+                                 "sample": desc}
+        wide[str(n)] = g
+    out["random_wide_n_rounds"] = wide
+    return out
+
+
 # ------------------------------------------------------------------ ranks
 def shot_indices(rank: int, steps: int, warmup: int) -> list:
     """Stream shot indices of one rank: every rank simulates its own shots
@@ -353,6 +460,7 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="replay the serving trace (p50/p99) also when N > 1 (it runs by default at N = 1)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' rates")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -572,9 +680,26 @@ def main():
                 line["batched"]["cpu_baseline"] = oracle_batched()
             except Exception as ex:
                 line["batched"]["cpu_baseline"] = {"error": repr(ex)}
+    if rank == 0 and not args.no_extras and not args.no_configs:
+        try:
+            line["configs"] = config_suite(sim, B, torch, flush, cpu=not args.no_cpu)
+        except Exception as ex:       # report, do not hide
+            line["configs"] = {"error": repr(ex)}
     if rank == 0 and (args.serve or world == 1) and not args.no_serve and not args.no_extras:
         from paper_2507_03092_gb300 import serve_trace
-        line["serve"] = serve_trace.replay(sim, B, torch)
+        circs = serve_trace.compile_circuits(sim)
+        line["serve"] = serve_trace.replay(sim, B, torch, circs=circs)
+        try:
+            sat = serve_trace.saturated(sim, B, torch, circs=circs)
+            pl = serve_trace.plain(sim, B, torch, circs=circs)
+            line["serve"]["saturated"] = sat
+            line["serve"]["capacity_shots_per_s"] = sat["capacity_shots_per_s"]
+            line["serve"]["plain"] = pl
+            line["serve"]["plain_shots_per_s"] = pl["plain_shots_per_s"]
+            if sat["capacity_shots_per_s"]:
+                line["serve"]["served_over_plain"] = sat["capacity_shots_per_s"] / pl["plain_shots_per_s"]
+        except Exception as ex:       # report, do not hide
+            line["serve"]["capacity_error"] = repr(ex)
     sim.close()
     if dist:
         dist.barrier()

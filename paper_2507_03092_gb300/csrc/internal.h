@@ -175,6 +175,7 @@ struct MeasScratch {
     uint16_t *mxs = nullptr;      // [count][max_meas][XSCAP] layer items j with X on q_j in the op's pivot row
     uint8_t *mxn = nullptr;       // [count][max_meas] entries of mxs (XS_OVER: more than XSCAP, XS_UNKNOWN: not computed)
     uint32_t *mxver = nullptr;    // [count][max_meas] version of the pivot row when mxs was computed
+    uint16_t *mpwn = nullptr;     // [count][max_meas] nonzero words of that pivot row
     uint32_t *rowver = nullptr;   // [count][32H] stabilizer-row versions (bumped whenever a row changes)
     uint16_t *qmap = nullptr;     // [count][n] qubit -> item of the current layer (0xffff: none)
     uint32_t *mpiv = nullptr;     // [count][max_meas] cached pivot (slot - 32H) or ~0

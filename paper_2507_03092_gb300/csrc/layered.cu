@@ -72,6 +72,7 @@ struct LArgs {
     uint16_t *mxs;                   // [B][max_meas][XSCAP] pivot-row X support over the layer's items
     uint8_t *mxn;                    // [B][max_meas] its length, XS_OVER or XS_UNKNOWN
     uint32_t *mxver;                 // [B][max_meas] pivot-row version it was computed at
+    uint16_t *mpwn;                  // [B][max_meas] nonzero words of the pivot row (x or z), same version
     uint32_t *rowver;                // [B][32H] stabilizer-row versions
     uint16_t *qmap;                  // [B][n]
     uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
@@ -647,44 +648,71 @@ __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_
 // One warp scans a measured column (CW words): pivot = first set row of the
 // stabilizer half (as slot - 32H, ~0 if none), size = number of set rows, and
 // when size <= SUPCAP the set rows (in no particular order) into sup[].
-// Each lane keeps 8 loads in flight.
+// Columns of a multiple of 4 words (16-byte aligned) are read as 16-byte
+// vectors, 512 words per batch (four per lane in flight, one round trip at
+// d = 71); others as words, 256 per batch.
 __device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ col, uint32_t H, uint32_t CW,
                                                  uint32_t &piv, uint32_t &size, uint16_t *__restrict__ sup) {
     const int lane = threadIdx.x & 31;
     uint32_t base = 0, pv = 0xffffffffu;
-    for (uint32_t w0 = 0; w0 < CW; w0 += 256) {
-        uint32_t v[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const uint32_t w = w0 + 32 * k + lane;
-            v[k] = w < CW ? col[w] : 0u;
-        }
+    // one batch: NV vectors of VW words per lane, word index of vector k, element e:
+    // w = VW * (v0 + 32 k + lane) + e (increasing in k, then e, for a lane)
+    auto batch = [&](const uint32_t (&v)[16], uint32_t wbase, uint32_t stride_w, int nk, int vw) {
         uint32_t c = 0, mine = 0xffffffffu;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            c += __popc(v[k]);
-            const uint32_t w = w0 + 32 * k + lane;
-            if (mine == 0xffffffffu && w >= H && v[k]) mine = 32 * (w - H) + __ffs(v[k]) - 1;
-        }
+        for (int k = 0; k < nk; k++)
+#pragma unroll
+            for (int e = 0; e < vw; e++) {
+                const uint32_t x = v[k * vw + e];
+                c += __popc(x);
+                const uint32_t w = wbase + stride_w * k + e;
+                if (mine == 0xffffffffu && w >= H && x) mine = 32 * (w - H) + __ffs(x) - 1;
+            }
         mine = __reduce_min_sync(FULL_MASK, mine);
         if (pv == 0xffffffffu) pv = mine;
-        uint32_t x = c;
+        uint32_t xs = c;
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
-            if (lane >= o) x += y;
+            const uint32_t y = __shfl_up_sync(FULL_MASK, xs, o);
+            if (lane >= o) xs += y;
         }
-        uint32_t pos = base + x - c;
+        uint32_t pos = base + xs - c;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            uint32_t m = v[k];
-            const uint32_t w = w0 + 32 * k + lane;
-            while (m && pos < SUPCAP) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                sup[pos++] = (uint16_t)(32 * w + b);
+        for (int k = 0; k < nk; k++)
+#pragma unroll
+            for (int e = 0; e < vw; e++) {
+                uint32_t m = v[k * vw + e];
+                const uint32_t w = wbase + stride_w * k + e;
+                while (m && pos < SUPCAP) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    sup[pos++] = (uint16_t)(32 * w + b);
+                }
             }
+        base += __shfl_sync(FULL_MASK, xs, 31);
+    };
+    if ((CW & 3u) == 0 && ((uintptr_t)col & 15u) == 0) {
+        const uint4 *__restrict__ c4 = reinterpret_cast<const uint4 *>(col);
+        const uint32_t n4 = CW >> 2;
+        for (uint32_t v0 = 0; v0 < n4; v0 += 128) {
+            uint32_t v[16];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t j = v0 + 32 * k + lane;
+                const uint4 q = j < n4 ? c4[j] : make_uint4(0u, 0u, 0u, 0u);
+                v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+            }
+            batch(v, 4 * (v0 + lane), 128, 4, 4);
         }
-        base += __shfl_sync(FULL_MASK, x, 31);
+    } else {
+        for (uint32_t w0 = 0; w0 < CW; w0 += 256) {
+            uint32_t v[16];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t w = w0 + 32 * k + lane;
+                v[k] = w < CW ? col[w] : 0u;
+            }
+            batch(v, w0 + lane, 32, 8, 1);
+        }
     }
     piv = pv;
     size = base;
@@ -850,23 +878,25 @@ __device__ __forceinline__ void rowsum_warp_sparse(uint32_t *rm, uint32_t RS, ui
 }
 
 constexpr int RAND_THREADS = 1024;
+constexpr int RAND_WARPS = RAND_THREADS / 32;
 constexpr uint32_t PCAP = WaveCaps::PCAP_MAX;
 constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;
 constexpr uint32_t PAIRCAP = WaveCaps::PAIRCAP_MAX;
 constexpr uint32_t JCAP = WaveCaps::JCAP_MAX;
-constexpr uint32_t HT = 4096;                 // chain hash slots (> PAIRCAP: never full)
+constexpr uint32_t HT = 4096;                 // row hash slots (> PAIRCAP: never full)
 constexpr uint32_t PWS = 4;                   // pivot words staged in shared memory per wave op
+constexpr uint32_t CKEYS = 32 * PWS;          // sort keys of one pass of a multi-pivot row
 constexpr uint16_t NOPIV = 0xffffu;
 constexpr uint16_t HEMPTY = 0xffffu;
 constexpr uint32_t QMAP_SMEM_MAX = 16384;     // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
 static_assert(WCAP <= RAND_THREADS, "one thread per window op");
-static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "chain hash larger than the pair list, power of two");
+static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pair list, power of two");
 
 // k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
 struct RandLayout {
-    uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, pacc, hkey, htail, dlist, ents, spc, spx,
-        spz, qmask, blocked, qmap, stat, stale, r, total;
+    uint32_t pend, wpiv, wbsz, wxn, wpw, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
+        wkeys, wlist, wacc, qmask, blocked, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
     const uint32_t at = o;
@@ -881,20 +911,23 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.wpiv = rl_take(o, 2 * WCAP);
     L.wbsz = rl_take(o, 2 * WCAP);
     L.wxn = rl_take(o, WCAP);
+    L.wpw = rl_take(o, 2 * WCAP);
     L.sel = rl_take(o, 2 * WCAP);
     L.sr = rl_take(o, WCAP);
     L.pwn = rl_take(o, 2 * WCAP);
     L.pairs = rl_take(o, 4 * PAIRCAP);
     L.nxt = rl_take(o, 2 * PAIRCAP);
     L.hslot = rl_take(o, 2 * PAIRCAP);
-    L.pacc = rl_take(o, 4 * PAIRCAP);
+    L.dlist = rl_take(o, 2 * PAIRCAP);
     L.hkey = rl_take(o, 2 * HT);
     L.htail = rl_take(o, 4 * HT);
-    L.dlist = rl_take(o, 2 * PAIRCAP);
     L.ents = rl_take(o, 4 * JCAP);
     L.spc = rl_take(o, 2 * WCAP * PWS);
     L.spx = rl_take(o, 4 * WCAP * PWS);
     L.spz = rl_take(o, 4 * WCAP * PWS);
+    L.wkeys = rl_take(o, 4 * CKEYS * RAND_WARPS);
+    L.wlist = rl_take(o, 2 * 32 * RAND_WARPS);
+    L.wacc = rl_take(o, 4 * 32 * RAND_WARPS);
     L.qmask = rl_take(o, 8 * H);
     L.blocked = rl_take(o, 4 * H);
     L.qmap = rl_take(o, item_smem ? 2 * n : 0u);
@@ -932,6 +965,25 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
     return res;
 }
 
+// Ascending bitonic sort of nk (a power of two, 32..CKEYS) keys in shared
+// memory by one warp.
+__device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = 2; k <= nk; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = lane; t < nk / 2; t += 32) {
+                const uint32_t i = 2 * j * (t / j) + (t % j), l = i + j;     // pair (i, l), i < l
+                const bool up = (i & k) == 0;
+                const uint32_t a = keys[i], b = keys[l];
+                if ((a > b) == up) {
+                    keys[i] = b;
+                    keys[l] = a;
+                }
+            }
+            __syncwarp();
+        }
+}
+
 // The random measurements of one measurement layer of one tableau (one CTA),
 // in waves.  Sequential CHP applies them one by one in circuit order (Sec. 2.4:
 // pivot, rowsum of the pivot into every other row with an X or Y on the
@@ -945,25 +997,28 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
 // columns and a window of up to WCAP pending ops costs the same as a small one.
 //
 // Per wave: (1) ordered list of pending random ops; (2) refresh of stale
-// pivots and X supports of the window; (3) selection: an op is blocked when an
-// earlier window op conflicts with it; (4) work lists: the rowsum pairs
-// (rows of the op's measured column, except its pivot and the destabilizer
-// partners of the wave's pivots, which end as copies of their pivot rows) are
-// linked per row through a shared-memory hash, the pivots' nonzero words are
-// staged in shared memory, and the pending ops whose measured column changes
-// are listed; (5) rowsums (a thread per pair: for each pivot word no earlier
-// pair of its row's chain holds, load the row word once and apply every pivot
-// of the chain holding that word, adding the powers of i), column updates and
-// row copies, which touch disjoint data, in one phase; (6) each row's sign
-// from 2 r + sum 2 r_p + the powers of i, applied at the start of the next
-// wave.  A chain holding a pivot with more than PWS nonzero words is applied
-// by one warp with full or word-listed rowsums before the copies.
+// pivots, X supports and pivot word counts of the window; (3) selection: an
+// op is blocked when an earlier window op conflicts with it; (4) work lists,
+// a warp per wave op: the rowsum pairs (rows of the op's measured column,
+// except its pivot and the destabilizer partners of the wave's pivots, which
+// end as copies of their pivot rows) linked per row through a shared-memory
+// hash, the pivot's nonzero words staged in shared memory, and the pending
+// ops whose measured column changes; (5) a row that receives one pivot gets
+// it from one thread (its few nonzero words loaded once); a row that receives
+// several gets them from one warp, which sorts the (word, chain position)
+// keys of the chain so that every word is loaded once and its pivots applied
+// in chain order -- the same order for every word of the row, which keeps the
+// sum of the powers of i exact; pivots that commute with the row give an even
+// power per pair, so each pair flips the row's sign by (r_p + power / 2) mod 2.
+// Column updates and row copies touch other data and run in the same phase.
+// A chain holding a pivot with more than PWS nonzero words is applied by one
+// warp with full or word-listed rowsums, before the row copies.
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t s_wt[32], s_wcnt[32];
     __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_firstrand, s_nrand, s_any, s_nstale, s_cut;
-    __shared__ uint32_t s_serial, s_ndense;
-    const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr;
+    __shared__ uint32_t s_serial, s_nmulti;
+    const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr, H4 = Hr >> 2;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const Layer M = a.P.layers[layer];
@@ -982,6 +1037,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *const mxs = a.mxs + t * a.m_stride * XSCAP;
     uint8_t *const mxn = a.mxn + t * a.m_stride;
     uint32_t *const mxver = a.mxver + t * a.m_stride;
+    uint16_t *const mpwn = a.mpwn + t * a.m_stride;
     uint32_t *const rowver = a.rowver + (size_t)t * 32 * H;
     uint16_t *const pwl = a.pwl + (size_t)t * WCAP * PWCAP;
     const bool item_smem = n <= QMAP_SMEM_MAX;
@@ -989,20 +1045,23 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *const wpiv = (uint16_t *)(smraw + Lo.wpiv);    // window: pivot (slot - 32H) or NOPIV
     uint16_t *const wbsz = (uint16_t *)(smraw + Lo.wbsz);    // window: |x-column support| (saturated)
     uint8_t *const wxn = smraw + Lo.wxn;                     // window: X-support length / XS_OVER
+    uint16_t *const wpw = (uint16_t *)(smraw + Lo.wpw);      // window: nonzero words of the pivot row
     uint16_t *const sel = (uint16_t *)(smraw + Lo.sel);      // wave: window positions
     uint8_t *const sr = smraw + Lo.sr;                       // wave: pivot sign before the wave
     uint16_t *const pwn = (uint16_t *)(smraw + Lo.pwn);      // wave: nonzero words of the pivot row
     uint32_t *const pairs = (uint32_t *)(smraw + Lo.pairs);  // row | wave index << 16
     uint16_t *const nxt = (uint16_t *)(smraw + Lo.nxt);      // next pair of the same row (0xffff ends)
     uint16_t *const hslot = (uint16_t *)(smraw + Lo.hslot);  // hash slot of the pair's row
-    int *const pacc = (int *)(smraw + Lo.pacc);              // powers of i summed per chain (at its first pair)
+    uint16_t *const dlist = (uint16_t *)(smraw + Lo.dlist);  // rows (first pairs) applied by warps
     uint16_t *const hkey = (uint16_t *)(smraw + Lo.hkey);    // hash: row
     uint32_t *const htail = (uint32_t *)(smraw + Lo.htail);  // hash: first pair of the row's chain
-    uint16_t *const dlist = (uint16_t *)(smraw + Lo.dlist);  // chains applied by warps
     uint32_t *const ents = (uint32_t *)(smraw + Lo.ents);    // item | wave index << 16 | bp << 31
     uint16_t *const spc = (uint16_t *)(smraw + Lo.spc);      // wave pivots' nonzero words: index,
     uint32_t *const spx = (uint32_t *)(smraw + Lo.spx);      //   x word
     uint32_t *const spz = (uint32_t *)(smraw + Lo.spz);      //   z word
+    uint32_t *const wkeys = (uint32_t *)(smraw + Lo.wkeys) + warp * CKEYS;   // per warp: sort keys
+    uint16_t *const wlist = (uint16_t *)(smraw + Lo.wlist) + warp * 32;      //   chain pairs of a pass
+    int *const wacc = (int *)(smraw + Lo.wacc) + warp * 32;                 //   powers of i per pair
     uint32_t *const qmask = (uint32_t *)(smraw + Lo.qmask);  // destabilizer partners of the wave's pivots
     uint32_t *const blocked = (uint32_t *)(smraw + Lo.blocked);   // per item: an earlier window op conflicts
     uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
@@ -1027,10 +1086,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             stat[i] = gstat[i];
             mstale[i] = gmstale[i];
         }
-    for (uint32_t h = threadIdx.x; h < HT; h += blockDim.x) {
-        hkey[h] = HEMPTY;
-        htail[h] = 0xffffffffu;
-    }
+    wacc[lane] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
     __syncthreads();
@@ -1044,36 +1100,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             tlast = now_;                                                     \
         }                                                                     \
     } while (0)
-    // the chain of pair e, from its first pair
     auto chain_first = [&](uint32_t e) { return htail[hslot[e]]; };
-    auto pivot_has = [&](uint32_t x, uint32_t c, uint32_t &px, uint32_t &pz) {
-        const uint32_t m = pwn[x];
-        for (uint32_t w = 0; w < m && w < PWS; w++)
-            if (spc[x * PWS + w] == c) {
-                px = spx[x * PWS + w];
-                pz = spz[x * PWS + w];
-                return true;
-            }
-        return false;
-    };
-    // (6) signs of the previous wave's word-task chains: 2 r + sum 2 r_p + the
-    // powers of i, set once per row by the thread of the chain's first pair
-    uint32_t prev_npair = 0;
-    bool signs_pending = false;          // block-uniform
-    auto chain_signs = [&]() {
-        for (uint32_t e = threadIdx.x; e < prev_npair; e += blockDim.x) {
-            if (chain_first(e) != e) continue;
-            bool dense = false;
-            for (uint32_t f = e; f != 0xffffu; f = nxt[f]) dense |= pwn[pairs[f] >> 16] > PWS;
-            if (dense) continue;                       // its warp has set the sign
-            const uint32_t row = pairs[e] & 0xffffu;
-            const uint32_t r_s = rbit(r, row);
-            int ev = (int)(2 * r_s) + pacc[e];
-            for (uint32_t f = e; f != 0xffffu; f = nxt[f]) ev += 2 * (int)sr[pairs[f] >> 16];
-            if (ev & 1) set_err(a.err, DERR_ODD_PHASE);
-            if ((uint32_t)((ev & 3) >> 1) != r_s) atomicXor(&r[row >> 5], 1u << (row & 31));
-            if (row >= 32 * H) rowver[row - 32 * H]++;
-        }
+    // a pair's sign flip: its pivot's sign plus half its (even) power of i
+    auto pair_flip = [&](uint32_t x, int acc) -> uint32_t {
+        if (acc & 1) set_err(a.err, DERR_ODD_PHASE);
+        return (sr[x] + (uint32_t)((acc & 3) >> 1)) & 1u;
     };
 
     bool full_scan = true;          // pending list rebuilt from all items (first wave, or overflow)
@@ -1081,11 +1112,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // qualifies), so 2*count+3 passes bound the loop; exceeding it is a bug
     const uint32_t glimit = min(2 * M.count + 3, a.caps.wave_limit);
     for (uint32_t guard = 0;; guard++) {
-        if (signs_pending) {
-            chain_signs();
-            signs_pending = false;
-        }
-        PHASE(5);
         if (guard >= glimit) {
             if (threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
             break;
@@ -1126,8 +1152,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 for (uint32_t d = 0; d < 8; d++)
                     if (d < cnt) pend[off + d] = keep[d];
             }
-            // the previous wave's chain hash is no longer read (its signs were
-            // applied before the scan's barriers)
             for (uint32_t h = threadIdx.x; h < HT; h += blockDim.x) {
                 hkey[h] = HEMPTY;
                 htail[h] = 0xffffffffu;
@@ -1138,7 +1162,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 s_np = min(s_tot, pcap);
                 s_nsel = 0; s_npair = 0; s_nent = 0; s_nstale = 0;
                 s_firstrand = 0xffffffffu; s_nrand = 0; s_cut = 0xffffffffu;
-                s_serial = 0; s_ndense = 0;
+                s_serial = 0; s_nmulti = 0;
             }
             __syncthreads();
         }
@@ -1155,14 +1179,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 pairs[atomicAdd(&s_nstale, 1u)] = k | 0x80000000u;
                 continue;
             }
-            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
+            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i], pw = mpwn[i];
             wpiv[k] = (uint16_t)pv;
             wbsz[k] = (uint16_t)min(bs, 65535u);
             wxn[k] = (uint8_t)xn;
+            wpw[k] = (uint16_t)pw;
             if (xn == XS_UNKNOWN || rowver[pv] != xv) pairs[atomicAdd(&s_nstale, 1u)] = k;
         }
         for (uint32_t w = (wfirst >> 5) + threadIdx.x; w <= (wlast >> 5); w += blockDim.x) blocked[w] = 0u;
-        if (lane == 0) s_wcnt[warp] = 0;
         __syncthreads();
         {
             const uint32_t nst = s_nstale;
@@ -1191,40 +1215,54 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 } else {
                     pv = wpiv[k];
                 }
-                // X support of the pivot row over the layer's items
+                // X support of the pivot row over the layer's items, and its
+                // nonzero words (x or z): 16-byte vectors of both planes
                 const uint32_t ver = rowver[pv];
-                const uint32_t *__restrict__ prow = rm + (size_t)(32 * H + pv) * RS;
+                const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)(32 * H + pv) * RS);
+                const uint4 *__restrict__ pz4 = px4 + H4;
                 if (lane == 0) s_wcnt[warp] = 0;
                 __syncwarp();
-                for (uint32_t c0 = 0; c0 < H; c0 += 32 * 8) {
-                    uint32_t v[8];
+                uint32_t nzw = 0;
+                for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
+                    uint4 vx[2], vz[2];
 #pragma unroll
-                    for (int kk = 0; kk < 8; kk++) {
-                        const uint32_t c = c0 + 32 * kk + lane;
-                        v[kk] = c < H ? prow[c] : 0u;
+                    for (int kk = 0; kk < 2; kk++) {
+                        const uint32_t j = j0 + 32 * kk + lane;
+                        vx[kk] = j < H4 ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
+                        vz[kk] = j < H4 ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
                     }
 #pragma unroll
-                    for (int kk = 0; kk < 8; kk++) {
-                        uint32_t m = v[kk];
-                        const uint32_t c = c0 + 32 * kk + lane;
-                        while (m) {
-                            const int b = __ffs(m) - 1;
-                            m &= m - 1;
-                            const uint32_t u = 32 * c + b;
-                            const uint32_t j = u < n ? qmap[u] : 0xffffu;
-                            if (j == 0xffffu) continue;
-                            const uint32_t pos = atomicAdd(&s_wcnt[warp], 1u);
-                            if (pos < XSCAP) mxs[(size_t)i * XSCAP + pos] = (uint16_t)j;
+                    for (int kk = 0; kk < 2; kk++) {
+                        const uint32_t j = j0 + 32 * kk + lane;
+                        const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
+                        const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            nzw += (xw[e] | zw[e]) != 0u;
+                            uint32_t m = xw[e];
+                            while (m) {
+                                const int b = __ffs(m) - 1;
+                                m &= m - 1;
+                                const uint32_t u = 32 * (4 * j + e) + b;
+                                const uint32_t jj = u < n ? qmap[u] : 0xffffu;
+                                if (jj == 0xffffu) continue;
+                                const uint32_t pos = atomicAdd(&s_wcnt[warp], 1u);
+                                if (pos < XSCAP) mxs[(size_t)i * XSCAP + pos] = (uint16_t)jj;
+                            }
                         }
                     }
                 }
+                nzw = __reduce_add_sync(FULL_MASK, nzw);
                 __syncwarp();
                 if (lane == 0) {
                     const uint32_t cnt = s_wcnt[warp];
                     const uint8_t xn = cnt <= XSCAP ? (uint8_t)cnt : XS_OVER;
+                    const uint16_t pw = (uint16_t)min(nzw, 0xffffu);
                     mxn[i] = xn;
                     mxver[i] = ver;
+                    mpwn[i] = pw;
                     wxn[k] = xn;
+                    wpw[k] = pw;
                     count(a, DC_XS_RECOMP, 1);
                 }
                 __syncwarp();
@@ -1268,6 +1306,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     sel[idx] = (uint16_t)k;
                     stat[i] = MS_WAVE;
                     atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
+                    if (wpw[k] > PWS) s_serial = 1;
                 }
             }
         }
@@ -1278,6 +1317,73 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
             const uint32_t k = sel[x], i = pend[k];
             const uint32_t q = wpiv[k], p = 32 * H + q;
+            // pending ops whose qubit has X or Y in row p or row q (their
+            // measured columns change), and the nonzero words of row p: 16-byte
+            // vectors of rows p (x, z) and q (x)
+            const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
+            const uint4 *__restrict__ pz4 = px4 + H4;
+            const uint4 *__restrict__ qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
+            uint32_t nzcnt = 0;
+            for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
+                uint4 vx[2], vz[2], vq[2];
+#pragma unroll
+                for (int kk = 0; kk < 2; kk++) {
+                    const uint32_t j = j0 + 32 * kk + lane;
+                    const bool in = j < H4;
+                    vx[kk] = in ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
+                    vz[kk] = in ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
+                    vq[kk] = in ? qx4[j] : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int kk = 0; kk < 2; kk++) {
+                    const uint32_t j = j0 + 32 * kk + lane;
+                    const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
+                    const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
+                    const uint32_t qw[4] = {vq[kk].x, vq[kk].y, vq[kk].z, vq[kk].w};
+                    uint32_t mine = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        mine += (xw[e] | zw[e]) != 0u;
+                        uint32_t mm = xw[e] | qw[e];
+                        while (mm) {
+                            const int b = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            const uint32_t u = 32 * (4 * j + e) + b;
+                            const uint32_t jj = u < n ? qmap[u] : 0xffffu;
+                            if (jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE)) {
+                                const uint32_t f = atomicAdd(&s_nent, 1u);
+                                if (f < jcap) ents[f] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
+                            }
+                        }
+                    }
+                    uint32_t incl = mine;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    uint32_t pos = nzcnt + incl - mine;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        if ((xw[e] | zw[e]) == 0u) continue;
+                        const uint32_t c = 4 * j + e;
+                        if (pos < PWCAP) pwl[x * PWCAP + pos] = (uint16_t)c;
+                        if (pos < PWS) {
+                            spc[x * PWS + pos] = (uint16_t)c;
+                            spx[x * PWS + pos] = xw[e];
+                            spz[x * PWS + pos] = zw[e];
+                        }
+                        pos++;
+                    }
+                    nzcnt += __shfl_sync(FULL_MASK, incl, 31);
+                }
+            }
+            if (lane == 0) {
+                pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
+                sr[x] = (uint8_t)rbit(r, p);
+                if (nzcnt > PWS) s_serial = 1;
+                dirty[p >> 5] = 1;
+                dirty[q >> 5] = 1;
+            }
             // rowsum pairs: rows of the measured column except the pivot and
             // the wave's destabilizer partners, linked per row
             auto add_pair = [&](uint32_t row) {
@@ -1286,7 +1392,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 const uint32_t f = atomicAdd(&s_npair, 1u);
                 if (f >= paircap) return;
                 pairs[f] = row | (x << 16);
-                pacc[f] = 0;
                 uint32_t h = (row * 2654435761u) >> 20;       // HT = 4096 slots
                 uint32_t probe = 0;
                 for (; probe < HT; probe++) {
@@ -1318,53 +1423,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     }
                 }
             }
-            // pending ops whose qubit has X or Y in row p or row q (their
-            // measured columns change), and the nonzero words of row p
-            const uint32_t *__restrict__ rp_ = rm + (size_t)p * RS;
-            const uint32_t *__restrict__ rq_ = rm + (size_t)q * RS;
-            uint32_t nzcnt = 0;
-            for (uint32_t c0 = 0; c0 < H; c0 += 32 * 6) {
-                uint32_t xp[6], zp[6], xq[6];
-#pragma unroll
-                for (int kk = 0; kk < 6; kk++) {
-                    const uint32_t c = c0 + 32 * kk + lane;
-                    xp[kk] = c < H ? rp_[c] : 0u;
-                    zp[kk] = c < H ? rp_[Hr + c] : 0u;
-                    xq[kk] = c < H ? rq_[c] : 0u;
-                }
-#pragma unroll
-                for (int kk = 0; kk < 6; kk++) {
-                    const uint32_t c = c0 + 32 * kk + lane;
-                    uint32_t mm = xp[kk] | xq[kk];
-                    while (mm) {
-                        const int b = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        const uint32_t u = 32 * c + b;
-                        const uint32_t j = u < n ? qmap[u] : 0xffffu;
-                        if (j != 0xffffu && (stat[j] == MS_RANDOM || stat[j] == MS_DETLATE)) {
-                            const uint32_t f = atomicAdd(&s_nent, 1u);
-                            if (f < jcap) ents[f] = j | (x << 16) | (((xp[kk] >> b) & 1u) << 31);
-                        }
-                    }
-                    const bool nzw = (xp[kk] | zp[kk]) != 0u;
-                    const uint32_t m = __ballot_sync(FULL_MASK, nzw);
-                    const uint32_t pos = nzcnt + __popc(m & ((1u << lane) - 1u));
-                    if (nzw && pos < PWCAP) pwl[x * PWCAP + pos] = (uint16_t)c;
-                    if (nzw && pos < PWS) {
-                        spc[x * PWS + pos] = (uint16_t)c;
-                        spx[x * PWS + pos] = xp[kk];
-                        spz[x * PWS + pos] = zp[kk];
-                    }
-                    nzcnt += __popc(m);
-                }
-            }
-            if (lane == 0) {
-                pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
-                sr[x] = (uint8_t)rbit(r, p);
-                if (nzcnt > PWS) s_serial = 1;
-                dirty[p >> 5] = 1;
-                dirty[q >> 5] = 1;
-            }
         }
         __syncthreads();
         PHASE(3);
@@ -1378,35 +1436,59 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // serial: a dense pivot, or an overflowed list whose fallback reads
         // pivot rows from the tableau -- the row copies wait for them
         const bool serial = s_serial || npair > paircap || nent > jcap;
-        // ---- (5a) rowsums of chains whose pivots are all staged: a thread per pair
+        // row copies: row q <- row p, row p <- +-Z_a (16-byte words over the
+        // Hr-word rows; the words past H are zero in every row), and the outcome
+        auto row_copies = [&]() {
+            for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+                const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
+                const MItem m = a.P.mitems[M.first + i];
+                const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
+                                                               : coin_bit(a.call->st, t, m.coin);
+                const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
+                uint4 *__restrict__ dq = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+#pragma unroll 4
+                for (uint32_t c = lane; c < H4; c += 32) {
+                    const uint4 xv = src[c], zv = src[H4 + c];
+                    dq[c] = xv;
+                    dq[H4 + c] = zv;
+                }
+                __syncwarp();
+                uint4 *dp = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
+                const uint32_t za = 1u << (m.q & 31), zsub = (m.q >> 5) & 3u;
+                for (uint32_t c = lane; c < H4; c += 32) {
+                    dp[c] = make_uint4(0u, 0u, 0u, 0u);
+                    const bool here = c == (m.q >> 7);
+                    dp[H4 + c] = make_uint4(here && zsub == 0 ? za : 0u, here && zsub == 1 ? za : 0u,
+                                            here && zsub == 2 ? za : 0u, here && zsub == 3 ? za : 0u);
+                }
+                if (lane == 0) {
+                    if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
+                    else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
+                    if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
+                    else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
+                    rowver[q]++;
+                    out[i] = (uint8_t)coin;
+                    stat[i] = MS_DONE;
+                    write_record(a, t, m.rec, coin);
+                    outcome_flips(a, t, layer, m, coin);
+                }
+            }
+        };
+        // ---- (5a) rows with one pivot: a thread each; the others listed for warps
         if (npair <= paircap) {
             for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
                 const uint32_t f0 = chain_first(e);
-                bool dense = false;
-                for (uint32_t f = f0; f != 0xffffu; f = nxt[f]) dense |= pwn[pairs[f] >> 16] > PWS;
-                if (dense) {
-                    if (f0 == e) dlist[atomicAdd(&s_ndense, 1u)] = (uint16_t)e;
+                const uint32_t x = pairs[e] >> 16, row = pairs[e] & 0xffffu;
+                const uint32_t nwd = pwn[x];
+                if (f0 != e || nxt[e] != 0xffffu || nwd > PWS) {
+                    if (f0 == e) dlist[atomicAdd(&s_nmulti, 1u)] = (uint16_t)e;
                     continue;
                 }
-                const uint32_t row = pairs[e] & 0xffffu, x = pairs[e] >> 16;
-                const uint32_t nwd = pwn[x];
-                // the words of this pair's pivot that no earlier pair of the chain holds
-                uint32_t own = 0;
-                for (uint32_t w = 0; w < nwd; w++) {
-                    const uint32_t c = spc[x * PWS + w];
-                    bool first = true;
-                    for (uint32_t f = f0; f != e; f = nxt[f]) {
-                        uint32_t px_, pz_;
-                        if (pivot_has(pairs[f] >> 16, c, px_, pz_)) { first = false; break; }
-                    }
-                    if (first) own |= 1u << w;
-                }
-                if (!own) continue;
                 uint32_t *rs = rm + (size_t)row * RS;
                 uint32_t xs[PWS], zs[PWS];
 #pragma unroll
                 for (uint32_t w = 0; w < PWS; w++) {
-                    const bool o = (own >> w) & 1u;
+                    const bool o = w < nwd;
                     const uint32_t c = o ? spc[x * PWS + w] : 0u;
                     xs[w] = o ? rs[c] : 0u;
                     zs[w] = o ? rs[Hr + c] : 0u;
@@ -1414,20 +1496,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 int acc = 0;
 #pragma unroll
                 for (uint32_t w = 0; w < PWS; w++) {
-                    if (!((own >> w) & 1u)) continue;
-                    const uint32_t c = spc[x * PWS + w];
-                    uint32_t xv = xs[w], zv = zs[w];
-                    for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
-                        uint32_t px_, pz_;
-                        if (!pivot_has(pairs[f] >> 16, c, px_, pz_)) continue;
-                        acc += phase_word(px_, pz_, xv, zv);
-                        xv ^= px_;
-                        zv ^= pz_;
-                    }
-                    rs[c] = xv;
-                    rs[Hr + c] = zv;
+                    if (w >= nwd) continue;
+                    const uint32_t c = spc[x * PWS + w], px_ = spx[x * PWS + w], pz_ = spz[x * PWS + w];
+                    acc += phase_word(px_, pz_, xs[w], zs[w]);
+                    rs[c] = xs[w] ^ px_;
+                    rs[Hr + c] = zs[w] ^ pz_;
                 }
-                if (acc) atomicAdd(&pacc[f0], acc);
+                if (pair_flip(x, acc)) atomicXor(&r[row >> 5], 1u << (row & 31));
+                if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
             }
         }
         // ---- (5b) measured columns of the remaining ops: x ^= x_{p,b} on the
@@ -1492,87 +1568,111 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 if (lane == 0) mstale[j] = 1;
             }
         }
-        if (serial) {
-            __syncthreads();
-            // chains holding a dense pivot: one warp per chain, pivots in chain
-            // order (pivot signs still unchanged: the copies come after)
-            if (npair <= paircap) {
-                const uint32_t nd = s_ndense;
-                for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) {
-                    const uint32_t e = dlist[d], row = pairs[e] & 0xffffu;
-                    for (uint32_t f = e; f != 0xffffu; f = nxt[f]) {
+        if (!serial) row_copies();               // pivots are staged: copies may overwrite them
+        __syncthreads();
+        // ---- (5c) rows with several pivots (or a dense one): a warp each
+        if (npair <= paircap) {
+            const uint32_t nm = s_nmulti;
+            for (uint32_t d = (uint32_t)warp; d < nm; d += (uint32_t)nw) {
+                const uint32_t e0 = dlist[d], row = pairs[e0] & 0xffffu;
+                bool dense = false;
+                for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++)
+                    dense |= pwn[pairs[f] >> 16] > PWS;
+                if (dense) {
+                    // pivots in chain order with warp rowsums (signs set inside;
+                    // pivot rows unchanged: the copies come after in this case)
+                    for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++) {
                         const uint32_t x = pairs[f] >> 16, p = 32 * H + wpiv[sel[x]];
                         if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
                         else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
                         __syncwarp();
                     }
-                    if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+                    if (lane == 0 && row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
+                    continue;
                 }
-            } else {
-                // pair-list overflow: one warp applies the pivots row by row, in wave order
-                for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
-                    for (uint32_t x = 0; x < nsel; x++) {
-                        const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                        uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
-                        if (w == (p >> 5)) m &= ~(1u << (p & 31));
-                        while (m) {
-                            const int b = __ffs(m) - 1;
-                            m &= m - 1;
-                            const uint32_t row = 32 * w + b;
-                            rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
-                            __syncwarp();
-                            if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+                uint32_t *rs = rm + (size_t)row * RS;
+                uint32_t cur = e0, flips = 0;
+                for (uint32_t pass = 0; cur < PAIRCAP && pass < PAIRCAP; pass++) {
+                    // up to 32 pairs of the chain, in chain order
+                    uint32_t cnt = 0;
+                    if (lane == 0) {
+                        while (cur < PAIRCAP && cnt < 32) {
+                            wlist[cnt++] = (uint16_t)cur;
+                            cur = nxt[cur];
                         }
+                    }
+                    cur = __shfl_sync(FULL_MASK, cur, 0);
+                    cnt = __shfl_sync(FULL_MASK, cnt, 0);
+                    __syncwarp();
+                    // sort keys (word, chain position, word slot)
+                    uint32_t nk = 32;
+                    while (nk < PWS * cnt) nk <<= 1;
+                    const uint32_t lx = (uint32_t)lane < cnt ? pairs[wlist[lane]] >> 16 : 0u;
+                    const uint32_t lnw = (uint32_t)lane < cnt ? pwn[lx] : 0u;
+                    for (uint32_t idx = lane; idx < nk; idx += 32) wkeys[idx] = 0xffffffffu;
+                    __syncwarp();
+#pragma unroll
+                    for (uint32_t w = 0; w < PWS; w++)
+                        if (w < lnw) wkeys[PWS * lane + w] = ((uint32_t)spc[lx * PWS + w] << 7) | ((uint32_t)lane << 2) | w;
+                    __syncwarp();
+                    warp_sort_keys(wkeys, nk);
+                    // each word's first key leads: loads the row word once and
+                    // applies the pivots holding that word, in chain order
+                    for (uint32_t idx = lane; idx < nk; idx += 32) {
+                        const uint32_t key = wkeys[idx];
+                        if (key == 0xffffffffu || (idx > 0 && (wkeys[idx - 1] >> 7) == (key >> 7))) continue;
+                        const uint32_t c = key >> 7;
+                        uint32_t xv = rs[c], zv = rs[Hr + c];
+                        for (uint32_t g = idx; g < nk && (wkeys[g] >> 7) == c; g++) {
+                            const uint32_t kg = wkeys[g], ml = (kg >> 2) & 31u, ms = kg & 3u;
+                            const uint32_t gx = pairs[wlist[ml]] >> 16;
+                            const uint32_t px_ = spx[gx * PWS + ms], pz_ = spz[gx * PWS + ms];
+                            atomicAdd(&wacc[ml], phase_word(px_, pz_, xv, zv));
+                            xv ^= px_;
+                            zv ^= pz_;
+                        }
+                        rs[c] = xv;
+                        rs[Hr + c] = zv;
+                    }
+                    __syncwarp();
+                    if ((uint32_t)lane < cnt) {
+                        flips ^= pair_flip(lx, wacc[lane]);
+                        wacc[lane] = 0;
+                    }
+                    __syncwarp();
+                }
+                flips = __reduce_xor_sync(FULL_MASK, flips);
+                if (lane == 0) {
+                    if (flips) atomicXor(&r[row >> 5], 1u << (row & 31));
+                    if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
+                }
+            }
+        } else {
+            // pair-list overflow: one warp applies the pivots row by row, in wave order
+            for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
+                for (uint32_t x = 0; x < nsel; x++) {
+                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                    uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
+                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const uint32_t row = 32 * w + b;
+                        rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                        __syncwarp();
+                        if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
                     }
                 }
             }
-            __syncthreads();
         }
-        // ---- (5c) row copies: row q <- row p, row p <- +-Z_a (16-byte words
-        // over the Hr-word rows; the words past H are zero in every row), and
-        // the outcome
-        for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
-            const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
-            const MItem m = a.P.mitems[M.first + i];
-            const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
-                                                           : coin_bit(a.call->st, t, m.coin);
-            const uint32_t H4 = Hr >> 2;
-            const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
-            uint4 *__restrict__ dq = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
-#pragma unroll 4
-            for (uint32_t c = lane; c < H4; c += 32) {
-                const uint4 xv = src[c], zv = src[H4 + c];
-                dq[c] = xv;
-                dq[H4 + c] = zv;
-            }
-            __syncwarp();
-            uint4 *dp = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
-            const uint32_t za = 1u << (m.q & 31), zsub = (m.q >> 5) & 3u;
-            for (uint32_t c = lane; c < H4; c += 32) {
-                dp[c] = make_uint4(0u, 0u, 0u, 0u);
-                const bool here = c == (m.q >> 7);
-                dp[H4 + c] = make_uint4(here && zsub == 0 ? za : 0u, here && zsub == 1 ? za : 0u,
-                                        here && zsub == 2 ? za : 0u, here && zsub == 3 ? za : 0u);
-            }
-            if (lane == 0) {
-                if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
-                else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
-                if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
-                else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
-                rowver[q]++;
-                out[i] = (uint8_t)coin;
-                stat[i] = MS_DONE;
-                write_record(a, t, m.rec, coin);
-                outcome_flips(a, t, layer, m, coin);
-            }
+        if (serial) {
+            __syncthreads();
+            row_copies();
         }
         __syncthreads();
         PHASE(4);
-        prev_npair = npair <= paircap ? npair : 0u;
-        signs_pending = prev_npair > 0;
     }
 #undef PHASE
-    if (signs_pending) chain_signs();
     __syncthreads();
     for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
     if (item_smem)
@@ -1680,6 +1780,7 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err)
         a.mxs = ms->mxs;
         a.mxn = ms->mxn;
         a.mxver = ms->mxver;
+        a.mpwn = ms->mpwn;
         a.rowver = ms->rowver;
         a.qmap = ms->qmap;
         a.ev = ms->ev;

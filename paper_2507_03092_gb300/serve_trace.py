@@ -120,3 +120,60 @@ def replay(sim, B, torch, rate=200.0, duration=60.0, seed=0, distances=DISTANCES
         out["records"] = {r.idx: B.records_to_numpy(buf) for r, buf in zip(trace, bufs)}
         out["trace"] = trace
     return out
+
+
+def saturated(sim, B, torch, n_requests=2000, seed=0, distances=DISTANCES, max_shots=256, p=1e-3,
+              hbm_budget=64 << 30, n_streams=16, max_inflight=64, max_batch_requests=32, circs=None):
+    """Capacity: the first ``n_requests`` requests of the trace submitted all
+    at once (an offered rate far above what the loop can serve), shots/s =
+    their shots / the time until the last one completes."""
+    trace = make_trace(200.0, 2.0 * n_requests / 200.0 + 10.0, seed, distances, max_shots)[:n_requests]
+    circs = circs or compile_circuits(sim, distances, p)
+    bufs = [sim.record_buffer(r.shots, circs[r.d][0].record_words) for r in trace]
+    B.stab_serve_start(sim.ctx, hbm_budget, max_inflight=max_inflight, n_streams=n_streams,
+                       max_batch_requests=max_batch_requests)
+    done = {}
+    t0 = time.monotonic()
+    try:
+        for r, buf in zip(trace, bufs):
+            B.stab_serve_submit(sim.ctx, circs[r.d][1], r.shots, r.seed, 0, buf)
+        B.stab_serve_drain(sim.ctx, timeout_s=3600.0)
+        for st in B.stab_serve_poll(sim.ctx):
+            done[st["req_id"]] = st
+    finally:
+        B.stab_serve_stop(sim.ctx)
+    ok = [st for st in done.values() if st["status"] == 0]
+    span = max(st["t_done"] for st in ok) - t0 if ok else float("nan")
+    shots = sum(r.shots for r in trace)
+    lat = np.array([st["t_done"] - st["t_submit"] for st in ok])
+    return {"requests": len(trace), "failed": len(trace) - len(ok), "shots": shots,
+            "makespan_s": span, "capacity_shots_per_s": shots / span if span > 0 else None,
+            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "offered": "all requests submitted at t = 0"}
+
+
+def plain(sim, B, torch, n_requests=200, seed=0, distances=DISTANCES, max_shots=256, p=1e-3, circs=None):
+    """The plain path on the same mix: one tableau per launch sequence (the
+    layered engine, one shot per stab_sample call, synchronised), timed on
+    one shot of each of the first ``n_requests`` requests; a request's time is
+    its shot count times that per-shot time, so shots/s = shots / sum of
+    request times over the sample."""
+    trace = make_trace(200.0, 2.0 * n_requests / 200.0 + 10.0, seed, distances, max_shots)[:n_requests]
+    circs = circs or compile_circuits(sim, distances, p)
+    per_d = {}
+    for d in sorted({r.d for r in trace}):
+        c, cid = circs[d]
+        rec = sim.record_buffer(1, c.record_words)
+        sim.sample(cid, c, 1, seed=1, engine=B.ENGINE_LAYERED, out=rec)     # warm-up
+        sim.sync()
+        t0 = time.perf_counter()
+        for k in range(3):
+            sim.sample(cid, c, 1, seed=2, shot_offset=k, engine=B.ENGINE_LAYERED, out=rec)
+            sim.sync()
+        per_d[d] = (time.perf_counter() - t0) / 3
+    tot_t = sum(r.shots * per_d[r.d] for r in trace)
+    shots = sum(r.shots for r in trace)
+    return {"requests_sampled": len(trace), "shots": shots, "plain_shots_per_s": shots / tot_t,
+            "per_shot_ms": {str(d): round(1e3 * v, 3) for d, v in per_d.items()},
+            "method": "layered engine, one shot per synchronised stab_sample call, host wall time"}
