@@ -144,7 +144,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t mm = std::max<uint32_t>(1, p.dev.max_meas);
     const size_t words = mm * p.CW * count, items = mm * count;
-    const size_t mxs_b = 2 * (size_t)XSCAP * items, mxn_b = items, mxver_b = 4 * items, mpwn_b = 2 * items;
+    const size_t mxs_b = 2 * (size_t)XSCAP * items, mxn_b = items, mxver_b = 4 * items;
     const size_t rowver_b = 4 * (size_t)32 * p.H * count;
     const size_t qmap_b = 2 * (size_t)p.n * count;
     const size_t piv_b = 4 * items, bsz_b = 4 * items, stale_b = items;
@@ -153,7 +153,7 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     const size_t flips_b = 4 * 2 * items;
     const size_t ev_b = 4 * (size_t)std::max<uint32_t>(1, p.dev.ev_total) * count;
     const size_t cnt_b = 4 * (size_t)std::max<size_t>(1, p.layers.size()) * count;
-    const size_t bytes = up(4 * words) + up(2 * items) + up(mxs_b) + up(mxn_b) + up(mxver_b) + up(mpwn_b) + up(rowver_b) +
+    const size_t bytes = up(4 * words) + up(2 * items) + up(mxs_b) + up(mxn_b) + up(mxver_b) + up(rowver_b) +
                          up(ev_b) + up(cnt_b) +
                          up(qmap_b) + up(piv_b) + up(bsz_b) + up(stale_b) + up(sup_b) + up(pwl_b) +
                          up(flips_b) + up(cnt_b) + up(sizeof(CallArgs));
@@ -166,7 +166,6 @@ static int ensure_ms(MeasScratch &ms, DevBuf &buf, const HostProg &p, uint32_t c
     ms.mxs = (uint16_t *)b; b += up(mxs_b);
     ms.mxn = (uint8_t *)b; b += up(mxn_b);
     ms.mxver = (uint32_t *)b; b += up(mxver_b);
-    ms.mpwn = (uint16_t *)b; b += up(mpwn_b);
     ms.rowver = (uint32_t *)b; b += up(rowver_b);
     ms.ev = (uint32_t *)b; b += up(ev_b);
     ms.ev_cnt = (uint32_t *)b; b += up(cnt_b);

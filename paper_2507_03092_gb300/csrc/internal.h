@@ -175,7 +175,6 @@ struct MeasScratch {
     uint16_t *mxs = nullptr;      // [count][max_meas][XSCAP] layer items j with X on q_j in the op's pivot row
     uint8_t *mxn = nullptr;       // [count][max_meas] entries of mxs (XS_OVER: more than XSCAP, XS_UNKNOWN: not computed)
     uint32_t *mxver = nullptr;    // [count][max_meas] version of the pivot row when mxs was computed
-    uint16_t *mpwn = nullptr;     // [count][max_meas] nonzero words of that pivot row
     uint32_t *rowver = nullptr;   // [count][32H] stabilizer-row versions (bumped whenever a row changes)
     uint16_t *qmap = nullptr;     // [count][n] qubit -> item of the current layer (0xffff: none)
     uint32_t *mpiv = nullptr;     // [count][max_meas] cached pivot (slot - 32H) or ~0
@@ -299,8 +298,9 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
 
 // device counters (unsigned long long) kept next to the error flag
 // DC_PHASE0 + k: SM cycles of k_meas_rand's per-wave phase k (0 pending list,
-// 1 pivot and X-support refresh, 2 selection, 3 work lists, 4 rowsums +
-// column updates + row copies, 5 chain signs)
+// 1 cached-state pass, 2 column rescans, 3 X-support rescans, 4 selection,
+// 5 work lists, 6 single-pivot rows + column updates + row copies,
+// 7 multi-pivot rows)
 enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
              DC_PIV_RECOMP = 6, DC_ROWSUM_PASSES = 7, DC_PHASE0 = 8, DC_N_PHASES = 11,
              DC_XS_RECOMP = 19, DC_N = 24 };

@@ -72,7 +72,6 @@ struct LArgs {
     uint16_t *mxs;                   // [B][max_meas][XSCAP] pivot-row X support over the layer's items
     uint8_t *mxn;                    // [B][max_meas] its length, XS_OVER or XS_UNKNOWN
     uint32_t *mxver;                 // [B][max_meas] pivot-row version it was computed at
-    uint16_t *mpwn;                  // [B][max_meas] nonzero words of the pivot row (x or z), same version
     uint32_t *rowver;                // [B][32H] stabilizer-row versions
     uint16_t *qmap;                  // [B][n]
     uint32_t *ev, *ev_cnt;           // [B][ev_total], [B][n_layers]
@@ -895,7 +894,7 @@ static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pa
 
 // k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
 struct RandLayout {
-    uint32_t pend, wpiv, wbsz, wxn, wpw, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
+    uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
         wkeys, wlist, wacc, qmask, blocked, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
@@ -911,7 +910,6 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.wpiv = rl_take(o, 2 * WCAP);
     L.wbsz = rl_take(o, 2 * WCAP);
     L.wxn = rl_take(o, WCAP);
-    L.wpw = rl_take(o, 2 * WCAP);
     L.sel = rl_take(o, 2 * WCAP);
     L.sr = rl_take(o, WCAP);
     L.pwn = rl_take(o, 2 * WCAP);
@@ -1018,6 +1016,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     __shared__ uint32_t s_wt[32], s_wcnt[32];
     __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_firstrand, s_nrand, s_any, s_nstale, s_cut;
     __shared__ uint32_t s_serial, s_nmulti;
+    __shared__ uint32_t xcnt[2 * RAND_WARPS];                // X-support counts of the 16-lane groups
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr, H4 = Hr >> 2;
     const uint32_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1037,7 +1036,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *const mxs = a.mxs + t * a.m_stride * XSCAP;
     uint8_t *const mxn = a.mxn + t * a.m_stride;
     uint32_t *const mxver = a.mxver + t * a.m_stride;
-    uint16_t *const mpwn = a.mpwn + t * a.m_stride;
     uint32_t *const rowver = a.rowver + (size_t)t * 32 * H;
     uint16_t *const pwl = a.pwl + (size_t)t * WCAP * PWCAP;
     const bool item_smem = n <= QMAP_SMEM_MAX;
@@ -1045,7 +1043,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *const wpiv = (uint16_t *)(smraw + Lo.wpiv);    // window: pivot (slot - 32H) or NOPIV
     uint16_t *const wbsz = (uint16_t *)(smraw + Lo.wbsz);    // window: |x-column support| (saturated)
     uint8_t *const wxn = smraw + Lo.wxn;                     // window: X-support length / XS_OVER
-    uint16_t *const wpw = (uint16_t *)(smraw + Lo.wpw);      // window: nonzero words of the pivot row
     uint16_t *const sel = (uint16_t *)(smraw + Lo.sel);      // wave: window positions
     uint8_t *const sr = smraw + Lo.sr;                       // wave: pivot sign before the wave
     uint16_t *const pwn = (uint16_t *)(smraw + Lo.pwn);      // wave: nonzero words of the pivot row
@@ -1087,6 +1084,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             mstale[i] = gmstale[i];
         }
     wacc[lane] = 0;
+    if (lane < 2) xcnt[2 * warp + lane] = 0u;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
     __syncthreads();
@@ -1171,105 +1169,107 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
         const uint32_t wfirst = pend[0], wlast = pend[nlook - 1];
-        // ---- (2) window: cached pivots and X supports; stale ones listed in
-        // `pairs` (free until the work lists), bit 31 = column rescan
+        // ---- (2) window: cached pivots and X supports.  Ops whose measured
+        // column changed are listed in `pairs` (free until the work lists) for
+        // a column rescan; ops whose pivot row changed (or is new) in `ents`
+        // for an X-support rescan.
         for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
             const uint32_t i = pend[k];
             if (mstale[i]) {
-                pairs[atomicAdd(&s_nstale, 1u)] = k | 0x80000000u;
+                pairs[atomicAdd(&s_nstale, 1u)] = k;
                 continue;
             }
-            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i], pw = mpwn[i];
+            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
             wpiv[k] = (uint16_t)pv;
             wbsz[k] = (uint16_t)min(bs, 65535u);
             wxn[k] = (uint8_t)xn;
-            wpw[k] = (uint16_t)pw;
-            if (xn == XS_UNKNOWN || rowver[pv] != xv) pairs[atomicAdd(&s_nstale, 1u)] = k;
+            if (xn == XS_UNKNOWN || rowver[pv] != xv) ents[atomicAdd(&s_nent, 1u)] = k;
         }
         for (uint32_t w = (wfirst >> 5) + threadIdx.x; w <= (wlast >> 5); w += blockDim.x) blocked[w] = 0u;
         __syncthreads();
+        PHASE(1);
+        // column rescans, a warp each; an op with a new pivot joins the X-support list
         {
             const uint32_t nst = s_nstale;
             for (uint32_t x = (uint32_t)warp; x < nst; x += (uint32_t)nw) {
-                const uint32_t ent = pairs[x], k = ent & 0x7fffffffu, i = pend[k];
-                uint32_t pv;
-                if (ent >> 31) {
-                    uint32_t bs;
-                    warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
-                    if (lane == 0) {
-                        mpiv[i] = pv;
-                        mbsz[i] = bs;
-                        mstale[i] = 0;
-                        count(a, DC_PIV_RECOMP, 1);
-                        wbsz[k] = (uint16_t)min(bs, 65535u);
+                const uint32_t k = pairs[x], i = pend[k];
+                uint32_t pv, bs;
+                warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
+                if (lane == 0) {
+                    mpiv[i] = pv;
+                    mbsz[i] = bs;
+                    mstale[i] = 0;
+                    count(a, DC_PIV_RECOMP, 1);
+                    wbsz[k] = (uint16_t)min(bs, 65535u);
+                    if (pv == 0xffffffffu) {             // became deterministic
+                        wpiv[k] = NOPIV;
+                        stat[i] = MS_DETLATE;
+                        count(a, DC_DET_NOW, 1);
+                    } else {
+                        wpiv[k] = (uint16_t)pv;
+                        ents[atomicAdd(&s_nent, 1u)] = k;
                     }
-                    if (pv == 0xffffffffu) {             // became deterministic (warp-uniform)
-                        if (lane == 0) {
-                            wpiv[k] = NOPIV;
-                            stat[i] = MS_DETLATE;
-                            count(a, DC_DET_NOW, 1);
-                        }
-                        continue;
-                    }
-                    if (lane == 0) wpiv[k] = (uint16_t)pv;
-                } else {
-                    pv = wpiv[k];
                 }
-                // X support of the pivot row over the layer's items, and its
-                // nonzero words (x or z): 16-byte vectors of both planes
-                const uint32_t ver = rowver[pv];
-                const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)(32 * H + pv) * RS);
-                const uint4 *__restrict__ pz4 = px4 + H4;
-                if (lane == 0) s_wcnt[warp] = 0;
-                __syncwarp();
-                uint32_t nzw = 0;
-                for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
-                    uint4 vx[2], vz[2];
+            }
+        }
+        __syncthreads();
+        PHASE(2);
+        // X supports of the listed pivot rows over the layer's items: 16 lanes
+        // per op (two ops per warp at once), 16-byte vectors of the x plane
+        {
+            const uint32_t nxs = s_nent;
+            const uint32_t sub = (uint32_t)lane >> 4, sl = (uint32_t)lane & 15u;
+            for (uint32_t x0 = 2 * (uint32_t)warp; x0 < nxs; x0 += 2 * (uint32_t)nw) {
+                const uint32_t x = x0 + sub;
+                const bool act = x < nxs;
+                const uint32_t k = act ? ents[x] : 0u, i = act ? pend[k] : 0u;
+                const uint32_t pv = act ? wpiv[k] : 0u;
+                uint32_t ver = 0;
+                if (act) {
+                    ver = rowver[pv];
+                    const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)(32 * H + pv) * RS);
+                    for (uint32_t j0 = 0; j0 < H4; j0 += 16 * 6) {
+                        uint4 v[6];
 #pragma unroll
-                    for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t j = j0 + 32 * kk + lane;
-                        vx[kk] = j < H4 ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
-                        vz[kk] = j < H4 ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
-                    }
+                        for (int kk = 0; kk < 6; kk++) {
+                            const uint32_t j = j0 + 16 * kk + sl;
+                            v[kk] = j < H4 ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
+                        }
 #pragma unroll
-                    for (int kk = 0; kk < 2; kk++) {
-                        const uint32_t j = j0 + 32 * kk + lane;
-                        const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
-                        const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
+                        for (int kk = 0; kk < 6; kk++) {
+                            const uint32_t j = j0 + 16 * kk + sl;
+                            const uint32_t xw[4] = {v[kk].x, v[kk].y, v[kk].z, v[kk].w};
 #pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            nzw += (xw[e] | zw[e]) != 0u;
-                            uint32_t m = xw[e];
-                            while (m) {
-                                const int b = __ffs(m) - 1;
-                                m &= m - 1;
-                                const uint32_t u = 32 * (4 * j + e) + b;
-                                const uint32_t jj = u < n ? qmap[u] : 0xffffu;
-                                if (jj == 0xffffu) continue;
-                                const uint32_t pos = atomicAdd(&s_wcnt[warp], 1u);
-                                if (pos < XSCAP) mxs[(size_t)i * XSCAP + pos] = (uint16_t)jj;
+                            for (int e = 0; e < 4; e++) {
+                                uint32_t m = xw[e];
+                                while (m) {
+                                    const int b = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    const uint32_t u = 32 * (4 * j + e) + b;
+                                    const uint32_t jj = u < n ? qmap[u] : 0xffffu;
+                                    if (jj == 0xffffu) continue;
+                                    const uint32_t pos = atomicAdd(&xcnt[2 * warp + sub], 1u);
+                                    if (pos < XSCAP) mxs[(size_t)i * XSCAP + pos] = (uint16_t)jj;
+                                }
                             }
                         }
                     }
                 }
-                nzw = __reduce_add_sync(FULL_MASK, nzw);
                 __syncwarp();
-                if (lane == 0) {
-                    const uint32_t cnt = s_wcnt[warp];
-                    const uint8_t xn = cnt <= XSCAP ? (uint8_t)cnt : XS_OVER;
-                    const uint16_t pw = (uint16_t)min(nzw, 0xffffu);
+                if (act && sl == 0) {
+                    const uint32_t c = xcnt[2 * warp + sub];
+                    const uint8_t xn = c <= XSCAP ? (uint8_t)c : XS_OVER;
                     mxn[i] = xn;
                     mxver[i] = ver;
-                    mpwn[i] = pw;
                     wxn[k] = xn;
-                    wpw[k] = pw;
+                    xcnt[2 * warp + sub] = 0u;
                     count(a, DC_XS_RECOMP, 1);
                 }
                 __syncwarp();
             }
         }
         __syncthreads();
-        PHASE(1);
+        PHASE(3);
         // ---- (3) selection: for every conflicting pair of window ops the
         // later one is blocked; an op whose X support overflowed its list
         // blocks every later op (and itself, unless it is the first)
@@ -1292,9 +1292,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }
         __syncthreads();
         if (s_nrand == 0) {             // block-uniform: the window became deterministic
-            PHASE(2);
+            PHASE(4);
             continue;
         }
+        if (threadIdx.x == 0) s_nent = 0;   // the X-support list is done with
         {
             const uint32_t cut = s_cut, fr = s_firstrand;
             for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
@@ -1306,12 +1307,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     sel[idx] = (uint16_t)k;
                     stat[i] = MS_WAVE;
                     atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
-                    if (wpw[k] > PWS) s_serial = 1;
                 }
             }
         }
         __syncthreads();
-        PHASE(2);
+        PHASE(4);
         // ---- (4) work lists, one warp per wave op
         const uint32_t nsel = min(s_nsel, wcap);
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
@@ -1324,10 +1324,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             const uint4 *__restrict__ pz4 = px4 + H4;
             const uint4 *__restrict__ qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
             uint32_t nzcnt = 0;
-            for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
-                uint4 vx[2], vz[2], vq[2];
+            for (uint32_t j0 = 0; j0 < H4; j0 += 96) {
+                uint4 vx[3], vz[3], vq[3];
 #pragma unroll
-                for (int kk = 0; kk < 2; kk++) {
+                for (int kk = 0; kk < 3; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
                     const bool in = j < H4;
                     vx[kk] = in ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
@@ -1335,7 +1335,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     vq[kk] = in ? qx4[j] : make_uint4(0u, 0u, 0u, 0u);
                 }
 #pragma unroll
-                for (int kk = 0; kk < 2; kk++) {
+                for (int kk = 0; kk < 3; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
                     const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
                     const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
@@ -1425,7 +1425,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         }
         __syncthreads();
-        PHASE(3);
+        PHASE(5);
         const uint32_t npair = s_npair, nent = s_nent;
         if (threadIdx.x == 0) {
             count(a, DC_WAVES, 1);
@@ -1511,30 +1511,47 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // partners, which end as copies of their pivots); then row q's bit is
         // x_{p,b} and row p's is 0.  Touches no bit of another wave op's p or q.
         if (nent <= jcap) {
+            // a thread per listed update whose wave op has a listed support
+            // (at most SUPCAP rows); larger columns by a warp each below
+            for (uint32_t e = threadIdx.x; e < nent; e += blockDim.x) {
+                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
+                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                if (bp && wbsz[k] > SUPCAP) continue;
+                uint32_t *cj = cols + (size_t)j * CW;
+                if (bp) {
+                    const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
+                    const uint32_t nb = wbsz[k];
+                    for (uint32_t f0 = 0; f0 < nb; f0 += 8) {
+                        uint32_t rows[8];
+#pragma unroll
+                        for (uint32_t f = 0; f < 8; f++) rows[f] = f0 + f < nb ? sp[f0 + f] : 0xffffffffu;
+#pragma unroll
+                        for (uint32_t f = 0; f < 8; f++) {
+                            const uint32_t row = rows[f];
+                            if (row == 0xffffffffu || row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
+                            atomicXor(&cj[row >> 5], 1u << (row & 31));
+                        }
+                    }
+                    atomicOr(&cj[q >> 5], 1u << (q & 31));
+                } else {
+                    atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                }
+                atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                mstale[j] = 1;
+            }
             for (uint32_t e = (uint32_t)warp; e < nent; e += (uint32_t)nw) {
                 const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
                 const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                if (!bp || wbsz[k] <= SUPCAP) continue;
                 uint32_t *cj = cols + (size_t)j * CW;
-                if (bp) {
-                    if (wbsz[k] <= SUPCAP) {
-                        const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
-                        for (uint32_t f = lane; f < wbsz[k]; f += 32) {
-                            const uint32_t row = sp[f];
-                            if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
-                            atomicXor(&cj[row >> 5], 1u << (row & 31));
-                        }
-                    } else {
-                        const uint32_t *col = cols + (size_t)pend[k] * CW;
-                        for (uint32_t w = lane; w < CW; w += 32) {
-                            uint32_t v = col[w] & ~qmask[w];
-                            if (w == (p >> 5)) v &= ~(1u << (p & 31));
-                            if (v) atomicXor(&cj[w], v);
-                        }
-                    }
+                const uint32_t *col = cols + (size_t)pend[k] * CW;
+                for (uint32_t w = lane; w < CW; w += 32) {
+                    uint32_t v = col[w] & ~qmask[w];
+                    if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                    if (v) atomicXor(&cj[w], v);
                 }
                 if (lane == 0) {
-                    if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
-                    else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                    atomicOr(&cj[q >> 5], 1u << (q & 31));
                     atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
                     mstale[j] = 1;
                 }
@@ -1570,6 +1587,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }
         if (!serial) row_copies();               // pivots are staged: copies may overwrite them
         __syncthreads();
+        PHASE(6);
         // ---- (5c) rows with several pivots (or a dense one): a warp each
         if (npair <= paircap) {
             const uint32_t nm = s_nmulti;
@@ -1670,7 +1688,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             row_copies();
         }
         __syncthreads();
-        PHASE(4);
+        PHASE(7);
     }
 #undef PHASE
     __syncthreads();
@@ -1780,7 +1798,6 @@ static LArgs make_args(const HostProg *p, Batch &b, MeasScratch *ms, int *d_err)
         a.mxs = ms->mxs;
         a.mxn = ms->mxn;
         a.mxver = ms->mxver;
-        a.mpwn = ms->mpwn;
         a.rowver = ms->rowver;
         a.qmap = ms->qmap;
         a.ev = ms->ev;
