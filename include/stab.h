@@ -346,10 +346,11 @@ int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
  * [3] deterministic measurements resolved by the batched kernel,
  * [4] sum over deterministic measurements of |K| (stabilizer rows multiplied),
  * [5] sum over random measurements of |A| (rows that received a rowsum),
- * [6] cached pivots recomputed, [7] rowsum passes (one per wave), [8..13] SM clock cycles spent by
- * the random-measurement kernel in its six per-wave phases (pending list,
- * pivot and X-support refresh, selection, work lists, rowsums with column
- * updates and row copies, chain signs), [19] pivot-row X supports recomputed.
+ * [6] cached pivots recomputed, [7] rowsum passes (one per wave), [8..15] SM clock cycles spent by
+ * the random-measurement kernel in its eight per-wave phases (pending list,
+ * cached-state pass, column rescans, X-support rescans, selection, work
+ * lists, single-pivot rows with column updates and row copies, multi-pivot
+ * rows), [19] pivot-row X supports recomputed.
  * n <= 24 entries are written. */
 int stab_engine_counters(stab_ctx *ctx, uint64_t *out, size_t n, int reset);
 

@@ -359,8 +359,9 @@ def stab_launch_count(ctx, reset=True) -> int:
 
 COUNTER_NAMES = ("waves", "wave_ops", "det_in_wave_kernel", "det", "sum_K", "sum_A",
                  "pivot_recomputes", "rowsum_passes",
-                 "cyc_pending", "cyc_refresh", "cyc_select", "cyc_lists", "cyc_apply", "cyc_signs",
-                 "unused14", "unused15", "unused16", "unused17", "unused18", "xsupport_recomputes")
+                 "cyc_pending", "cyc_cached", "cyc_col_rescans", "cyc_xs_rescans", "cyc_select",
+                 "cyc_lists", "cyc_apply_single", "cyc_apply_multi", "unused16", "unused17", "unused18",
+                 "xsupport_recomputes")
 
 
 def stab_engine_counters(ctx, reset=True) -> dict:

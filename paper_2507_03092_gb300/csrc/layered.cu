@@ -1340,7 +1340,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
                     const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
                     const uint32_t qw[4] = {vq[kk].x, vq[kk].y, vq[kk].z, vq[kk].w};
-                    uint32_t mine = 0;
+                    uint32_t mine = 0, ne = 0;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         mine += (xw[e] | zw[e]) != 0u;
@@ -1350,9 +1350,30 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                             mm &= mm - 1;
                             const uint32_t u = 32 * (4 * j + e) + b;
                             const uint32_t jj = u < n ? qmap[u] : 0xffffu;
-                            if (jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE)) {
-                                const uint32_t f = atomicAdd(&s_nent, 1u);
-                                if (f < jcap) ents[f] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
+                            ne += jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE);
+                        }
+                    }
+                    if (__any_sync(FULL_MASK, ne != 0)) {
+                        uint32_t ie = ne;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(FULL_MASK, ie, o);
+                            if (lane >= o) ie += y;
+                        }
+                        uint32_t ebase = 0;
+                        if (lane == 31) ebase = atomicAdd(&s_nent, ie);
+                        ebase = __shfl_sync(FULL_MASK, ebase, 31) + ie - ne;
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            uint32_t mm = ne ? (xw[e] | qw[e]) : 0u;
+                            while (mm) {
+                                const int b = __ffs(mm) - 1;
+                                mm &= mm - 1;
+                                const uint32_t u = 32 * (4 * j + e) + b;
+                                const uint32_t jj = u < n ? qmap[u] : 0xffffu;
+                                if (jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE)) {
+                                    if (ebase < jcap) ents[ebase] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
+                                    ebase++;
+                                }
                             }
                         }
                     }
@@ -1386,10 +1407,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
             // rowsum pairs: rows of the measured column except the pivot and
             // the wave's destabilizer partners, linked per row
-            auto add_pair = [&](uint32_t row) {
-                dirty[row >> 5] = 1;
-                if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) return;
-                const uint32_t f = atomicAdd(&s_npair, 1u);
+            // link pair f (row, this wave op) into its row's chain
+            auto link_pair = [&](uint32_t f, uint32_t row) {
                 if (f >= paircap) return;
                 pairs[f] = row | (x << 16);
                 uint32_t h = (row * 2654435761u) >> 20;       // HT = 4096 slots
@@ -1410,16 +1429,32 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 hslot[f] = (uint16_t)h;
             };
             if (wbsz[k] <= SUPCAP) {
+                // one append per warp and batch (a single shared counter would
+                // otherwise take every lane's atomic in turn)
                 const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                for (uint32_t e = lane; e < wbsz[k]; e += 32) add_pair(sp[e]);
+                const uint32_t nb = wbsz[k];
+                for (uint32_t e0 = 0; e0 < nb; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    const uint32_t row = e < nb ? sp[e] : 0u;
+                    if (e < nb) dirty[row >> 5] = 1;
+                    const bool keep = e < nb && row != p && !((qmask[row >> 5] >> (row & 31)) & 1u);
+                    const uint32_t bal = __ballot_sync(FULL_MASK, keep);
+                    uint32_t base = 0;
+                    if (lane == 0 && bal) base = atomicAdd(&s_npair, (uint32_t)__popc(bal));
+                    base = __shfl_sync(FULL_MASK, base, 0);
+                    if (keep) link_pair(base + __popc(bal & ((1u << lane) - 1u)), row);
+                }
             } else {
                 const uint32_t *col = cols + (size_t)i * CW;
                 for (uint32_t w = lane; w < CW; w += 32) {
                     uint32_t m = col[w];
+                    if (m) dirty[w] = 1;
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        add_pair(32 * w + b);
+                        const uint32_t row = 32 * w + b;
+                        if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
+                        link_pair(atomicAdd(&s_npair, 1u), row);
                     }
                 }
             }
@@ -1521,6 +1556,9 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 if (bp) {
                     const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
                     const uint32_t nb = wbsz[k];
+                    // support rows come in increasing word order (column scan
+                    // order), so rows of one word are adjacent: one atomic per word
+                    uint32_t cw = 0xffffffffu, cm = 0u;
                     for (uint32_t f0 = 0; f0 < nb; f0 += 8) {
                         uint32_t rows[8];
 #pragma unroll
@@ -1529,9 +1567,15 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         for (uint32_t f = 0; f < 8; f++) {
                             const uint32_t row = rows[f];
                             if (row == 0xffffffffu || row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
-                            atomicXor(&cj[row >> 5], 1u << (row & 31));
+                            if ((row >> 5) != cw) {
+                                if (cm) atomicXor(&cj[cw], cm);
+                                cw = row >> 5;
+                                cm = 0u;
+                            }
+                            cm |= 1u << (row & 31);
                         }
                     }
+                    if (cm) atomicXor(&cj[cw], cm);
                     atomicOr(&cj[q >> 5], 1u << (q & 31));
                 } else {
                     atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
@@ -1634,23 +1678,56 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         if (w < lnw) wkeys[PWS * lane + w] = ((uint32_t)spc[lx * PWS + w] << 7) | ((uint32_t)lane << 2) | w;
                     __syncwarp();
                     warp_sort_keys(wkeys, nk);
-                    // each word's first key leads: loads the row word once and
-                    // applies the pivots holding that word, in chain order
-                    for (uint32_t idx = lane; idx < nk; idx += 32) {
-                        const uint32_t key = wkeys[idx];
-                        if (key == 0xffffffffu || (idx > 0 && (wkeys[idx - 1] >> 7) == (key >> 7))) continue;
-                        const uint32_t c = key >> 7;
-                        uint32_t xv = rs[c], zv = rs[Hr + c];
-                        for (uint32_t g = idx; g < nk && (wkeys[g] >> 7) == c; g++) {
-                            const uint32_t kg = wkeys[g], ml = (kg >> 2) & 31u, ms = kg & 3u;
+                    // the sorted keys, 32 at a time: a segmented XOR prefix scan
+                    // over each word's keys (chain order) gives every pivot the
+                    // row word it meets, so all phases are computed at once;
+                    // a word's last key stores the word (carries run across rows)
+                    uint32_t carry_c = 0xffffffffu, carry_x = 0u, carry_z = 0u;
+                    for (uint32_t r0 = 0; r0 < nk; r0 += 32) {
+                        const uint32_t key = wkeys[r0 + lane];
+                        const bool valid = key != 0xffffffffu;
+                        const uint32_t c = valid ? key >> 7 : 0xffffffffu;
+                        const uint32_t ml = (key >> 2) & 31u, ms = key & 3u;
+                        uint32_t px_ = 0u, pz_ = 0u, sx = 0u, sz = 0u;
+                        if (valid) {
                             const uint32_t gx = pairs[wlist[ml]] >> 16;
-                            const uint32_t px_ = spx[gx * PWS + ms], pz_ = spz[gx * PWS + ms];
-                            atomicAdd(&wacc[ml], phase_word(px_, pz_, xv, zv));
-                            xv ^= px_;
-                            zv ^= pz_;
+                            px_ = spx[gx * PWS + ms];
+                            pz_ = spz[gx * PWS + ms];
+                            sx = rs[c];
+                            sz = rs[Hr + c];
                         }
-                        rs[c] = xv;
-                        rs[Hr + c] = zv;
+                        const uint32_t cprev = __shfl_up_sync(FULL_MASK, c, 1);
+                        const uint32_t cnext = __shfl_down_sync(FULL_MASK, c, 1);
+                        bool head = lane == 0 ? c != carry_c : c != cprev;
+                        uint32_t ix = px_, iz = pz_;
+                        bool hacc = head;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t yx = __shfl_up_sync(FULL_MASK, ix, o);
+                            const uint32_t yz = __shfl_up_sync(FULL_MASK, iz, o);
+                            const bool yh = __shfl_up_sync(FULL_MASK, hacc, o);
+                            if (lane >= o && !hacc) {
+                                ix ^= yx;
+                                iz ^= yz;
+                                hacc = yh;
+                            }
+                        }
+                        if (!hacc) {               // segment continues from the previous row
+                            ix ^= carry_x;
+                            iz ^= carry_z;
+                        }
+                        if (valid) {
+                            const uint32_t rx = sx ^ ix ^ px_, rz = sz ^ iz ^ pz_;   // row word before this pivot
+                            atomicAdd(&wacc[ml], phase_word(px_, pz_, rx, rz));
+                            const bool last = lane == 31 ? (r0 + 32 >= nk || (wkeys[r0 + 32] >> 7) != c) : cnext != c;
+                            if (last) {
+                                rs[c] = sx ^ ix;
+                                rs[Hr + c] = sz ^ iz;
+                            }
+                        }
+                        carry_c = __shfl_sync(FULL_MASK, c, 31);
+                        carry_x = __shfl_sync(FULL_MASK, ix, 31);
+                        carry_z = __shfl_sync(FULL_MASK, iz, 31);
+                        __syncwarp();
                     }
                     __syncwarp();
                     if ((uint32_t)lane < cnt) {
