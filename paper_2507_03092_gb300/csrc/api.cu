@@ -206,13 +206,13 @@ stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n) {
 
 // One device allocation holds every array of a compiled program, followed by
 // its DevProg descriptor (used by the resident engine's job table).
-static constexpr int PROG_ARRAYS = 7;
+static constexpr int PROG_ARRAYS = 8;
 static size_t prog_layout(const HostProg &P, size_t off[PROG_ARRAYS + 1]) {
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
                                     P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
                                     P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
-                                    P.mfactors.size() * sizeof(uint32_t)};
+                                    P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t)};
     size_t o = 0;
     for (int k = 0; k < PROG_ARRAYS; k++) {
         off[k] = o;
@@ -245,12 +245,13 @@ static int upload_prog(HostProg &P) {
     P.dev.sitems = (const SItem *)(b + off[4]);
     P.dev.item_layer = (const uint32_t *)(b + off[5]);
     P.dev.mfactors = (const uint32_t *)(b + off[6]);
+    P.dev.sab = (const uint32_t *)(b + off[7]);
     const void *src[PROG_ARRAYS] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
-                                    P.sitems.data(), P.item_layer.data(), P.mfactors.data()};
+                                    P.sitems.data(), P.item_layer.data(), P.mfactors.data(), P.sab.data()};
     const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
                                     P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
                                     P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
-                                    P.mfactors.size() * sizeof(uint32_t)};
+                                    P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t)};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < PROG_ARRAYS && !e; k++)
         if (sz[k]) e = cudaMemcpy(b + off[k], src[k], sz[k], cudaMemcpyHostToDevice);
@@ -276,7 +277,7 @@ int run_layered_shots(stab_ctx *ctx, const HostProg &user_prog, uint32_t shots, 
     const size_t per = batch_bytes(p.n, 1);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3 + work.bytes);
+    size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3 + work.cap);
     // grid.y indexes the tableau: at most 65535 per launch
     uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>({(size_t)shots, budget / per, (size_t)65535}));
     if (work.n != p.n || work.count < chunk) {

@@ -281,6 +281,7 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
     }
     // ---- packed items, item -> layer map, noise-event capacities ----
     P.sitems.resize(P.gitems.size());
+    P.sab.resize(P.gitems.size());
     P.item_layer.resize(P.gitems.size());
     uint32_t ev_total = 0;
     for (uint32_t l = 0; l < P.layers.size(); l++) {
@@ -295,6 +296,7 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
             const GItem &g = P.gitems[i];
             P.sitems[i].ab = (g.a & 0xffffu) | ((g.b & 0xffffu) << 16);
             P.sitems[i].g = g.gate;
+            P.sab[i] = P.sitems[i].ab;
             P.item_layer[i] = l;
             if (g.nn) L.n_noisy++;
             if (g.gate != L.uniform) L.uniform = 0;

@@ -83,6 +83,7 @@ struct DevProg {          // by-value descriptor handed to kernels
     const MItem *mitems;
     const Thr *thr;
     const SItem *sitems;      // packed copy of gitems (layered engine)
+    const uint32_t *sab;      // their qubit pairs alone (a | b << 16), read by uniform layers
     const uint32_t *item_layer; // layer index of each gate item
     uint32_t record_words, coin_words, noise_words, max_meas;
     uint32_t max_gitems, n_gitems, n_mitems, ev_total;
@@ -105,6 +106,7 @@ struct HostProg {
     std::vector<MItem> mitems;
     std::vector<Thr> thr;
     std::vector<SItem> sitems;
+    std::vector<uint32_t> sab;
     std::vector<uint32_t> item_layer;
     std::vector<Run> runs;
     std::vector<uint32_t> mfactors;
@@ -165,7 +167,8 @@ struct Batch {
                                   // bit 1 the current measurement layer has random ops
     bool rm_valid = false;
     void *mem = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0;             // bytes the current layout uses
+    size_t cap = 0;               // bytes allocated (a smaller layout reuses them)
 };
 
 struct MeasScratch {

@@ -281,6 +281,36 @@ __device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_
     }
 }
 
+// A uniform layer (every item the same gate KIND): 4-byte qubit pairs, eight
+// per thread loaded before any is used, so a layer of up to 8 x blockDim items
+// costs one round trip for its items.
+template <uint32_t KIND>
+__device__ __forceinline__ void gate_items_u(const uint32_t *__restrict__ ab, uint32_t count, uint32_t *sx,
+                                             uint32_t *sz, uint32_t &racc) {
+    for (uint32_t i0 = threadIdx.x; i0 < count; i0 += 8 * blockDim.x) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t i = i0 + k * blockDim.x;
+            v[k] = i < count ? __ldg(ab + i) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (i0 + k * blockDim.x >= count) break;
+            const uint32_t ga = v[k] & 0xffffu, gb = v[k] >> 16;
+            if (KIND == STAB_H || KIND == STAB_S) {
+                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                racc ^= apply_gate(KIND, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za;
+            } else {
+                uint32_t xa = sx[ga], za = sz[ga], xb = sx[gb], zb = sz[gb];
+                racc ^= apply_gate(KIND, xa, za, xb, zb);
+                sx[ga] = xa; sz[ga] = za; sx[gb] = xb; sz[gb] = zb;
+            }
+        }
+    }
+}
+
 // A layer whose noise events overflowed their slots: every draw of the layer
 // evaluated again (kept out of line: the common path needs none of this).
 __device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t count, const Thr *thr,
@@ -380,11 +410,12 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         // items in groups of 4 per thread, all four loaded before any is used;
         // layers made of one gate kind (every layer of a surface-code round)
         // run a loop specialised to it
+        const uint32_t *__restrict__ iab = a.P.sab + L.first;
         switch (L.uniform) {
-        case STAB_H: gate_items<STAB_H>(it, L.count, sx, sz, racc); break;
-        case STAB_CX: gate_items<STAB_CX>(it, L.count, sx, sz, racc); break;
-        case STAB_CZ: gate_items<STAB_CZ>(it, L.count, sx, sz, racc); break;
-        case STAB_S: gate_items<STAB_S>(it, L.count, sx, sz, racc); break;
+        case STAB_H: gate_items_u<STAB_H>(iab, L.count, sx, sz, racc); break;
+        case STAB_CX: gate_items_u<STAB_CX>(iab, L.count, sx, sz, racc); break;
+        case STAB_CZ: gate_items_u<STAB_CZ>(iab, L.count, sx, sz, racc); break;
+        case STAB_S: gate_items_u<STAB_S>(iab, L.count, sx, sz, racc); break;
         default: gate_items<0>(it, L.count, sx, sz, racc); break;
         }
         __syncthreads();
@@ -1822,25 +1853,34 @@ size_t batch_bytes(uint32_t n, uint32_t count) {
     return per * count + 1024;
 }
 
+// Lay out `count` tableaux of n qubits in the batch's allocation, reusing it
+// when it is large enough (no cudaFree / cudaMalloc, so no device-wide
+// synchronisation) and allocating a larger one otherwise.
 int batch_alloc(Batch &b, uint32_t n, uint32_t count, std::string *err) {
-    batch_free(b);
-    b.n = n;
-    b.H = (n + 31) / 32;
-    b.CW = 2 * b.H;
-    b.count = count;
-    const size_t Hr = round4(b.H), RS = 2 * Hr;
-    b.qm_stride = 2 * (size_t)b.CW * n;
-    b.rm_stride = 64 * (size_t)b.H * RS;
-    const size_t qm_b = 4 * b.qm_stride * count, rm_b = 4 * b.rm_stride * count;
-    const size_t r_b = 4 * (size_t)b.CW * count, d_b = (size_t)b.CW * count, f_b = 4 * (size_t)count;
+    const size_t H = (n + 31) / 32, CW = 2 * H;
+    const size_t Hr = round4((uint32_t)H), RS = 2 * Hr;
+    const size_t qm_stride = 2 * CW * (size_t)n, rm_stride = 64 * H * RS;
+    const size_t qm_b = 4 * qm_stride * count, rm_b = 4 * rm_stride * count;
+    const size_t r_b = 4 * CW * count, d_b = CW * count, f_b = 4 * (size_t)count;
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    b.bytes = up(qm_b) + up(rm_b) + up(r_b) + up(d_b) + up(f_b);
-    if (cudaMalloc(&b.mem, b.bytes) != cudaSuccess) {
-        cudaGetLastError();
-        b.mem = nullptr;
-        *err = "cudaMalloc of " + std::to_string(b.bytes) + " bytes for tableaux failed";
-        return STAB_ERR_OOM;
+    const size_t need = up(qm_b) + up(rm_b) + up(r_b) + up(d_b) + up(f_b);
+    if (!b.mem || b.cap < need) {
+        batch_free(b);
+        if (cudaMalloc(&b.mem, need) != cudaSuccess) {
+            cudaGetLastError();
+            b.mem = nullptr;
+            *err = "cudaMalloc of " + std::to_string(need) + " bytes for tableaux failed";
+            return STAB_ERR_OOM;
+        }
+        b.cap = need;
     }
+    b.n = n;
+    b.H = (uint32_t)H;
+    b.CW = (uint32_t)CW;
+    b.count = count;
+    b.qm_stride = qm_stride;
+    b.rm_stride = rm_stride;
+    b.bytes = need;
     char *p = (char *)b.mem;
     b.qm = (uint32_t *)p; p += up(qm_b);
     b.rm = (uint32_t *)p; p += up(rm_b);

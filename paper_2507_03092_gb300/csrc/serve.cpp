@@ -2,10 +2,14 @@
 //
 // Requests (shots of a compiled circuit with seeded streams) are queued by
 // stab_serve_submit.  A scheduler thread admits queued requests in arrival
-// order whenever a launch slot is free and the request's device footprint
-// fits the remaining HBM budget.  Small-tableau requests that are waiting
-// together are merged into one resident-engine launch (their shots become
-// jobs of one persistent kernel); larger ones get a layered-engine launch.
+// order whenever a launch slot is free and the device memory the slots hold,
+// plus what the request's slot still has to grow by, fits the HBM budget.
+// Slots keep their buffers between requests (a smaller request reuses them
+// without cudaFree / cudaMalloc); idle slots give theirs back only when
+// nothing is in flight and the next request would not fit otherwise.
+// Small-tableau requests that are waiting together are merged into one
+// resident-engine launch (their shots become jobs of one persistent kernel);
+// larger ones get a layered-engine launch.
 // Each launch runs on its own CUDA stream, so requests admitted while others
 // are on the GPU overlap with them on the device.  A host callback on the
 // launch's stream stamps the completion time and frees the slot, and the
@@ -42,10 +46,12 @@ struct Slot {
     DevBuf ms_buf, jobs;
     unsigned int *counter = nullptr;
     std::vector<Request> reqs;     // requests of the launch in flight
-    size_t footprint = 0;
+    size_t held = 0;               // device bytes the slot's buffers hold
     int status = STAB_OK;
     struct ServeState *owner = nullptr;
 };
+
+static size_t slot_held(const Slot &s) { return s.work.cap + s.ms_buf.cap + s.jobs.cap; }
 
 struct ServeState {
     stab_serve_config cfg{};
@@ -54,7 +60,7 @@ struct ServeState {
     std::deque<Request> queue;
     std::vector<std::unique_ptr<Slot>> slots;
     std::vector<stab_request_status> done;
-    size_t used_bytes = 0;
+    size_t held_bytes = 0;         // sum of the slots' held bytes
     uint64_t next_id = 1;
     size_t inflight = 0;
     bool stop = false;
@@ -77,16 +83,14 @@ static void CUDART_CB on_done(void *arg) {
         st.t_done = t;
         S->done.push_back(st);
     }
-    S->used_bytes -= s->footprint;
     S->inflight -= s->reqs.size();
     s->reqs.clear();
-    s->footprint = 0;
     s->busy = false;
     S->cv.notify_all();
 }
 
 static size_t request_footprint(const HostProg &p, uint32_t shots, bool resident) {
-    if (resident) return (size_t)shots * (sizeof(ResJob) + resident_smem_per_tableau(p.n));
+    if (resident) return (size_t)shots * sizeof(ResJob);    // its job table (tableaux live in shared memory)
     const size_t mm = std::max<uint32_t>(1, layered_prog(p).dev.max_meas);
     return batch_bytes(p.n, shots) + (size_t)shots * mm * (4 * p.CW + 2);
 }
@@ -108,13 +112,32 @@ static void scheduler(stab_ctx *ctx, ServeState *S) {
         std::vector<Request> take;
         size_t bytes = 0;
         const Request &head = S->queue.front();
-        if (S->used_bytes + head.footprint > S->cfg.hbm_budget_bytes && S->used_bytes > 0) {
-            S->cv.wait_for(lk, std::chrono::milliseconds(2));
-            continue;
-        }
         if (S->inflight >= S->cfg.max_inflight) {
             S->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
+        }
+        auto extra_for = [&](size_t need) { return need > slot->held ? need - slot->held : (size_t)0; };
+        if (S->held_bytes + extra_for(head.footprint) > S->cfg.hbm_budget_bytes) {
+            bool any_busy = false;
+            for (auto &s : S->slots) any_busy |= s->busy;
+            if (any_busy) {
+                S->cv.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
+            }
+            // nothing in flight: idle slots give their buffers back, largest first
+            // (cudaFree synchronises the device, which is idle)
+            while (S->held_bytes + extra_for(head.footprint) > S->cfg.hbm_budget_bytes) {
+                Slot *big = nullptr;
+                for (auto &s : S->slots)
+                    if (s.get() != slot && s->held && (!big || s->held > big->held)) big = s.get();
+                if (!big) big = slot->held ? slot : nullptr;
+                if (!big) break;
+                batch_free(big->work);
+                big->ms_buf.release();
+                big->jobs.release();
+                S->held_bytes -= big->held;
+                big->held = 0;
+            }
         }
         take.push_back(head);
         bytes += head.footprint;
@@ -123,7 +146,7 @@ static void scheduler(stab_ctx *ctx, ServeState *S) {
             while (!S->queue.empty() && take.size() < S->cfg.max_batch_requests &&
                    S->inflight + take.size() < S->cfg.max_inflight) {
                 const Request &nx = S->queue.front();
-                if (!nx.resident || S->used_bytes + bytes + nx.footprint > S->cfg.hbm_budget_bytes) break;
+                if (!nx.resident || S->held_bytes + extra_for(bytes + nx.footprint) > S->cfg.hbm_budget_bytes) break;
                 take.push_back(nx);
                 bytes += nx.footprint;
                 S->queue.pop_front();
@@ -133,9 +156,7 @@ static void scheduler(stab_ctx *ctx, ServeState *S) {
         for (auto &r : take) r.t_admit = ta;
         slot->busy = true;
         slot->reqs = take;
-        slot->footprint = bytes;
         slot->status = STAB_OK;
-        S->used_bytes += bytes;
         S->inflight += take.size();
         lk.unlock();
         int rc = STAB_OK;
@@ -173,6 +194,11 @@ static void scheduler(stab_ctx *ctx, ServeState *S) {
         slot->status = rc;
         cudaError_t e = cudaLaunchHostFunc(slot->stream, on_done, slot);
         lk.lock();
+        {
+            const size_t h = slot_held(*slot);         // buffers may have grown for this launch
+            S->held_bytes += h - slot->held;
+            slot->held = h;
+        }
         if (e != cudaSuccess) {
             cudaGetLastError();
             lk.unlock();
