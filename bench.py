@@ -18,6 +18,7 @@ Under torchrun (N > 1) every rank simulates its own shots on its own GPU
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import subprocess
@@ -388,6 +389,7 @@ def config_suite(sim, B, torch, flush, cpu=True):
     import oracle
     cores = os.cpu_count() or 1
     out = {}
+    stage("configs: C1")
     c1 = C.surface_code_memory(3, p=1e-3)
     g, (coins, noise) = gpu_rates(sim, B, torch, c1, 1024, flush)
     if cpu:
@@ -400,6 +402,7 @@ def config_suite(sim, B, torch, flush, cpu=True):
         g["cpu_baseline"] = {"kind": "oracle", "one_core_shots_per_s": 1024 / t1,
                              "all_cores_shots_per_s": 1024 / tn, "cores": cores, "sample": "all 1024 shots"}
     out["c1_d3_1024_shots"] = g
+    stage("configs: C2")
     c2 = C.random_clifford_layers(1000, 200, seed=0)
     g, (coins, noise) = gpu_rates(sim, B, torch, c2, 1, flush, engine=B.ENGINE_LAYERED)
     if cpu:
@@ -407,6 +410,7 @@ def config_suite(sim, B, torch, flush, cpu=True):
         g["cpu_baseline"] = {"kind": "oracle", "ops_per_s": ops, "measurements_per_s": meas, "cores": 1,
                              "sample": desc}
     out["c2_random_clifford_n1000_200_layers"] = g
+    stage("configs: C3 noiseless")
     c3 = C.surface_code_memory(71)
     g, (coins, noise) = gpu_rates(sim, B, torch, c3, 1, flush, engine=B.ENGINE_LAYERED)
     if cpu:
@@ -416,6 +420,7 @@ def config_suite(sim, B, torch, flush, cpu=True):
     out["c3_d71_noiseless"] = g
     wide = {}
     for n in (256, 1024, 2048):
+        stage(f"configs: random n-wide n={n}")
         cw = C.random_wide_benchmark(n, n, seed=1)
         g, (coins, noise) = gpu_rates(sim, B, torch, cw, 1, flush, reps=2, engine=B.ENGINE_LAYERED)
         if cpu:
@@ -446,7 +451,13 @@ def aggregate(t_local_s: float, ops_per_step: int, steps: int, world: int, dist=
 
 
 # ------------------------------------------------------------------ main arm
+def stage(msg):
+    """Progress marker on stderr (the JSON line is the only stdout output)."""
+    print(f"[bench] {time.strftime('%H:%M:%S')} {msg}", file=sys.stderr, flush=True)
+
+
 def main():
+    faulthandler.enable()            # a fatal signal prints the Python stack to stderr
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -666,11 +677,13 @@ def main():
                          f"{float(np.mean(step_ms_prof)):.3f} ms per step); the timed steps replay CUDA graphs",
         "wall_s_timed": t_wall,
     }
+    stage("timed steps done")
     if rank == 0 and not args.no_cpu:
         v, desc, _ = oracle_ops_per_s(circ, coins[0], noise[0], budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": "ops/s", "cores": 1, "kind": "oracle",
                                 "sample": desc}
     if rank == 0 and not args.no_extras:
+        stage("batched")
         try:
             line["batched"] = batched_vs_plain(sim, B, torch)
         except Exception as ex:       # report, do not hide
@@ -681,6 +694,7 @@ def main():
             except Exception as ex:
                 line["batched"]["cpu_baseline"] = {"error": repr(ex)}
     if rank == 0 and not args.no_extras and not args.no_configs:
+        stage("configs")
         try:
             line["configs"] = config_suite(sim, B, torch, flush, cpu=not args.no_cpu)
         except Exception as ex:       # report, do not hide
@@ -688,7 +702,9 @@ def main():
     if rank == 0 and (args.serve or world == 1) and not args.no_serve and not args.no_extras:
         from paper_2507_03092_gb300 import serve_trace
         circs = serve_trace.compile_circuits(sim)
+        stage("serve replay")
         line["serve"] = serve_trace.replay(sim, B, torch, circs=circs)
+        stage("serve capacity")
         try:
             sat = serve_trace.saturated(sim, B, torch, circs=circs)
             pl = serve_trace.plain(sim, B, torch, circs=circs)

@@ -926,7 +926,7 @@ static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pa
 // k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
 struct RandLayout {
     uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
-        wkeys, wlist, wacc, qmask, blocked, qmap, stat, stale, r, total;
+        wkeys, wlist, wacc, qmask, blocked, pmask, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
     const uint32_t at = o;
@@ -959,6 +959,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.wacc = rl_take(o, 4 * 32 * RAND_WARPS);
     L.qmask = rl_take(o, 8 * H);
     L.blocked = rl_take(o, 4 * H);
+    L.pmask = rl_take(o, 4 * H);
     L.qmap = rl_take(o, item_smem ? 2 * n : 0u);
     L.stat = rl_take(o, item_smem ? n : 0u);
     L.stale = rl_take(o, item_smem ? n : 0u);
@@ -1092,6 +1093,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     int *const wacc = (int *)(smraw + Lo.wacc) + warp * 32;                 //   powers of i per pair
     uint32_t *const qmask = (uint32_t *)(smraw + Lo.qmask);  // destabilizer partners of the wave's pivots
     uint32_t *const blocked = (uint32_t *)(smraw + Lo.blocked);   // per item: an earlier window op conflicts
+    // per qubit: its layer item is still random or became deterministic during
+    // the layer (the items whose measured columns are kept current); scans of
+    // pivot and destabilizer rows test only these bits
+    uint32_t *const pmask = (uint32_t *)(smraw + Lo.pmask);
     uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
     uint8_t *const stat = item_smem ? smraw + Lo.stat : gstat;
     uint8_t *const mstale = item_smem ? smraw + Lo.stale : gmstale;
@@ -1116,8 +1121,13 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }
     wacc[lane] = 0;
     if (lane < 2) xcnt[2 * warp + lane] = 0u;
+    for (uint32_t w = threadIdx.x; w < H; w += blockDim.x) pmask[w] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
+    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+        const uint32_t q = a.P.mitems[M.first + i].q;
+        qmap[q] = (uint16_t)i;
+        if (gstat[i] == MS_RANDOM) atomicOr(&pmask[q >> 5], 1u << (q & 31));
+    }
     __syncthreads();
 
     unsigned long long tlast = clock64();
@@ -1272,7 +1282,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                             const uint32_t xw[4] = {v[kk].x, v[kk].y, v[kk].z, v[kk].w};
 #pragma unroll
                             for (int e = 0; e < 4; e++) {
-                                uint32_t m = xw[e];
+                                uint32_t m = 4 * j + e < H ? xw[e] & pmask[4 * j + e] : 0u;
                                 while (m) {
                                     const int b = __ffs(m) - 1;
                                     m &= m - 1;
@@ -1371,11 +1381,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
                     const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
                     const uint32_t qw[4] = {vq[kk].x, vq[kk].y, vq[kk].z, vq[kk].w};
+                    uint32_t pmk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) pmk[e] = 4 * j + e < H ? pmask[4 * j + e] : 0u;
                     uint32_t mine = 0, ne = 0;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         mine += (xw[e] | zw[e]) != 0u;
-                        uint32_t mm = xw[e] | qw[e];
+                        uint32_t mm = (xw[e] | qw[e]) & pmk[e];
                         while (mm) {
                             const int b = __ffs(mm) - 1;
                             mm &= mm - 1;
@@ -1395,7 +1408,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         ebase = __shfl_sync(FULL_MASK, ebase, 31) + ie - ne;
 #pragma unroll
                         for (int e = 0; e < 4; e++) {
-                            uint32_t mm = ne ? (xw[e] | qw[e]) : 0u;
+                            uint32_t mm = ne ? ((xw[e] | qw[e]) & pmk[e]) : 0u;
                             while (mm) {
                                 const int b = __ffs(mm) - 1;
                                 mm &= mm - 1;
@@ -1505,39 +1518,40 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // row copies: row q <- row p, row p <- +-Z_a (16-byte words over the
         // Hr-word rows; the words past H are zero in every row), and the outcome
         auto row_copies = [&]() {
-            for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+            // a thread per (wave op, 16-byte element of the x|z row): reads row
+            // p's element, writes it to row q and row p's new element (+-Z_a)
+            const uint32_t per = 2 * H4;
+            for (uint32_t tt = threadIdx.x; tt < nsel * per; tt += blockDim.x) {
+                const uint32_t x = tt / per, c = tt % per;
+                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                const uint32_t mq = a.P.mitems[M.first + pend[k]].q;
+                uint4 *__restrict__ rp4 = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
+                uint4 *__restrict__ rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+                const uint4 v = rp4[c];
+                rq4[c] = v;
+                uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                if (c == H4 + (mq >> 7)) {
+                    const uint32_t za = 1u << (mq & 31), zsub = (mq >> 5) & 3u;
+                    z = make_uint4(zsub == 0 ? za : 0u, zsub == 1 ? za : 0u, zsub == 2 ? za : 0u, zsub == 3 ? za : 0u);
+                }
+                rp4[c] = z;
+            }
+            // signs, outcome, record, pending mask: a thread per wave op
+            for (uint32_t x = threadIdx.x; x < nsel; x += blockDim.x) {
                 const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
                 const MItem m = a.P.mitems[M.first + i];
                 const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
                                                                : coin_bit(a.call->st, t, m.coin);
-                const uint4 *__restrict__ src = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
-                uint4 *__restrict__ dq = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
-#pragma unroll 4
-                for (uint32_t c = lane; c < H4; c += 32) {
-                    const uint4 xv = src[c], zv = src[H4 + c];
-                    dq[c] = xv;
-                    dq[H4 + c] = zv;
-                }
-                __syncwarp();
-                uint4 *dp = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
-                const uint32_t za = 1u << (m.q & 31), zsub = (m.q >> 5) & 3u;
-                for (uint32_t c = lane; c < H4; c += 32) {
-                    dp[c] = make_uint4(0u, 0u, 0u, 0u);
-                    const bool here = c == (m.q >> 7);
-                    dp[H4 + c] = make_uint4(here && zsub == 0 ? za : 0u, here && zsub == 1 ? za : 0u,
-                                            here && zsub == 2 ? za : 0u, here && zsub == 3 ? za : 0u);
-                }
-                if (lane == 0) {
-                    if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
-                    else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
-                    if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
-                    else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
-                    rowver[q]++;
-                    out[i] = (uint8_t)coin;
-                    stat[i] = MS_DONE;
-                    write_record(a, t, m.rec, coin);
-                    outcome_flips(a, t, layer, m, coin);
-                }
+                if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
+                else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
+                if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
+                else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
+                rowver[q]++;
+                atomicAnd(&pmask[m.q >> 5], ~(1u << (m.q & 31)));
+                out[i] = (uint8_t)coin;
+                stat[i] = MS_DONE;
+                write_record(a, t, m.rec, coin);
+                outcome_flips(a, t, layer, m, coin);
             }
         };
         // ---- (5a) rows with one pivot: a thread each; the others listed for warps
