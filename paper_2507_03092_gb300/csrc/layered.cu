@@ -2094,6 +2094,17 @@ void prog_graphs_free(HostProg &p) {
     p.gkey.clear();
 }
 
+// Launch sequences longer than this are issued plainly instead of being
+// captured as one graph: a program of tens of thousands of layers (the random
+// n-wide benchmark at n = 2048 has 4.2 M ops) made capture crash the host
+// process, while graphs of a few thousand nodes replay fine.
+constexpr uint64_t GRAPH_MAX_NODES = 4096;
+static uint64_t graph_nodes(const HostProg &p) {
+    uint64_t k = 4;                                   // memsets, noise events
+    for (const Run &R : p.runs) k += R.type == LT_GATE ? 1 : 7;
+    return k;
+}
+
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
@@ -2113,7 +2124,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     ca.rec_stride = rec_stride;
     cudaError_t e = cudaMemcpyAsync(ms.call, &ca, sizeof ca, cudaMemcpyHostToDevice, s);
     if (e) return e;
-    if (!gsl || !gsl->gs || (kp && kp->mask))
+    if (!gsl || !gsl->gs || (kp && kp->mask) || graph_nodes(p) > GRAPH_MAX_NODES)
         return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
     // Graph replay on the slot's stream, after the work already queued on s.
     // The captured sequence depends only on the kernel arguments (per-call

@@ -86,3 +86,26 @@ def test_apply_circuit_graph_replay_tableau(sim):
         assert np.array_equal(B.records_to_numpy(rec)[0], want)
         for g, w in zip(B.stab_get_tableau(sim.ctx, 0, circ.n), wtab):
             assert np.array_equal(g, w)
+
+
+def test_long_program_runs_without_one_graph():
+    """A launch sequence longer than the graph budget (here the random n-wide
+    benchmark at n = 48 with 1200 rounds: several thousand layers) is issued
+    as plain launches instead of one captured graph; its records still match
+    the oracle's, over two calls."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    circ = C.random_wide_benchmark(48, 1200, seed=7)
+    s = B.Simulator(0)
+    try:
+        cid = s.compile(circ)
+        assert s.info(cid)["n_layers"] > 2000
+        coins, noise = S.streams_for(circ, 5, range(2))
+        want, _ = oracle.sample(circ, coins, noise)
+        for _ in range(2):
+            got = B.records_to_numpy(s.sample(cid, circ, 2, coins, noise, engine=B.ENGINE_LAYERED))
+            s.sync()
+            assert np.array_equal(got, want)
+    finally:
+        s.close()
