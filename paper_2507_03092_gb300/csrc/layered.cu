@@ -926,7 +926,7 @@ static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pa
 // k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
 struct RandLayout {
     uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
-        wkeys, wlist, wacc, qmask, blocked, pmask, qmap, stat, stale, r, total;
+        wkeys, wlist, wacc, qmask, blocked, pmask, wq, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
     const uint32_t at = o;
@@ -960,6 +960,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.qmask = rl_take(o, 8 * H);
     L.blocked = rl_take(o, 4 * H);
     L.pmask = rl_take(o, 4 * H);
+    L.wq = rl_take(o, 4 * WCAP);
     L.qmap = rl_take(o, item_smem ? 2 * n : 0u);
     L.stat = rl_take(o, item_smem ? n : 0u);
     L.stale = rl_take(o, item_smem ? n : 0u);
@@ -1097,6 +1098,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // the layer (the items whose measured columns are kept current); scans of
     // pivot and destabilizer rows test only these bits
     uint32_t *const pmask = (uint32_t *)(smraw + Lo.pmask);
+    uint32_t *const wq = (uint32_t *)(smraw + Lo.wq);        // wave: measured qubit
     uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
     uint8_t *const stat = item_smem ? smraw + Lo.stat : gstat;
     uint8_t *const mstale = item_smem ? smraw + Lo.stale : gmstale;
@@ -1375,6 +1377,18 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     vz[kk] = in ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
                     vq[kk] = in ? qx4[j] : make_uint4(0u, 0u, 0u, 0u);
                 }
+                // row q <- row p: no other op of the wave reads or writes row q
+                // (it is no rowsum target), and this lane stores only the
+                // elements it has just read
+                uint4 *__restrict__ rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+#pragma unroll
+                for (int kk = 0; kk < 3; kk++) {
+                    const uint32_t j = j0 + 32 * kk + lane;
+                    if (j < H4) {
+                        rq4[j] = vx[kk];
+                        rq4[H4 + j] = vz[kk];
+                    }
+                }
 #pragma unroll
                 for (int kk = 0; kk < 3; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
@@ -1445,6 +1459,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             if (lane == 0) {
                 pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
                 sr[x] = (uint8_t)rbit(r, p);
+                wq[x] = a.P.mitems[M.first + i].q;
+                // row q's sign is the pivot's (read by no other op of the wave)
+                if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
+                else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
                 if (nzcnt > PWS) s_serial = 1;
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
@@ -1515,35 +1533,26 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // serial: a dense pivot, or an overflowed list whose fallback reads
         // pivot rows from the tableau -- the row copies wait for them
         const bool serial = s_serial || npair > paircap || nent > jcap;
-        // row copies: row q <- row p, row p <- +-Z_a (16-byte words over the
-        // Hr-word rows; the words past H are zero in every row), and the outcome
+        // pivot rows become +-Z_a (16-byte stores over the Hr-word rows; the
+        // words past H are zero in every row), with the coin as sign, and the
+        // outcome; row q already holds the old pivot row (work lists)
         auto row_copies = [&]() {
-            // a thread per (wave op, 16-byte element of the x|z row): reads row
-            // p's element, writes it to row q and row p's new element (+-Z_a)
-            const uint32_t per = 2 * H4;
-            for (uint32_t tt = threadIdx.x; tt < nsel * per; tt += blockDim.x) {
-                const uint32_t x = tt / per, c = tt % per;
-                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                const uint32_t mq = a.P.mitems[M.first + pend[k]].q;
-                uint4 *__restrict__ rp4 = reinterpret_cast<uint4 *>(rm + (size_t)p * RS);
-                uint4 *__restrict__ rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
-                const uint4 v = rp4[c];
-                rq4[c] = v;
+            const uint32_t per = 2 * H4, tot = nsel * per;
+            for (uint32_t tt = threadIdx.x; tt < tot; tt += blockDim.x) {
+                const uint32_t x = tt / per, c = tt % per, p = 32 * H + wpiv[sel[x]], mq = wq[x];
                 uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 if (c == H4 + (mq >> 7)) {
                     const uint32_t za = 1u << (mq & 31), zsub = (mq >> 5) & 3u;
                     z = make_uint4(zsub == 0 ? za : 0u, zsub == 1 ? za : 0u, zsub == 2 ? za : 0u, zsub == 3 ? za : 0u);
                 }
-                rp4[c] = z;
+                reinterpret_cast<uint4 *>(rm + (size_t)p * RS)[c] = z;
             }
-            // signs, outcome, record, pending mask: a thread per wave op
+            // sign, outcome, record, pending mask: a thread per wave op
             for (uint32_t x = threadIdx.x; x < nsel; x += blockDim.x) {
                 const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
                 const MItem m = a.P.mitems[M.first + i];
                 const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
                                                                : coin_bit(a.call->st, t, m.coin);
-                if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
-                else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
                 if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
                 else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
                 rowver[q]++;
@@ -1591,25 +1600,33 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // partners, which end as copies of their pivots); then row q's bit is
         // x_{p,b} and row p's is 0.  Touches no bit of another wave op's p or q.
         if (nent <= jcap) {
-            // a thread per listed update whose wave op has a listed support
-            // (at most SUPCAP rows); larger columns by a warp each below
-            for (uint32_t e = threadIdx.x; e < nent; e += blockDim.x) {
-                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
-                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                if (bp && wbsz[k] > SUPCAP) continue;
-                uint32_t *cj = cols + (size_t)j * CW;
-                if (bp) {
-                    const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
-                    const uint32_t nb = wbsz[k];
-                    // support rows come in increasing word order (column scan
-                    // order), so rows of one word are adjacent: one atomic per word
-                    uint32_t cw = 0xffffffffu, cm = 0u;
-                    for (uint32_t f0 = 0; f0 < nb; f0 += 8) {
-                        uint32_t rows[8];
+            // 8 lanes per listed update whose wave op has a listed support (at
+            // most SUPCAP rows, 8 per lane loaded at once); larger columns by a
+            // warp each below
+            {
+                const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
+                for (uint32_t e0 = 4 * (uint32_t)warp; e0 < nent; e0 += 4 * (uint32_t)nw) {
+                    const uint32_t e = e0 + sub;
+                    const bool act = e < nent;
+                    const uint32_t j = act ? ents[e] & 0xffffu : 0u, x = act ? (ents[e] >> 16) & 0x7fffu : 0u;
+                    const uint32_t bp = act ? ents[e] >> 31 : 0u;
+                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                    if (!act || (bp && wbsz[k] > SUPCAP)) continue;
+                    uint32_t *cj = cols + (size_t)j * CW;
+                    if (bp) {
+                        const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
+                        const uint32_t nb = wbsz[k];
+                        uint32_t rows[SUPCAP / 8];
 #pragma unroll
-                        for (uint32_t f = 0; f < 8; f++) rows[f] = f0 + f < nb ? sp[f0 + f] : 0xffffffffu;
+                        for (uint32_t f = 0; f < SUPCAP / 8; f++) {
+                            const uint32_t idx = sl + 8 * f;
+                            rows[f] = idx < nb ? sp[idx] : 0xffffffffu;
+                        }
+                        // this lane's rows: every 8th of the list, in increasing
+                        // word order, so rows of one word are often adjacent
+                        uint32_t cw = 0xffffffffu, cm = 0u;
 #pragma unroll
-                        for (uint32_t f = 0; f < 8; f++) {
+                        for (uint32_t f = 0; f < SUPCAP / 8; f++) {
                             const uint32_t row = rows[f];
                             if (row == 0xffffffffu || row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
                             if ((row >> 5) != cw) {
@@ -1619,14 +1636,15 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                             }
                             cm |= 1u << (row & 31);
                         }
+                        if (cm) atomicXor(&cj[cw], cm);
                     }
-                    if (cm) atomicXor(&cj[cw], cm);
-                    atomicOr(&cj[q >> 5], 1u << (q & 31));
-                } else {
-                    atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                    if (sl == 0) {
+                        if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
+                        else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                        atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                        mstale[j] = 1;
+                    }
                 }
-                atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
-                mstale[j] = 1;
             }
             for (uint32_t e = (uint32_t)warp; e < nent; e += (uint32_t)nw) {
                 const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
@@ -1728,18 +1746,27 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     // row word it meets, so all phases are computed at once;
                     // a word's last key stores the word (carries run across rows)
                     uint32_t carry_c = 0xffffffffu, carry_x = 0u, carry_z = 0u;
-                    for (uint32_t r0 = 0; r0 < nk; r0 += 32) {
+                    uint32_t pre_x[CKEYS / 32], pre_z[CKEYS / 32];      // row words, loaded at once
+#pragma unroll
+                    for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
+                        const uint32_t key = 32 * rr < nk ? wkeys[32 * rr + lane] : 0xffffffffu;
+                        pre_x[rr] = key != 0xffffffffu ? rs[key >> 7] : 0u;
+                        pre_z[rr] = key != 0xffffffffu ? rs[Hr + (key >> 7)] : 0u;
+                    }
+#pragma unroll
+                    for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
+                        const uint32_t r0 = 32 * rr;
+                        if (r0 >= nk) break;
                         const uint32_t key = wkeys[r0 + lane];
                         const bool valid = key != 0xffffffffu;
                         const uint32_t c = valid ? key >> 7 : 0xffffffffu;
                         const uint32_t ml = (key >> 2) & 31u, ms = key & 3u;
-                        uint32_t px_ = 0u, pz_ = 0u, sx = 0u, sz = 0u;
+                        uint32_t px_ = 0u, pz_ = 0u;
+                        const uint32_t sx = pre_x[rr], sz = pre_z[rr];
                         if (valid) {
                             const uint32_t gx = pairs[wlist[ml]] >> 16;
                             px_ = spx[gx * PWS + ms];
                             pz_ = spz[gx * PWS + ms];
-                            sx = rs[c];
-                            sz = rs[Hr + c];
                         }
                         const uint32_t cprev = __shfl_up_sync(FULL_MASK, c, 1);
                         const uint32_t cnext = __shfl_down_sync(FULL_MASK, c, 1);
