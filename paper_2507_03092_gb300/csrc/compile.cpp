@@ -134,35 +134,47 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         }
     }
     // ---- layer ----
-    // owner[q] = index of the item in the current layer touching q, or -1
-    std::vector<int64_t> owner(n, -1);
-    std::vector<uint32_t> touched;
-    int cur = -1;          // current layer type, -1 = none
-    uint32_t first = 0;
-    uint64_t m_ord = 0, c_ord = 0, l_ord = 0, n_gates = 0, n_real = 0;
-    auto close_layer = [&]() {
-        if (cur < 0) return;
-        Layer L{};
-        L.type = (uint32_t)cur;
-        L.first = first;
-        L.count = (cur == LT_GATE ? (uint32_t)P.gitems.size() : (uint32_t)P.mitems.size()) - first;
-        L.has_cond = 0;
-        if (cur == LT_MEAS)
-            for (uint32_t i = L.first; i < L.first + L.count; i++)
-                if (P.mitems[i].flags & (MF_RESET | MF_RESET_ERR | MF_RESET_AFTER)) L.has_cond = 1;
-        if (L.count) P.layers.push_back(L);
-        for (uint32_t q : touched) owner[q] = -1;
-        touched.clear();
-        cur = -1;
+    // Two open layers, one per class (unitary/noise items, measurement items).
+    // An op joins the last layer of its class when every qubit it touches was
+    // last used in an earlier layer; otherwise it starts a new layer of its
+    // class at the end.  Ops on disjoint qubits commute, so the layered
+    // program equals the op list: an op never moves before an earlier op on
+    // one of its qubits, and measurement-class ops keep their circuit order
+    // (each goes into the last measurement layer or a new one after it), which
+    // keeps the coin each random outcome reads the one of the op list.
+    struct LB {
+        int type;
+        std::vector<GItem> g;
+        std::vector<MItem> m;
     };
-    auto open_layer = [&](int type) {
-        close_layer();
-        cur = type;
-        first = type == LT_GATE ? (uint32_t)P.gitems.size() : (uint32_t)P.mitems.size();
+    struct Ref {
+        int32_t layer = -1, idx = -1;
     };
-    auto touch = [&](uint32_t q, int64_t item) { owner[q] = item; touched.push_back(q); };
+    std::vector<LB> lays;
+    std::vector<int32_t> front(n, -1);   // layer of the last op on each qubit
+    std::vector<Ref> last_g(n);          // gate/noise item of the last op on q (if it was one)
     // last_m[q]: the measurement item of the last op on q if that op was an M or R
-    std::vector<int64_t> last_m(n, -1);
+    std::vector<Ref> last_m(n);
+    int32_t last_gl = -1, last_ml = -1;  // the open (last) layer of each class
+    uint64_t m_ord = 0, c_ord = 0, l_ord = 0, n_gates = 0, n_real = 0;
+    auto gate_layer = [&](int32_t lb) {
+        if (last_gl >= 0 && lb <= last_gl) return last_gl;
+        lays.push_back(LB{LT_GATE, {}, {}});
+        return last_gl = (int32_t)lays.size() - 1;
+    };
+    auto meas_layer = [&](int32_t lb) {
+        if (last_ml >= 0 && lb <= last_ml) return last_ml;
+        lays.push_back(LB{LT_MEAS, {}, {}});
+        return last_ml = (int32_t)lays.size() - 1;
+    };
+    auto put_gate = [&](const GItem &g) {
+        const int32_t L = gate_layer(std::max(front[g.a], front[g.b]) + 1);
+        lays[L].g.push_back(g);
+        const Ref r{L, (int32_t)lays[L].g.size() - 1};
+        front[g.a] = front[g.b] = L;
+        last_g[g.a] = last_g[g.b] = r;
+        last_m[g.a] = last_m[g.b] = Ref{};
+    };
 
     for (size_t k = 0; k < n_ops; k++) {
         const stab_op &o = ops[k];
@@ -171,9 +183,9 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         n_real++;
         if (kind == STAB_MPP) {
             const uint32_t nf = o.q0;
-            bool clash = cur != LT_MEAS;
-            for (uint32_t i = 1; i <= nf; i++) clash |= owner[ops[k + i].q0] >= 0;
-            if (clash) open_layer(LT_MEAS);
+            int32_t lb = 0;
+            for (uint32_t i = 1; i <= nf; i++) lb = std::max(lb, front[ops[k + i].q0] + 1);
+            const int32_t L = meas_layer(lb);
             MItem m{};
             m.q = ops[k + nf].q0;
             m.coin = (uint32_t)c_ord++;
@@ -184,27 +196,26 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
             for (uint32_t i = 1; i <= nf; i++) {
                 const stab_op &f = ops[k + i];
                 P.mfactors.push_back(f.q0 | (f.q1 << 30));
-                touch(f.q0, (int64_t)P.mitems.size());
-                last_m[f.q0] = -1;
+                front[f.q0] = L;
+                last_g[f.q0] = Ref{};
+                last_m[f.q0] = Ref{};
             }
-            P.mitems.push_back(m);
+            lays[L].m.push_back(m);
             k += nf;
             continue;
         }
         uint32_t a = o.q0, b = is_two(kind) ? o.q1 : o.q0;
-        if (kind == STAB_R && last_m[a] >= 0) {
+        if (kind == STAB_R && last_m[a].layer >= 0) {
             // R right after M/R on the same qubit: deterministic, outcome = that
             // measurement's; fold it in as "X if the outcome was 1" (or drop it
             // after a reset, whose outcome is 0).  Its coin slot is still used up.
-            MItem &prev = P.mitems[(size_t)last_m[a]];
+            MItem &prev = lays[last_m[a].layer].m[last_m[a].idx];
             if (!(prev.flags & (MF_RESET | MF_RESET_AFTER))) prev.flags |= MF_RESET_AFTER;
             c_ord++;
             continue;
         }
-        last_m[a] = -1;
-        if (is_two(kind)) last_m[b] = -1;
         if (is_meas_class(kind)) {
-            if (cur != LT_MEAS || owner[a] >= 0) open_layer(LT_MEAS);
+            const int32_t L = meas_layer(front[a] + 1);
             MItem m{};
             m.q = a;
             m.rec = 0xffffffffu;
@@ -218,53 +229,55 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
                 if (kind == STAB_M) m.rec = (uint32_t)m_ord++;
                 else m.flags = MF_RESET;
             }
-            touch(a, (int64_t)P.mitems.size());
-            if (kind != STAB_RESET_ERR) last_m[a] = (int64_t)P.mitems.size();
-            P.mitems.push_back(m);
+            lays[L].m.push_back(m);
+            front[a] = L;
+            last_g[a] = Ref{};
+            last_m[a] = kind != STAB_RESET_ERR ? Ref{L, (int32_t)lays[L].m.size() - 1} : Ref{};
             continue;
         }
         if (is_gate(kind)) {
             n_gates++;
-            bool free_ = cur == LT_GATE && owner[a] < 0 && owner[b] < 0;
-            if (!free_) open_layer(LT_GATE);
             GItem g{};
             g.a = a; g.b = b; g.gate = kind;
-            int64_t idx = (int64_t)P.gitems.size();
-            touch(a, idx);
-            if (b != a) touch(b, idx);
-            P.gitems.push_back(g);
+            put_gate(g);
             continue;
         }
-        // noise op
+        // noise op: joins the item of the gate (or noise) that was the last op
+        // on its qubits, applied after it, else an item of its own
         uint32_t nl = (uint32_t)l_ord++;
-        bool attached = false;
-        if (cur == LT_GATE) {
-            int64_t oa = owner[a], ob = owner[b];
-            if (oa >= 0 && (b == a || ob == oa)) {
-                GItem &g = P.gitems[(size_t)oa];
-                if (g.nn < 2) {
-                    uint8_t t;
-                    if (b == a) t = (a == g.a) ? NT_A : NT_B;
-                    else t = (a == g.a) ? NT_AB : NT_BA;
-                    g.nk[g.nn] = kind; g.nt[g.nn] = t; g.nl[g.nn] = nl; g.np[g.nn] = o.arg;
-                    g.nn++;
-                    attached = true;
-                }
+        const Ref ra = last_g[a], rb = last_g[b];
+        if (ra.layer >= 0 && (b == a || (rb.layer == ra.layer && rb.idx == ra.idx))) {
+            GItem &g = lays[ra.layer].g[ra.idx];
+            if (g.nn < 2 && (b == a || (g.a != g.b && (a == g.a || a == g.b)))) {
+                uint8_t t;
+                if (b == a) t = (a == g.a) ? NT_A : NT_B;
+                else t = (a == g.a) ? NT_AB : NT_BA;
+                g.nk[g.nn] = kind; g.nt[g.nn] = t; g.nl[g.nn] = nl; g.np[g.nn] = o.arg;
+                g.nn++;
+                last_m[a] = last_m[b] = Ref{};
+                continue;
             }
         }
-        if (!attached) {
-            bool free_ = cur == LT_GATE && owner[a] < 0 && owner[b] < 0;
-            if (!free_) open_layer(LT_GATE);
-            GItem g{};
-            g.a = a; g.b = b; g.gate = 0; g.nn = 1;
-            g.nk[0] = kind; g.nt[0] = (b == a) ? NT_A : NT_AB; g.nl[0] = nl; g.np[0] = o.arg;
-            int64_t idx = (int64_t)P.gitems.size();
-            touch(a, idx);
-            if (b != a) touch(b, idx);
-            P.gitems.push_back(g);
-        }
+        GItem g{};
+        g.a = a; g.b = b; g.gate = 0; g.nn = 1;
+        g.nk[0] = kind; g.nt[0] = (b == a) ? NT_A : NT_AB; g.nl[0] = nl; g.np[0] = o.arg;
+        put_gate(g);
     }
-    close_layer();
+    // flatten: items of each layer contiguous, layers in order
+    for (const LB &lb : lays) {
+        Layer L{};
+        L.type = (uint32_t)lb.type;
+        if (lb.type == LT_GATE) {
+            L.first = (uint32_t)P.gitems.size();
+            L.count = (uint32_t)lb.g.size();
+            P.gitems.insert(P.gitems.end(), lb.g.begin(), lb.g.end());
+        } else {
+            L.first = (uint32_t)P.mitems.size();
+            L.count = (uint32_t)lb.m.size();
+            P.mitems.insert(P.mitems.end(), lb.m.begin(), lb.m.end());
+        }
+        if (L.count) P.layers.push_back(L);
+    }
     // folded resets may have flagged items of layers closed earlier
     for (auto &L : P.layers)
         if (L.type == LT_MEAS) {

@@ -228,7 +228,7 @@ struct WaveCaps {
     // lowered only by tests, to see the guard fire and the context survive.
     uint32_t wave_limit = 0xffffffffu;
 };
-constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list
+constexpr uint32_t SUPCAP = 64;        // rows kept in a measured column's support list (two per lane of a warp)
 constexpr uint32_t PWCAP = 64;         // nonzero words kept per pivot row
 constexpr uint32_t XSCAP = 32;         // layer items kept per pivot-row X support
 constexpr uint8_t XS_OVER = 0xff, XS_UNKNOWN = 0xfe;

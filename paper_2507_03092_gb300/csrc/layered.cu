@@ -1360,6 +1360,13 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
             const uint32_t k = sel[x], i = pend[k];
             const uint32_t q = wpiv[k], p = 32 * H + q;
+            // loads of this op that do not depend on the row scans, issued
+            // first: its support list (two entries per lane) and its qubit
+            const uint32_t nb = wbsz[k];
+            const uint16_t *sp = msup + (size_t)i * SUPCAP;
+            const uint32_t sup0 = nb <= SUPCAP && (uint32_t)lane < nb ? sp[lane] : 0u;
+            const uint32_t sup1 = nb <= SUPCAP && (uint32_t)lane + 32 < nb ? sp[lane + 32] : 0u;
+            const uint32_t mq = lane == 0 ? a.P.mitems[M.first + i].q : 0u;
             // pending ops whose qubit has X or Y in row p or row q (their
             // measured columns change), and the nonzero words of row p: 16-byte
             // vectors of rows p (x, z) and q (x)
@@ -1367,10 +1374,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             const uint4 *__restrict__ pz4 = px4 + H4;
             const uint4 *__restrict__ qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
             uint32_t nzcnt = 0;
-            for (uint32_t j0 = 0; j0 < H4; j0 += 96) {
-                uint4 vx[3], vz[3], vq[3];
+            for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
+                uint4 vx[2], vz[2], vq[2];
 #pragma unroll
-                for (int kk = 0; kk < 3; kk++) {
+                for (int kk = 0; kk < 2; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
                     const bool in = j < H4;
                     vx[kk] = in ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
@@ -1382,7 +1389,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 // elements it has just read
                 uint4 *__restrict__ rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
 #pragma unroll
-                for (int kk = 0; kk < 3; kk++) {
+                for (int kk = 0; kk < 2; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
                     if (j < H4) {
                         rq4[j] = vx[kk];
@@ -1390,7 +1397,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     }
                 }
 #pragma unroll
-                for (int kk = 0; kk < 3; kk++) {
+                for (int kk = 0; kk < 2; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
                     const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
                     const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
@@ -1459,7 +1466,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             if (lane == 0) {
                 pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
                 sr[x] = (uint8_t)rbit(r, p);
-                wq[x] = a.P.mitems[M.first + i].q;
+                wq[x] = mq;
                 // row q's sign is the pivot's (read by no other op of the wave)
                 if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
                 else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
@@ -1490,14 +1497,12 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 nxt[f] = prev == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)prev;
                 hslot[f] = (uint16_t)h;
             };
-            if (wbsz[k] <= SUPCAP) {
+            if (nb <= SUPCAP) {
                 // one append per warp and batch (a single shared counter would
                 // otherwise take every lane's atomic in turn)
-                const uint16_t *sp = msup + (size_t)i * SUPCAP;
-                const uint32_t nb = wbsz[k];
                 for (uint32_t e0 = 0; e0 < nb; e0 += 32) {
                     const uint32_t e = e0 + lane;
-                    const uint32_t row = e < nb ? sp[e] : 0u;
+                    const uint32_t row = e0 == 0 ? sup0 : sup1;
                     if (e < nb) dirty[row >> 5] = 1;
                     const bool keep = e < nb && row != p && !((qmask[row >> 5] >> (row & 31)) & 1u);
                     const uint32_t bal = __ballot_sync(FULL_MASK, keep);
