@@ -233,7 +233,7 @@ C4_T1T2 = {"T1": 100e-6, "T2": 80e-6, "t1q": 50e-9, "t2q": 300e-9, "tm": 1e-6}
 C4_DISTANCES = (3, 5, 7, 9, 11)
 
 
-def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
+def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0, autotune=True, reps=3):
     T = C4_T1T2
     dists = S.shot_distances(seed, shots)
     groups, keep, circs = [], [], {}
@@ -249,12 +249,13 @@ def batched_vs_plain(sim, B, torch, shots=4096, plain_shots=64, seed=0):
         g.d_record, g.record_words = rec.data_ptr(), circ.record_words
         groups.append(g)
         keep.append(rec)
-    B.stab_autotune(sim.ctx, [circs[d][1] for d in circs], 256)
+    if autotune:
+        B.stab_autotune(sim.ctx, [circs[d][1] for d in circs], 256)
     tunes = {d: B.stab_get_tune(sim.ctx, circs[d][0].n) for d in circs}
     B.stab_sample_batch(sim.ctx, groups)            # warm-up
     sim.sync()
     ts = []
-    for _ in range(3):
+    for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         B.stab_sample_batch(sim.ctx, groups)
@@ -473,6 +474,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving trace")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' rates")
     ap.add_argument("--ref-step-s", type=float, default=8.0)
+    ap.add_argument("--only", choices=["batched"], default=None,
+                    help="run one workload alone (for profiling): 'batched' = the 4096-shot mixed-distance "
+                         "batch, default launch shapes, one warm-up and one timed call")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -486,6 +490,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.only == "batched":
+        sim = B.Simulator(local)
+        res = batched_vs_plain(sim, B, torch, plain_shots=5, autotune=False, reps=1)
+        sim.close()
+        print(json.dumps({"only": "batched", "batched": res}), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
