@@ -90,19 +90,23 @@ def l2_sweep(sim, B, torch):
     props = torch.cuda.get_device_properties(sim.device)
     l2_bytes = int(getattr(props, "L2_cache_size", 0) or 0)
     per = {}
-    for mb in (8, 16, 32, 48, 64):
-        per[mb] = B.stab_probe_copy(sim.ctx, mb << 20, 200)
+    for mb in (8, 16, 32, 48, 64, 80, 96, 112, 128):
+        per[mb] = B.stab_probe_copy(sim.ctx, mb << 20, 200 if mb <= 64 else 50)
     best_mb = max(per, key=per.get)
+    # largest working set that still gets at least 90 % of the best figure
+    knee = max(mb for mb, v in per.items() if v >= 0.9 * per[best_mb])
     hbm_probe = B.stab_probe_copy(sim.ctx, 2 << 30, 5)
-    return {"l2_gbs": per[best_mb], "best_working_set_mb": best_mb,
+    return {"l2_gbs": per[best_mb], "best_working_set_mb": best_mb, "l2_effective_bytes": knee << 20,
             "per_working_set_gbs": {str(k): round(v, 1) for k, v in per.items()},
             "l2_cache_bytes": l2_bytes, "hbm_gbs_same_probe": hbm_probe,
-            "method": "stab_probe_copy: 16-byte ld/st.cg copy, 200 passes in one launch over "
-                      "two buffers of half the working set, CUDA events; read + write bytes"}
+            "method": "stab_probe_copy: 16-byte ld/st.cg copy, 200 passes (50 above 64 MB) in one "
+                      "launch over two buffers of half the working set, CUDA events; read + write bytes; "
+                      "l2_effective_bytes = the largest working set still within 10 % of the best"}
 
 
 def roof_bound(working_set_bytes, l2_bytes):
-    """'l2' when one launch's working set fits the L2 cache, else 'hbm'."""
+    """'l2' when one launch's working set fits the L2 cache (the largest
+    working set the copy probe still runs at L2 speed), else 'hbm'."""
     return "l2" if l2_bytes and working_set_bytes <= l2_bytes else "hbm"
 
 
@@ -606,7 +610,7 @@ def main():
     ds = kstats[dom]
     hbm, src = peaks()
     l2 = l2_sweep(sim, B, torch)
-    l2_gbs, l2_size = l2["l2_gbs"], l2["l2_cache_bytes"]
+    l2_gbs, l2_size = l2["l2_gbs"], min(l2["l2_cache_bytes"] or 0, l2["l2_effective_bytes"])
     qm_b, rm_b = tableau_bytes(circ.n)
     # one launch's working set: a gate run reads and writes the column-packed
     # copy and writes the row-packed stabilizer half; the random-measurement

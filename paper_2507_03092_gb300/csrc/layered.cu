@@ -1003,7 +1003,8 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
     for (uint32_t k = 2; k <= nk; k <<= 1)
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
             for (uint32_t t = lane; t < nk / 2; t += 32) {
-                const uint32_t i = 2 * j * (t / j) + (t % j), l = i + j;     // pair (i, l), i < l
+                // pair (i, l = i + j), i < l: t with a zero bit inserted at j (a power of two)
+                const uint32_t i = ((t & ~(j - 1u)) << 1) | (t & (j - 1u)), l = i + j;
                 const bool up = (i & k) == 0;
                 const uint32_t a = keys[i], b = keys[l];
                 if ((a > b) == up) {
