@@ -306,7 +306,11 @@ cudaError_t resident_run(const ResJob *d_jobs, uint32_t n_jobs, uint32_t max_n,
 // 7 multi-pivot rows)
 enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K = 4, DC_SUM_A = 5,
              DC_PIV_RECOMP = 6, DC_ROWSUM_PASSES = 7, DC_PHASE0 = 8, DC_N_PHASES = 11,
-             DC_XS_RECOMP = 19, DC_N = 24 };
+             DC_XS_RECOMP = 19, DC_N = 24,
+             // SM cycles of warp 0's sub-steps: work lists (row scans, pair lists),
+             // multi-pivot rows (chain walk and keys, sort, scan rows)
+             DC_W0_LIST_SCAN = 16, DC_W0_LIST_PAIRS = 17, DC_W0_MULTI_WALK = 18, DC_W0_MULTI_SORT = 20,
+             DC_W0_MULTI_ROWS = 21 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

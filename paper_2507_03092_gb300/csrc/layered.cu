@@ -248,8 +248,8 @@ __global__ void k_noise_events(LArgs a) {
 // groups of 4 per thread, all four loaded before any is used).  KIND != 0:
 // every item of the layer is that gate (no per-item dispatch).
 template <uint32_t KIND>
-__device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_t count, uint32_t *sx,
-                                           uint32_t *sz, uint32_t &racc) {
+__device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_t count, uint2 *sxz,
+                                           uint32_t &racc) {
     for (uint32_t i0 = threadIdx.x; i0 < count; i0 += 4 * blockDim.x) {
         uint2 v[4];
 #pragma unroll
@@ -261,22 +261,17 @@ __device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_
         for (int k = 0; k < 4; k++) {
             const uint32_t ga = v[k].x & 0xffffu, gb = v[k].x >> 16, gk = v[k].y;
             if (!gk) continue;
-            if (KIND == STAB_H || KIND == STAB_S) {
-                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
-                racc ^= apply_gate(KIND, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za;
-            } else if (KIND == STAB_CX || KIND == STAB_CZ) {
-                uint32_t xa = sx[ga], za = sz[ga], xb = sx[gb], zb = sz[gb];
-                racc ^= apply_gate(KIND, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za; sx[gb] = xb; sz[gb] = zb;
-            } else {
-                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
-                const bool two = gb != ga;
-                if (two) { xb = sx[gb]; zb = sz[gb]; }
-                racc ^= apply_gate(gk, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za;
-                if (two) { sx[gb] = xb; sz[gb] = zb; }
+            const uint2 va = sxz[ga];
+            uint32_t xa = va.x, za = va.y, xb = 0, zb = 0;
+            const bool two = gb != ga;
+            if (two) {
+                const uint2 vb = sxz[gb];
+                xb = vb.x;
+                zb = vb.y;
             }
+            racc ^= apply_gate(gk, xa, za, xb, zb);
+            sxz[ga] = make_uint2(xa, za);
+            if (two) sxz[gb] = make_uint2(xb, zb);
         }
     }
 }
@@ -285,8 +280,8 @@ __device__ __forceinline__ void gate_items(const uint2 *__restrict__ it, uint32_
 // per thread loaded before any is used, so a layer of up to 8 x blockDim items
 // costs one round trip for its items.
 template <uint32_t KIND>
-__device__ __forceinline__ void gate_items_u(const uint32_t *__restrict__ ab, uint32_t count, uint32_t *sx,
-                                             uint32_t *sz, uint32_t &racc) {
+__device__ __forceinline__ void gate_items_u(const uint32_t *__restrict__ ab, uint32_t count, uint2 *sxz,
+                                             uint32_t &racc) {
     for (uint32_t i0 = threadIdx.x; i0 < count; i0 += 8 * blockDim.x) {
         uint32_t v[8];
 #pragma unroll
@@ -299,13 +294,16 @@ __device__ __forceinline__ void gate_items_u(const uint32_t *__restrict__ ab, ui
             if (i0 + k * blockDim.x >= count) break;
             const uint32_t ga = v[k] & 0xffffu, gb = v[k] >> 16;
             if (KIND == STAB_H || KIND == STAB_S) {
-                uint32_t xa = sx[ga], za = sz[ga], xb = 0, zb = 0;
+                const uint2 va = sxz[ga];
+                uint32_t xa = va.x, za = va.y, xb = 0, zb = 0;
                 racc ^= apply_gate(KIND, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za;
+                sxz[ga] = make_uint2(xa, za);
             } else {
-                uint32_t xa = sx[ga], za = sz[ga], xb = sx[gb], zb = sz[gb];
+                const uint2 va = sxz[ga], vb = sxz[gb];
+                uint32_t xa = va.x, za = va.y, xb = vb.x, zb = vb.y;
                 racc ^= apply_gate(KIND, xa, za, xb, zb);
-                sx[ga] = xa; sz[ga] = za; sx[gb] = xb; sz[gb] = zb;
+                sxz[ga] = make_uint2(xa, za);
+                sxz[gb] = make_uint2(xb, zb);
             }
         }
     }
@@ -314,15 +312,14 @@ __device__ __forceinline__ void gate_items_u(const uint32_t *__restrict__ ab, ui
 // A layer whose noise events overflowed their slots: every draw of the layer
 // evaluated again (kept out of line: the common path needs none of this).
 __device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t count, const Thr *thr,
-                                                 const CallArgs *call, uint32_t t, const uint32_t *sx,
-                                                 const uint32_t *sz) {
+                                                 const CallArgs *call, uint32_t t, const uint2 *sxz) {
     uint32_t racc = 0;
     for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) {
         const GItem gi = items[k];
         if (!gi.nn) continue;
         uint32_t Pa, Pb;
         item_noise(gi, call->st, t, thr, Pa, Pb);
-        racc ^= xz_flip(Pa, sx[gi.a], sz[gi.a]) ^ xz_flip(Pb, sx[gi.b], sz[gi.b]);
+        racc ^= xz_flip(Pa, sxz[gi.a].x, sxz[gi.a].y) ^ xz_flip(Pb, sxz[gi.b].x, sxz[gi.b].y);
     }
     return racc;
 }
@@ -345,7 +342,9 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         s_layer[threadIdx.x] = a.P.layers[l];
         s_evc[threadIdx.x] = a.ev_cnt ? a.ev_cnt[(size_t)t * a.P.n_layers + l] : 0u;
     }
-    uint32_t *sx = smem, *sz = smem + n;
+    // the slice: word w of column j's x and z planes side by side (one 8-byte
+    // shared-memory access per column and gate operand)
+    uint2 *sxz = reinterpret_cast<uint2 *>(smem);
     uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
     uint32_t *rm = a.rm + t * a.rm_stride;
     uint8_t *dirty = a.dirty + (size_t)t * CW;
@@ -368,17 +367,11 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t j = j0 + k * bd;
-                if (j < n) {
-                    sx[j] = vx[k];
-                    sz[j] = vz[k];
-                }
+                if (j < n) sxz[j] = make_uint2(vx[k], vz[k]);
             }
         }
     } else {
-        slice_load_rm(rm, a.RS, a.Hr, H, n, w, [&](uint32_t j, uint32_t x, uint32_t z) {
-            sx[j] = x;
-            sz[j] = z;
-        });
+        slice_load_rm(rm, a.RS, a.Hr, H, n, w, [&](uint32_t j, uint32_t x, uint32_t z) { sxz[j] = make_uint2(x, z); });
     }
     __syncthreads();
     uint32_t racc = 0;
@@ -390,7 +383,7 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         const uint32_t *fl = a.flips + t * 2 * a.m_stride;
         for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
             const uint32_t f = fl[e], q = f & 0x3fffffffu;
-            racc ^= (f >> 30) == 1u ? sz[q] : sx[q];
+            racc ^= (f >> 30) == 1u ? sxz[q].y : sxz[q].x;
         }
         __syncthreads();          // every flip has read its pre-gate word
     }
@@ -412,25 +405,28 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         // run a loop specialised to it
         const uint32_t *__restrict__ iab = a.P.sab + L.first;
         switch (L.uniform) {
-        case STAB_H: gate_items_u<STAB_H>(iab, L.count, sx, sz, racc); break;
-        case STAB_CX: gate_items_u<STAB_CX>(iab, L.count, sx, sz, racc); break;
-        case STAB_CZ: gate_items_u<STAB_CZ>(iab, L.count, sx, sz, racc); break;
-        case STAB_S: gate_items_u<STAB_S>(iab, L.count, sx, sz, racc); break;
-        default: gate_items<0>(it, L.count, sx, sz, racc); break;
+        case STAB_H: gate_items_u<STAB_H>(iab, L.count, sxz, racc); break;
+        case STAB_CX: gate_items_u<STAB_CX>(iab, L.count, sxz, racc); break;
+        case STAB_CZ: gate_items_u<STAB_CZ>(iab, L.count, sxz, racc); break;
+        case STAB_S: gate_items_u<STAB_S>(iab, L.count, sxz, racc); break;
+        default: gate_items<0>(it, L.count, sxz, racc); break;
         }
         __syncthreads();
         if (L.n_noisy) {
             // the layer's Pauli errors act after its gates
             const uint32_t cnt = ecnt;
             if (cnt <= L.ev_cap) {
-                if (threadIdx.x < cnt) racc ^= xz_flip(my_ev >> 30, sx[my_ev & 0x3fffffffu], sz[my_ev & 0x3fffffffu]);
+                if (threadIdx.x < cnt) {
+                    const uint2 v = sxz[my_ev & 0x3fffffffu];
+                    racc ^= xz_flip(my_ev >> 30, v.x, v.y);
+                }
                 const uint32_t *ev = a.ev + (size_t)t * a.P.ev_total + L.ev_off;
                 for (uint32_t e = threadIdx.x + blockDim.x; e < cnt; e += blockDim.x) {
                     const uint32_t v = ev[e], q = v & 0x3fffffffu;
-                    racc ^= xz_flip(v >> 30, sx[q], sz[q]);
+                    racc ^= xz_flip(v >> 30, sxz[q].x, sxz[q].y);
                 }
             } else {
-                racc ^= layer_noise_all(a.P.gitems + L.first, L.count, a.P.thr, a.call, t, sx, sz);
+                racc ^= layer_noise_all(a.P.gitems + L.first, L.count, a.P.thr, a.call, t, sxz);
             }
             __syncthreads();
         }
@@ -440,8 +436,9 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sred[warp] = racc;
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        qx[(size_t)w * n + j] = sx[j];
-        qz[(size_t)w * n + j] = sz[j];
+        const uint2 v = sxz[j];
+        qx[(size_t)w * n + j] = v.x;
+        qz[(size_t)w * n + j] = v.y;
     }
     __syncthreads();
     if (warp == 0) {
@@ -455,8 +452,8 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     if (w == 0 && threadIdx.x == 0) a.tflags[t] &= ~TF_DESTAB_FRESH;
     if (g.want_rm && w >= H) {        // stabilizer half only (see TF_DESTAB_FRESH)
         slice_store_rm(rm, a.RS, a.Hr, H, w,
-                       [&](uint32_t j) { return j < n ? sx[j] : 0u; },
-                       [&](uint32_t j) { return j < n ? sz[j] : 0u; });
+                       [&](uint32_t j) { return j < n ? sxz[j].x : 0u; },
+                       [&](uint32_t j) { return j < n ? sxz[j].y : 0u; });
     }
 }
 
@@ -1142,6 +1139,20 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             tlast = now_;                                                     \
         }                                                                     \
     } while (0)
+    // sub-step times of warp 0 inside a phase (instrumentation, profiling only)
+    unsigned long long tstep = 0;
+#define STEP_START()                                                          \
+    do {                                                                      \
+        if (threadIdx.x == 0 && a.stats) tstep = clock64();                    \
+    } while (0)
+#define STEP(slot)                                                            \
+    do {                                                                      \
+        if (threadIdx.x == 0 && a.stats) {                                    \
+            const unsigned long long now_ = clock64();                         \
+            atomicAdd(&a.stats[(slot)], now_ - tstep);                        \
+            tstep = now_;                                                     \
+        }                                                                     \
+    } while (0)
     auto chain_first = [&](uint32_t e) { return htail[hslot[e]]; };
     // a pair's sign flip: its pivot's sign plus half its (even) power of i
     auto pair_flip = [&](uint32_t x, int acc) -> uint32_t {
@@ -1359,6 +1370,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // ---- (4) work lists, one warp per wave op
         const uint32_t nsel = min(s_nsel, wcap);
         for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+            STEP_START();
             const uint32_t k = sel[x], i = pend[k];
             const uint32_t q = wpiv[k], p = 32 * H + q;
             // loads of this op that do not depend on the row scans, issued
@@ -1475,6 +1487,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
             }
+            STEP(DC_W0_LIST_SCAN);
             // rowsum pairs: rows of the measured column except the pivot and
             // the wave's destabilizer partners, linked per row
             // link pair f (row, this wave op) into its row's chain
@@ -1526,6 +1539,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     }
                 }
             }
+            STEP(DC_W0_LIST_PAIRS);
         }
         __syncthreads();
         PHASE(5);
@@ -1723,6 +1737,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 }
                 uint32_t *rs = rm + (size_t)row * RS;
                 uint32_t cur = e0, flips = 0;
+                STEP_START();
                 for (uint32_t pass = 0; cur < PAIRCAP && pass < PAIRCAP; pass++) {
                     // up to 32 pairs of the chain, in chain order
                     uint32_t cnt = 0;
@@ -1746,7 +1761,9 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     for (uint32_t w = 0; w < PWS; w++)
                         if (w < lnw) wkeys[PWS * lane + w] = ((uint32_t)spc[lx * PWS + w] << 7) | ((uint32_t)lane << 2) | w;
                     __syncwarp();
+                    STEP(DC_W0_MULTI_WALK);
                     warp_sort_keys(wkeys, nk);
+                    STEP(DC_W0_MULTI_SORT);
                     // the sorted keys, 32 at a time: a segmented XOR prefix scan
                     // over each word's keys (chain order) gives every pivot the
                     // row word it meets, so all phases are computed at once;
@@ -1808,6 +1825,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         __syncwarp();
                     }
                     __syncwarp();
+                    STEP(DC_W0_MULTI_ROWS);
                     if ((uint32_t)lane < cnt) {
                         flips ^= pair_flip(lx, wacc[lane]);
                         wacc[lane] = 0;
@@ -1846,6 +1864,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         PHASE(7);
     }
 #undef PHASE
+#undef STEP
+#undef STEP_START
     __syncthreads();
     for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
     if (item_smem)
