@@ -205,6 +205,7 @@ struct CallArgs {
 struct LaunchCfg {
     int sm_count = 0;
     size_t smem_optin = 0;
+    uint32_t rand_cluster = 1;    // CTAs per tableau of the random-measurement kernel (set per run)
 };
 
 // Capacities of the random-measurement wave kernel's shared-memory lists.

@@ -39,8 +39,16 @@
 //    loads each slice when one follows, else by this kernel.
 #include "device_common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace cg = cooperative_groups;
 
 namespace stab {
 
@@ -650,6 +658,68 @@ __device__ int det_outcome_warp(const uint32_t *__restrict__ rm, uint32_t RS, ui
     return (e >> 1) & 1;
 }
 
+// The same outcome from a listed support: lst[0..nk) are the set destabilizer
+// slots of the column (nk <= SUPCAP, in any order; the row product is the same
+// in every order because stabilizer rows commute), each naming stabilizer row
+// 32H + slot.  Each row is read whole, as 8-byte vectors (DET_NV per lane per
+// plane: one round trip per row for H <= 64 * DET_NV words, 320 at DET_NV = 5,
+// which covers d = 71); needs an 8-byte aligned rm and an even Hr.
+constexpr int DET_NV = 5;
+__device__ __forceinline__ int det_outcome_list(const uint32_t *__restrict__ rm, uint32_t RS, uint32_t Hr,
+                                                uint32_t H, const uint32_t *__restrict__ r,
+                                                const uint16_t *lst, uint32_t nk, uint32_t q, int *err) {
+    const int lane = threadIdx.x & 31;
+    int acc = 0, rsum = 0;
+    bool ok = true;
+    for (uint32_t e = lane; e < nk; e += 32) rsum += (int)rbit(r, 32 * H + lst[e]);
+    const uint32_t H2 = (H + 1) >> 1;
+    for (uint32_t v0 = 0; v0 < H2; v0 += 32 * DET_NV) {
+        uint32_t zp[2 * DET_NV], xp[2 * DET_NV];
+#pragma unroll
+        for (int k = 0; k < 2 * DET_NV; k++) { zp[k] = 0u; xp[k] = 0u; }
+        for (uint32_t e = 0; e < nk; e++) {
+            const uint32_t *__restrict__ row = rm + (size_t)(32 * H + lst[e]) * RS;
+            const uint2 *__restrict__ rx = reinterpret_cast<const uint2 *>(row);
+            const uint2 *__restrict__ rz = reinterpret_cast<const uint2 *>(row + Hr);
+            uint2 xv[DET_NV], zv[DET_NV];
+#pragma unroll
+            for (int k = 0; k < DET_NV; k++) {
+                const uint32_t j = v0 + 32 * k + lane;
+                xv[k] = j < H2 ? rx[j] : make_uint2(0u, 0u);
+                zv[k] = j < H2 ? rz[j] : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < DET_NV; k++) {
+                const uint32_t w = 2 * (v0 + 32 * k + lane);
+                // a word past H (row padding, odd H) takes no part
+                const uint32_t x0 = xv[k].x, z0 = zv[k].x;
+                const uint32_t x1 = w + 1 < H ? xv[k].y : 0u, z1 = w + 1 < H ? zv[k].y : 0u;
+                acc += __popc(x0 & z0) + 2 * __popc(x0 & zp[2 * k]) + __popc(x1 & z1) +
+                       2 * __popc(x1 & zp[2 * k + 1]);
+                zp[2 * k] ^= z0;
+                xp[2 * k] ^= x0;
+                zp[2 * k + 1] ^= z1;
+                xp[2 * k + 1] ^= x1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * DET_NV; k++) {
+            const uint32_t w = 2 * (v0 + 32 * (k >> 1) + lane) + (k & 1);
+            if (w < H) {
+                const uint32_t wantz = (w == (q >> 5)) ? (1u << (q & 31)) : 0u;
+                ok &= (xp[k] == 0u) && (zp[k] == wantz);
+            }
+        }
+    }
+    acc = __reduce_add_sync(FULL_MASK, acc);
+    rsum = __reduce_add_sync(FULL_MASK, rsum);
+    const int e = (acc + 2 * rsum) & 3;
+    if (!__all_sync(FULL_MASK, ok)) set_err(err, DERR_BAD_PRODUCT);
+    if (e & 1) set_err(err, DERR_ODD_PHASE);
+    __syncwarp();
+    return (e >> 1) & 1;
+}
+
 __device__ __forceinline__ void count(const LArgs &a, int k, unsigned long long v) {
     if (a.stats && v) atomicAdd(&a.stats[k], v);
 }
@@ -676,15 +746,18 @@ __device__ __forceinline__ void write_record(const LArgs &a, uint32_t t, uint32_
 // stabilizer half (as slot - 32H, ~0 if none), size = number of set rows, and
 // when size <= SUPCAP the set rows (in no particular order) into sup[].
 // Columns of a multiple of 4 words (16-byte aligned) are read as 16-byte
-// vectors, 512 words per batch (four per lane in flight, one round trip at
-// d = 71); others as words, 256 per batch.
-__device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ col, uint32_t H, uint32_t CW,
-                                                 uint32_t &piv, uint32_t &size, uint16_t *__restrict__ sup) {
+// vectors, NV4 per lane in flight (128 * NV4 words per batch: NV4 = 5 takes a
+// d = 71 column, 632 words, in one round trip); others as words, 256 per
+// batch.  sup may point to shared or global memory.
+template <int NV4 = 4>
+__device__ __forceinline__ void warp_column_scan(const uint32_t *col, uint32_t H, uint32_t CW,
+                                                 uint32_t &piv, uint32_t &size, uint16_t *sup) {
+    constexpr int VN = 4 * NV4 > 8 ? 4 * NV4 : 8;
     const int lane = threadIdx.x & 31;
     uint32_t base = 0, pv = 0xffffffffu;
     // one batch: NV vectors of VW words per lane, word index of vector k, element e:
     // w = VW * (v0 + 32 k + lane) + e (increasing in k, then e, for a lane)
-    auto batch = [&](const uint32_t (&v)[16], uint32_t wbase, uint32_t stride_w, int nk, int vw) {
+    auto batch = [&](const uint32_t (&v)[VN], uint32_t wbase, uint32_t stride_w, int nk, int vw) {
         uint32_t c = 0, mine = 0xffffffffu;
 #pragma unroll
         for (int k = 0; k < nk; k++)
@@ -718,21 +791,21 @@ __device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ co
         base += __shfl_sync(FULL_MASK, xs, 31);
     };
     if ((CW & 3u) == 0 && ((uintptr_t)col & 15u) == 0) {
-        const uint4 *__restrict__ c4 = reinterpret_cast<const uint4 *>(col);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(col);
         const uint32_t n4 = CW >> 2;
-        for (uint32_t v0 = 0; v0 < n4; v0 += 128) {
-            uint32_t v[16];
+        for (uint32_t v0 = 0; v0 < n4; v0 += 32 * NV4) {
+            uint32_t v[VN];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < NV4; k++) {
                 const uint32_t j = v0 + 32 * k + lane;
                 const uint4 q = j < n4 ? c4[j] : make_uint4(0u, 0u, 0u, 0u);
                 v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
             }
-            batch(v, 4 * (v0 + lane), 128, 4, 4);
+            batch(v, 4 * (v0 + lane), 128, NV4, 4);
         }
     } else {
         for (uint32_t w0 = 0; w0 < CW; w0 += 256) {
-            uint32_t v[16];
+            uint32_t v[VN];
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 const uint32_t w = w0 + 32 * k + lane;
@@ -745,9 +818,20 @@ __device__ __forceinline__ void warp_column_scan(const uint32_t *__restrict__ co
     size = base;
 }
 
-constexpr int DET_WARPS = 8;
+constexpr int DET_WARPS = 4;
+// The general product as an out-of-line call for k_meas_det, whose list
+// path is kept at 56 registers (nine 4-warp CTAs per SM) by not inlining it.
+__device__ __noinline__ int det_outcome_warp_ool(const uint32_t *__restrict__ rm, uint32_t RS, uint32_t Hr,
+                                                 uint32_t H, const uint32_t *__restrict__ r,
+                                                 const uint32_t *__restrict__ colK, uint32_t q,
+                                                 uint32_t *__restrict__ scratch, int *err) {
+    return det_outcome_warp(rm, RS, Hr, H, r, colK, q, scratch, err);
+}
+// shared words per warp of k_meas_det: the 2H-word scratch of the general
+// product, at least SUPCAP 16-bit support entries
+__host__ __device__ constexpr uint32_t det_smem_words(uint32_t H) { return 2 * H > SUPCAP / 2 ? 2 * H : SUPCAP / 2; }
 
-__global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t layer) {
+__global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_t layer) {
     extern __shared__ uint32_t smem[];
     const uint32_t H = a.P.H, CW = a.P.CW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -769,12 +853,18 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
         }
     }
     const uint32_t *col = a.cols + t * a.cols_stride + (size_t)i * CW;
-    // pivot (first stabilizer row of the column), column size and support,
-    // cached for the random-measurement kernel
+    uint32_t *scratch = smem + (size_t)warp * det_smem_words(H);
+    uint16_t *lst = reinterpret_cast<uint16_t *>(scratch);
+    // pivot (first stabilizer row of the column), column size and support
+    // (into shared memory; copied out, for the random-measurement kernel, when
+    // the op is random)
     uint32_t pv, csize;
     const size_t ci = t * a.m_stride + i;
-    warp_column_scan(col, H, CW, pv, csize, a.msup + ci * SUPCAP);
+    warp_column_scan<5>(col, H, CW, pv, csize, lst);
+    __syncwarp();
     if (pv != 0xffffffffu) {
+        uint16_t *sup = a.msup + ci * SUPCAP;
+        for (uint32_t e = lane; e < min(csize, SUPCAP); e += 32) sup[e] = lst[e];
         if (lane == 0) {
             stat[i] = MS_RANDOM;
             atomicOr(&a.tflags[t], TF_RAND_LAYER);
@@ -785,17 +875,16 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_det(LArgs a, uint32_t l
         }
         return;
     }
-    if (a.stats) {
-        uint32_t k = 0;
-        for (uint32_t w = lane; w < H; w += 32) k += __popc(col[w]);
-        k = __reduce_add_sync(FULL_MASK, k);
-        if (lane == 0) {
-            count(a, DC_DET, 1);
-            count(a, DC_SUM_K, k);
-        }
+    // deterministic: the stabilizer half is empty, so csize = K, the number of
+    // set destabilizer bits, and lst holds their slots when K <= SUPCAP
+    if (a.stats && lane == 0) {
+        count(a, DC_DET, 1);
+        count(a, DC_SUM_K, csize);
     }
-    const int o = det_outcome_warp(a.rm + t * a.rm_stride, a.RS, a.Hr, H, a.r + (size_t)t * CW,
-                                   col, m.q, smem + (size_t)warp * 2 * H, a.err);
+    const uint32_t *rm = a.rm + t * a.rm_stride;
+    const int o = (csize <= SUPCAP && (a.Hr & 1u) == 0 && ((uintptr_t)rm & 7u) == 0)
+                      ? det_outcome_list(rm, a.RS, a.Hr, H, a.r + (size_t)t * CW, lst, csize, m.q, a.err)
+                      : det_outcome_warp_ool(rm, a.RS, a.Hr, H, a.r + (size_t)t * CW, col, m.q, scratch, a.err);
     if (lane == 0) {
         stat[i] = MS_DONE;
         out[i] = (uint8_t)o;
@@ -840,8 +929,8 @@ constexpr int RSW = 5;
 __device__ __forceinline__ void rowsum_warp(uint32_t *rm, uint32_t RS, uint32_t Hr, uint32_t H,
                                             uint32_t *r, uint32_t s, uint32_t p, int *err) {
     const int lane = threadIdx.x & 31;
-    const uint32_t *__restrict__ rp = rm + (size_t)p * RS;
-    uint32_t *__restrict__ rs = rm + (size_t)s * RS;
+    const uint32_t *rp = rm + (size_t)p * RS;
+    uint32_t *rs = rm + (size_t)s * RS;
     const uint32_t rwords = lane == 0 ? ((r[s >> 5] >> (s & 31)) & 1u) | (((r[p >> 5] >> (p & 31)) & 1u) << 1) : 0u;
     int acc = 0;
     for (uint32_t c0 = 0; c0 < H; c0 += 32 * RSW) {
@@ -882,8 +971,8 @@ __device__ __forceinline__ void rowsum_warp_sparse(uint32_t *rm, uint32_t RS, ui
                                                    uint32_t s, uint32_t p, const uint16_t *wl,
                                                    uint32_t nwl, int *err) {
     const int lane = threadIdx.x & 31;
-    const uint32_t *__restrict__ rp = rm + (size_t)p * RS;
-    uint32_t *__restrict__ rs = rm + (size_t)s * RS;
+    const uint32_t *rp = rm + (size_t)p * RS;
+    uint32_t *rs = rm + (size_t)s * RS;
     const uint32_t rwords = lane == 0 ? ((r[s >> 5] >> (s & 31)) & 1u) | (((r[p >> 5] >> (p & 31)) & 1u) << 1) : 0u;
     const uint32_t c0 = lane < nwl ? wl[lane] : 0u, c1 = lane + 32 < nwl ? wl[lane + 32] : 0u;
     const bool in0 = lane < nwl, in1 = lane + 32 < nwl;
@@ -914,15 +1003,19 @@ constexpr uint32_t HT = 4096;                 // row hash slots (> PAIRCAP: neve
 constexpr uint32_t PWS = 4;                   // pivot words staged in shared memory per wave op
 constexpr uint32_t CKEYS = 32 * PWS;          // sort keys of one pass of a multi-pivot row
 constexpr uint16_t NOPIV = 0xffffu;
-constexpr uint16_t HEMPTY = 0xffffu;
+constexpr uint32_t HEMPTY = 0xffffffffu;
 constexpr uint32_t QMAP_SMEM_MAX = 16384;     // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
 static_assert(WCAP <= RAND_THREADS, "one thread per window op");
 static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pair list, power of two");
 
 // k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
+// The wave state's scalars, read and written by every CTA of the cluster.
+struct RandShared {
+    uint32_t np, nsel, npair, nent, firstrand, nrand, nstale, cut, serial, nmulti;
+};
 struct RandLayout {
-    uint32_t pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
+    uint32_t sh, pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
         wkeys, wlist, wacc, qmask, blocked, pmask, wq, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
@@ -934,6 +1027,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     RandLayout L;
     uint32_t o = 0;
     const bool item_smem = n <= QMAP_SMEM_MAX;
+    L.sh = rl_take(o, sizeof(RandShared));
     L.pend = rl_take(o, 2 * PCAP);
     L.wpiv = rl_take(o, 2 * WCAP);
     L.wbsz = rl_take(o, 2 * WCAP);
@@ -945,7 +1039,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.nxt = rl_take(o, 2 * PAIRCAP);
     L.hslot = rl_take(o, 2 * PAIRCAP);
     L.dlist = rl_take(o, 2 * PAIRCAP);
-    L.hkey = rl_take(o, 2 * HT);
+    L.hkey = rl_take(o, 4 * HT);
     L.htail = rl_take(o, 4 * HT);
     L.ents = rl_take(o, 4 * JCAP);
     L.spc = rl_take(o, 2 * WCAP * PWS);
@@ -1044,13 +1138,19 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
 // warp with full or word-listed rowsums, before the row copies.
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ uint32_t s_wt[32], s_wcnt[32];
-    __shared__ uint32_t s_np, s_tot, s_nsel, s_npair, s_nent, s_firstrand, s_nrand, s_any, s_nstale, s_cut;
-    __shared__ uint32_t s_serial, s_nmulti;
+    __shared__ uint32_t s_wt[32], s_tot, s_any;              // this CTA's block scans and first test
     __shared__ uint32_t xcnt[2 * RAND_WARPS];                // X-support counts of the 16-lane groups
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr, H4 = Hr >> 2;
-    const uint32_t t = blockIdx.x;
+    // one cluster of CTAs per tableau: rank 0 holds the wave state in its
+    // shared memory, and the threads of every rank work on it (through
+    // distributed shared memory); per-warp scratch stays in each CTA's own
+    const cg::cluster_group cl = cg::this_cluster();
+    const uint32_t crank = cl.block_rank(), ncl = cl.num_blocks();
+    const uint32_t t = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t gtid = crank * blockDim.x + threadIdx.x, GT = ncl * blockDim.x;   // cluster-wide
+    const uint32_t gwarp = crank * (uint32_t)nw + (uint32_t)warp, GW = ncl * (uint32_t)nw;
+    const bool lead = crank == 0;
     const Layer M = a.P.layers[layer];
     const RandLayout Lo = rand_layout(n, H);
     const uint32_t pcap = a.caps.pcap, wcap = min(a.caps.wcap, WCAP), paircap = a.caps.paircap,
@@ -1070,70 +1170,76 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint32_t *const rowver = a.rowver + (size_t)t * 32 * H;
     uint16_t *const pwl = a.pwl + (size_t)t * WCAP * PWCAP;
     const bool item_smem = n <= QMAP_SMEM_MAX;
-    uint16_t *const pend = (uint16_t *)(smraw + Lo.pend);    // pending item indices, circuit order
-    uint16_t *const wpiv = (uint16_t *)(smraw + Lo.wpiv);    // window: pivot (slot - 32H) or NOPIV
-    uint16_t *const wbsz = (uint16_t *)(smraw + Lo.wbsz);    // window: |x-column support| (saturated)
-    uint8_t *const wxn = smraw + Lo.wxn;                     // window: X-support length / XS_OVER
-    uint16_t *const sel = (uint16_t *)(smraw + Lo.sel);      // wave: window positions
-    uint8_t *const sr = smraw + Lo.sr;                       // wave: pivot sign before the wave
-    uint16_t *const pwn = (uint16_t *)(smraw + Lo.pwn);      // wave: nonzero words of the pivot row
-    uint32_t *const pairs = (uint32_t *)(smraw + Lo.pairs);  // row | wave index << 16
-    uint16_t *const nxt = (uint16_t *)(smraw + Lo.nxt);      // next pair of the same row (0xffff ends)
-    uint16_t *const hslot = (uint16_t *)(smraw + Lo.hslot);  // hash slot of the pair's row
-    uint16_t *const dlist = (uint16_t *)(smraw + Lo.dlist);  // rows (first pairs) applied by warps
-    uint16_t *const hkey = (uint16_t *)(smraw + Lo.hkey);    // hash: row
-    uint32_t *const htail = (uint32_t *)(smraw + Lo.htail);  // hash: first pair of the row's chain
-    uint32_t *const ents = (uint32_t *)(smraw + Lo.ents);    // item | wave index << 16 | bp << 31
-    uint16_t *const spc = (uint16_t *)(smraw + Lo.spc);      // wave pivots' nonzero words: index,
-    uint32_t *const spx = (uint32_t *)(smraw + Lo.spx);      //   x word
-    uint32_t *const spz = (uint32_t *)(smraw + Lo.spz);      //   z word
-    uint32_t *const wkeys = (uint32_t *)(smraw + Lo.wkeys) + warp * CKEYS;   // per warp: sort keys
-    uint16_t *const wlist = (uint16_t *)(smraw + Lo.wlist) + warp * 32;      //   chain pairs of a pass
-    int *const wacc = (int *)(smraw + Lo.wacc) + warp * 32;                 //   powers of i per pair
-    uint32_t *const qmask = (uint32_t *)(smraw + Lo.qmask);  // destabilizer partners of the wave's pivots
-    uint32_t *const blocked = (uint32_t *)(smraw + Lo.blocked);   // per item: an earlier window op conflicts
-    // per qubit: its layer item is still random or became deterministic during
-    // the layer (the items whose measured columns are kept current); scans of
-    // pivot and destabilizer rows test only these bits
-    uint32_t *const pmask = (uint32_t *)(smraw + Lo.pmask);
-    uint32_t *const wq = (uint32_t *)(smraw + Lo.wq);        // wave: measured qubit
-    uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
-    uint8_t *const stat = item_smem ? smraw + Lo.stat : gstat;
-    uint8_t *const mstale = item_smem ? smraw + Lo.stale : gmstale;
-    uint32_t *const r = (uint32_t *)(smraw + Lo.r);          // sign column, copied back at the end
-
+    // every rank's first test reads only global memory, so all ranks leave
+    // together or none does (no rank may leave while others can still reach
+    // rank 0's shared memory)
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
         if (gstat[i] == MS_RANDOM) s_any = 1;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lead && threadIdx.x == 0) {
         // k_destab_to_rm has made the destabilizer half current if it was not
         if (a.tflags[t] & TF_RAND_LAYER) a.tflags[t] = TF_DESTAB_FRESH;
     }
     if (!s_any) return;
-    for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) r[w] = gr[w];
-    for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = 0xffffu;
+    cl.sync();                         // every rank has started: rank 0's shared memory is reachable
+    unsigned char *const sm = lead ? smraw : static_cast<unsigned char *>(cl.map_shared_rank((void *)smraw, 0));
+    RandShared *const S = reinterpret_cast<RandShared *>(sm + Lo.sh);
+    uint16_t *const pend = (uint16_t *)(sm + Lo.pend);    // pending item indices, circuit order
+    uint16_t *const wpiv = (uint16_t *)(sm + Lo.wpiv);    // window: pivot (slot - 32H) or NOPIV
+    uint16_t *const wbsz = (uint16_t *)(sm + Lo.wbsz);    // window: |x-column support| (saturated)
+    uint8_t *const wxn = sm + Lo.wxn;                     // window: X-support length / XS_OVER
+    uint16_t *const sel = (uint16_t *)(sm + Lo.sel);      // wave: window positions
+    uint8_t *const sr = sm + Lo.sr;                       // wave: pivot sign before the wave
+    uint16_t *const pwn = (uint16_t *)(sm + Lo.pwn);      // wave: nonzero words of the pivot row
+    uint32_t *const pairs = (uint32_t *)(sm + Lo.pairs);  // row | wave index << 16
+    uint16_t *const nxt = (uint16_t *)(sm + Lo.nxt);      // next pair of the same row (0xffff ends)
+    uint16_t *const hslot = (uint16_t *)(sm + Lo.hslot);  // hash slot of the pair's row
+    uint16_t *const dlist = (uint16_t *)(sm + Lo.dlist);  // rows (first pairs) applied by warps
+    uint32_t *const hkey = (uint32_t *)(sm + Lo.hkey);    // hash: row
+    uint32_t *const htail = (uint32_t *)(sm + Lo.htail);  // hash: first pair of the row's chain
+    uint32_t *const ents = (uint32_t *)(sm + Lo.ents);    // item | wave index << 16 | bp << 31
+    uint16_t *const spc = (uint16_t *)(sm + Lo.spc);      // wave pivots' nonzero words: index,
+    uint32_t *const spx = (uint32_t *)(sm + Lo.spx);      //   x word
+    uint32_t *const spz = (uint32_t *)(sm + Lo.spz);      //   z word
+    uint32_t *const wkeys = (uint32_t *)(smraw + Lo.wkeys) + warp * CKEYS;   // per warp: sort keys
+    uint16_t *const wlist = (uint16_t *)(smraw + Lo.wlist) + warp * 32;      //   chain pairs of a pass
+    int *const wacc = (int *)(smraw + Lo.wacc) + warp * 32;                 //   powers of i per pair
+    uint32_t *const qmask = (uint32_t *)(sm + Lo.qmask);  // destabilizer partners of the wave's pivots
+    uint32_t *const blocked = (uint32_t *)(sm + Lo.blocked);   // per item: an earlier window op conflicts
+    // per qubit: its layer item is still random or became deterministic during
+    // the layer (the items whose measured columns are kept current); scans of
+    // pivot and destabilizer rows test only these bits
+    uint32_t *const pmask = (uint32_t *)(sm + Lo.pmask);
+    uint32_t *const wq = (uint32_t *)(sm + Lo.wq);        // wave: measured qubit
+    uint16_t *const qmap = item_smem ? (uint16_t *)(sm + Lo.qmap) : a.qmap + (size_t)t * n;
+    uint8_t *const stat = item_smem ? sm + Lo.stat : gstat;
+    uint8_t *const mstale = item_smem ? sm + Lo.stale : gmstale;
+    uint32_t *const r = (uint32_t *)(sm + Lo.r);          // sign column, copied back at the end
+
+    for (uint32_t w = gtid; w < CW; w += GT) r[w] = gr[w];
+    for (uint32_t q = gtid; q < n; q += GT) qmap[q] = 0xffffu;
     if (item_smem)
-        for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+        for (uint32_t i = gtid; i < M.count; i += GT) {
             stat[i] = gstat[i];
             mstale[i] = gmstale[i];
         }
     wacc[lane] = 0;
     if (lane < 2) xcnt[2 * warp + lane] = 0u;
-    for (uint32_t w = threadIdx.x; w < H; w += blockDim.x) pmask[w] = 0u;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+    for (uint32_t w = gtid; w < H; w += GT) pmask[w] = 0u;
+    cl.sync();
+    for (uint32_t i = gtid; i < M.count; i += GT) {
         const uint32_t q = a.P.mitems[M.first + i].q;
         qmap[q] = (uint16_t)i;
         if (gstat[i] == MS_RANDOM) atomicOr(&pmask[q >> 5], 1u << (q & 31));
     }
-    __syncthreads();
+    cl.sync();
 
     unsigned long long tlast = clock64();
 #define PHASE(k)                                                              \
     do {                                                                      \
-        if (threadIdx.x == 0 && a.stats) {                                    \
+        if (lead && threadIdx.x == 0 && a.stats) {                            \
             const unsigned long long now_ = clock64();                         \
             atomicAdd(&a.stats[DC_PHASE0 + (k)], now_ - tlast);               \
             tlast = now_;                                                     \
@@ -1143,11 +1249,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     unsigned long long tstep = 0;
 #define STEP_START()                                                          \
     do {                                                                      \
-        if (threadIdx.x == 0 && a.stats) tstep = clock64();                    \
+        if (lead && threadIdx.x == 0 && a.stats) tstep = clock64();            \
     } while (0)
 #define STEP(slot)                                                            \
     do {                                                                      \
-        if (threadIdx.x == 0 && a.stats) {                                    \
+        if (lead && threadIdx.x == 0 && a.stats) {                            \
             const unsigned long long now_ = clock64();                         \
             atomicAdd(&a.stats[(slot)], now_ - tstep);                        \
             tstep = now_;                                                     \
@@ -1166,13 +1272,13 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     const uint32_t glimit = min(2 * M.count + 3, a.caps.wave_limit);
     for (uint32_t guard = 0;; guard++) {
         if (guard >= glimit) {
-            if (threadIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+            if (gtid == 0) set_err(a.err, DERR_BOUNDS);
             break;
         }
         // ---- (1) ordered list of pending random measurements (first pcap):
         // from all items on the first wave or after an overflow, else by
-        // compacting the previous list (ops only ever leave it)
-        {
+        // compacting the previous list (ops only ever leave it); rank 0 alone
+        if (lead) {
             if (full_scan) {
                 uint32_t cnt = 0;
                 const uint32_t per = (M.count + blockDim.x - 1) / blockDim.x;
@@ -1187,7 +1293,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 full_scan = s_tot > pcap;
             } else {
                 // each thread owns at most PCAP / RAND_THREADS = 8 entries
-                const uint32_t np0 = s_np;
+                const uint32_t np0 = S->np;
                 const uint32_t per = (np0 + blockDim.x - 1) / blockDim.x;
                 const uint32_t k0 = threadIdx.x * per, k1 = min(np0, k0 + per);
                 uint16_t keep[8];
@@ -1212,15 +1318,15 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
             __syncthreads();
             if (threadIdx.x == 0) {
-                s_np = min(s_tot, pcap);
-                s_nsel = 0; s_npair = 0; s_nent = 0; s_nstale = 0;
-                s_firstrand = 0xffffffffu; s_nrand = 0; s_cut = 0xffffffffu;
-                s_serial = 0; s_nmulti = 0;
+                S->np = min(s_tot, pcap);
+                S->nsel = 0; S->npair = 0; S->nent = 0; S->nstale = 0;
+                S->firstrand = 0xffffffffu; S->nrand = 0; S->cut = 0xffffffffu;
+                S->serial = 0; S->nmulti = 0;
             }
-            __syncthreads();
         }
+        cl.sync();
         PHASE(0);
-        const uint32_t np = s_np;
+        const uint32_t np = S->np;
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
         const uint32_t wfirst = pend[0], wlast = pend[nlook - 1];
@@ -1228,25 +1334,25 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // column changed are listed in `pairs` (free until the work lists) for
         // a column rescan; ops whose pivot row changed (or is new) in `ents`
         // for an X-support rescan.
-        for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+        for (uint32_t k = gtid; k < nlook; k += GT) {
             const uint32_t i = pend[k];
             if (mstale[i]) {
-                pairs[atomicAdd(&s_nstale, 1u)] = k;
+                pairs[atomicAdd(&S->nstale, 1u)] = k;
                 continue;
             }
             const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
             wpiv[k] = (uint16_t)pv;
             wbsz[k] = (uint16_t)min(bs, 65535u);
             wxn[k] = (uint8_t)xn;
-            if (xn == XS_UNKNOWN || rowver[pv] != xv) ents[atomicAdd(&s_nent, 1u)] = k;
+            if (xn == XS_UNKNOWN || rowver[pv] != xv) ents[atomicAdd(&S->nent, 1u)] = k;
         }
-        for (uint32_t w = (wfirst >> 5) + threadIdx.x; w <= (wlast >> 5); w += blockDim.x) blocked[w] = 0u;
-        __syncthreads();
+        for (uint32_t w = (wfirst >> 5) + gtid; w <= (wlast >> 5); w += GT) blocked[w] = 0u;
+        cl.sync();
         PHASE(1);
         // column rescans, a warp each; an op with a new pivot joins the X-support list
         {
-            const uint32_t nst = s_nstale;
-            for (uint32_t x = (uint32_t)warp; x < nst; x += (uint32_t)nw) {
+            const uint32_t nst = S->nstale;
+            for (uint32_t x = gwarp; x < nst; x += GW) {
                 const uint32_t k = pairs[x], i = pend[k];
                 uint32_t pv, bs;
                 warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
@@ -1262,19 +1368,19 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         count(a, DC_DET_NOW, 1);
                     } else {
                         wpiv[k] = (uint16_t)pv;
-                        ents[atomicAdd(&s_nent, 1u)] = k;
+                        ents[atomicAdd(&S->nent, 1u)] = k;
                     }
                 }
             }
         }
-        __syncthreads();
+        cl.sync();
         PHASE(2);
         // X supports of the listed pivot rows over the layer's items: 16 lanes
         // per op (two ops per warp at once), 16-byte vectors of the x plane
         {
-            const uint32_t nxs = s_nent;
+            const uint32_t nxs = S->nent;
             const uint32_t sub = (uint32_t)lane >> 4, sl = (uint32_t)lane & 15u;
-            for (uint32_t x0 = 2 * (uint32_t)warp; x0 < nxs; x0 += 2 * (uint32_t)nw) {
+            for (uint32_t x0 = 2 * gwarp; x0 < nxs; x0 += 2 * GW) {
                 const uint32_t x = x0 + sub;
                 const bool act = x < nxs;
                 const uint32_t k = act ? ents[x] : 0u, i = act ? pend[k] : 0u;
@@ -1282,7 +1388,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 uint32_t ver = 0;
                 if (act) {
                     ver = rowver[pv];
-                    const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)(32 * H + pv) * RS);
+                    const uint4 *px4 = reinterpret_cast<const uint4 *>(rm + (size_t)(32 * H + pv) * RS);
                     for (uint32_t j0 = 0; j0 < H4; j0 += 16 * 6) {
                         uint4 v[6];
 #pragma unroll
@@ -1323,18 +1429,18 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 __syncwarp();
             }
         }
-        __syncthreads();
+        cl.sync();
         PHASE(3);
         // ---- (3) selection: for every conflicting pair of window ops the
         // later one is blocked; an op whose X support overflowed its list
         // blocks every later op (and itself, unless it is the first)
-        for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+        for (uint32_t k = gtid; k < nlook; k += GT) {
             if (wpiv[k] == NOPIV) continue;
-            atomicMin(&s_firstrand, k);
-            atomicAdd(&s_nrand, 1u);
+            atomicMin(&S->firstrand, k);
+            atomicAdd(&S->nrand, 1u);
             const uint32_t i = pend[k], xn = wxn[k];
             if (xn == XS_OVER) {
-                atomicMin(&s_cut, k);
+                atomicMin(&S->cut, k);
                 continue;
             }
             const uint16_t *xl = mxs + (size_t)i * XSCAP;
@@ -1345,19 +1451,19 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 atomicOr(&blocked[late >> 5], 1u << (late & 31));
             }
         }
-        __syncthreads();
-        if (s_nrand == 0) {             // block-uniform: the window became deterministic
+        cl.sync();
+        if (S->nrand == 0) {             // block-uniform: the window became deterministic
             PHASE(4);
             continue;
         }
-        if (threadIdx.x == 0) s_nent = 0;   // the X-support list is done with
+        if (gtid == 0) S->nent = 0;   // the X-support list is done with
         {
-            const uint32_t cut = s_cut, fr = s_firstrand;
-            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+            const uint32_t cut = S->cut, fr = S->firstrand;
+            for (uint32_t k = gtid; k < nlook; k += GT) {
                 const uint32_t i = pend[k];
                 if (wpiv[k] == NOPIV || ((blocked[i >> 5] >> (i & 31)) & 1u)) continue;
                 if (k > cut || (k == cut && k != fr)) continue;
-                const uint32_t idx = atomicAdd(&s_nsel, 1u);
+                const uint32_t idx = atomicAdd(&S->nsel, 1u);
                 if (idx < wcap) {
                     sel[idx] = (uint16_t)k;
                     stat[i] = MS_WAVE;
@@ -1365,11 +1471,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 }
             }
         }
-        __syncthreads();
+        cl.sync();
         PHASE(4);
         // ---- (4) work lists, one warp per wave op
-        const uint32_t nsel = min(s_nsel, wcap);
-        for (uint32_t x = (uint32_t)warp; x < nsel; x += (uint32_t)nw) {
+        const uint32_t nsel = min(S->nsel, wcap);
+        for (uint32_t x = gwarp; x < nsel; x += GW) {
             STEP_START();
             const uint32_t k = sel[x], i = pend[k];
             const uint32_t q = wpiv[k], p = 32 * H + q;
@@ -1383,9 +1489,9 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             // pending ops whose qubit has X or Y in row p or row q (their
             // measured columns change), and the nonzero words of row p: 16-byte
             // vectors of rows p (x, z) and q (x)
-            const uint4 *__restrict__ px4 = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
-            const uint4 *__restrict__ pz4 = px4 + H4;
-            const uint4 *__restrict__ qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
+            const uint4 *px4 = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
+            const uint4 *pz4 = px4 + H4;
+            const uint4 *qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
             uint32_t nzcnt = 0;
             for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
                 uint4 vx[2], vz[2], vq[2];
@@ -1400,7 +1506,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 // row q <- row p: no other op of the wave reads or writes row q
                 // (it is no rowsum target), and this lane stores only the
                 // elements it has just read
-                uint4 *__restrict__ rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+                uint4 *rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++) {
                     const uint32_t j = j0 + 32 * kk + lane;
@@ -1438,7 +1544,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                             if (lane >= o) ie += y;
                         }
                         uint32_t ebase = 0;
-                        if (lane == 31) ebase = atomicAdd(&s_nent, ie);
+                        if (lane == 31) ebase = atomicAdd(&S->nent, ie);
                         ebase = __shfl_sync(FULL_MASK, ebase, 31) + ie - ne;
 #pragma unroll
                         for (int e = 0; e < 4; e++) {
@@ -1483,7 +1589,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 // row q's sign is the pivot's (read by no other op of the wave)
                 if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
                 else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
-                if (nzcnt > PWS) s_serial = 1;
+                if (nzcnt > PWS) S->serial = 1;
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
             }
@@ -1497,8 +1603,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 uint32_t h = (row * 2654435761u) >> 20;       // HT = 4096 slots
                 uint32_t probe = 0;
                 for (; probe < HT; probe++) {
-                    const uint16_t old = atomicCAS(&hkey[h], HEMPTY, (uint16_t)row);
-                    if (old == HEMPTY || old == (uint16_t)row) break;
+                    const uint32_t old = atomicCAS(&hkey[h], HEMPTY, row);
+                    if (old == HEMPTY || old == row) break;
                     h = (h + 1) & (HT - 1);
                 }
                 if (probe == HT) {                   // cannot happen: HT > paircap
@@ -1521,7 +1627,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     const bool keep = e < nb && row != p && !((qmask[row >> 5] >> (row & 31)) & 1u);
                     const uint32_t bal = __ballot_sync(FULL_MASK, keep);
                     uint32_t base = 0;
-                    if (lane == 0 && bal) base = atomicAdd(&s_npair, (uint32_t)__popc(bal));
+                    if (lane == 0 && bal) base = atomicAdd(&S->npair, (uint32_t)__popc(bal));
                     base = __shfl_sync(FULL_MASK, base, 0);
                     if (keep) link_pair(base + __popc(bal & ((1u << lane) - 1u)), row);
                 }
@@ -1535,16 +1641,16 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         m &= m - 1;
                         const uint32_t row = 32 * w + b;
                         if (row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
-                        link_pair(atomicAdd(&s_npair, 1u), row);
+                        link_pair(atomicAdd(&S->npair, 1u), row);
                     }
                 }
             }
             STEP(DC_W0_LIST_PAIRS);
         }
-        __syncthreads();
+        cl.sync();
         PHASE(5);
-        const uint32_t npair = s_npair, nent = s_nent;
-        if (threadIdx.x == 0) {
+        const uint32_t npair = S->npair, nent = S->nent;
+        if (gtid == 0) {
             count(a, DC_WAVES, 1);
             count(a, DC_WAVE_OPS, nsel);
             count(a, DC_SUM_A, npair);
@@ -1552,13 +1658,13 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         }
         // serial: a dense pivot, or an overflowed list whose fallback reads
         // pivot rows from the tableau -- the row copies wait for them
-        const bool serial = s_serial || npair > paircap || nent > jcap;
+        const bool serial = S->serial || npair > paircap || nent > jcap;
         // pivot rows become +-Z_a (16-byte stores over the Hr-word rows; the
         // words past H are zero in every row), with the coin as sign, and the
         // outcome; row q already holds the old pivot row (work lists)
         auto row_copies = [&]() {
             const uint32_t per = 2 * H4, tot = nsel * per;
-            for (uint32_t tt = threadIdx.x; tt < tot; tt += blockDim.x) {
+            for (uint32_t tt = gtid; tt < tot; tt += GT) {
                 const uint32_t x = tt / per, c = tt % per, p = 32 * H + wpiv[sel[x]], mq = wq[x];
                 uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 if (c == H4 + (mq >> 7)) {
@@ -1568,7 +1674,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 reinterpret_cast<uint4 *>(rm + (size_t)p * RS)[c] = z;
             }
             // sign, outcome, record, pending mask: a thread per wave op
-            for (uint32_t x = threadIdx.x; x < nsel; x += blockDim.x) {
+            for (uint32_t x = gtid; x < nsel; x += GT) {
                 const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
                 const MItem m = a.P.mitems[M.first + i];
                 const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
@@ -1585,12 +1691,12 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         };
         // ---- (5a) rows with one pivot: a thread each; the others listed for warps
         if (npair <= paircap) {
-            for (uint32_t e = threadIdx.x; e < npair; e += blockDim.x) {
+            for (uint32_t e = gtid; e < npair; e += GT) {
                 const uint32_t f0 = chain_first(e);
                 const uint32_t x = pairs[e] >> 16, row = pairs[e] & 0xffffu;
                 const uint32_t nwd = pwn[x];
                 if (f0 != e || nxt[e] != 0xffffu || nwd > PWS) {
-                    if (f0 == e) dlist[atomicAdd(&s_nmulti, 1u)] = (uint16_t)e;
+                    if (f0 == e) dlist[atomicAdd(&S->nmulti, 1u)] = (uint16_t)e;
                     continue;
                 }
                 uint32_t *rs = rm + (size_t)row * RS;
@@ -1625,7 +1731,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             // warp each below
             {
                 const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
-                for (uint32_t e0 = 4 * (uint32_t)warp; e0 < nent; e0 += 4 * (uint32_t)nw) {
+                for (uint32_t e0 = 4 * gwarp; e0 < nent; e0 += 4 * GW) {
                     const uint32_t e = e0 + sub;
                     const bool act = e < nent;
                     const uint32_t j = act ? ents[e] & 0xffffu : 0u, x = act ? (ents[e] >> 16) & 0x7fffu : 0u;
@@ -1666,7 +1772,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     }
                 }
             }
-            for (uint32_t e = (uint32_t)warp; e < nent; e += (uint32_t)nw) {
+            for (uint32_t e = gwarp; e < nent; e += GW) {
                 const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
                 const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
                 if (!bp || wbsz[k] <= SUPCAP) continue;
@@ -1686,7 +1792,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         } else {
             // list overflow: every remaining op's column from the wave's columns
             // and the (not yet overwritten) pivot rows
-            for (uint32_t j = (uint32_t)warp; j < M.count; j += (uint32_t)nw) {
+            for (uint32_t j = gwarp; j < M.count; j += GW) {
                 if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
                 uint32_t *cj = cols + (size_t)j * CW;
                 const uint32_t qb = a.P.mitems[M.first + j].q;
@@ -1713,12 +1819,12 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         }
         if (!serial) row_copies();               // pivots are staged: copies may overwrite them
-        __syncthreads();
+        cl.sync();
         PHASE(6);
         // ---- (5c) rows with several pivots (or a dense one): a warp each
         if (npair <= paircap) {
-            const uint32_t nm = s_nmulti;
-            for (uint32_t d = (uint32_t)warp; d < nm; d += (uint32_t)nw) {
+            const uint32_t nm = S->nmulti;
+            for (uint32_t d = gwarp; d < nm; d += GW) {
                 const uint32_t e0 = dlist[d], row = pairs[e0] & 0xffffu;
                 bool dense = false;
                 for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++)
@@ -1840,7 +1946,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         } else {
             // pair-list overflow: one warp applies the pivots row by row, in wave order
-            for (uint32_t w = (uint32_t)warp; w < CW; w += (uint32_t)nw) {
+            for (uint32_t w = gwarp; w < CW; w += GW) {
                 for (uint32_t x = 0; x < nsel; x++) {
                     const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
                     uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
@@ -1857,22 +1963,25 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             }
         }
         if (serial) {
-            __syncthreads();
+            cl.sync();
             row_copies();
         }
-        __syncthreads();
+        cl.sync();
         PHASE(7);
     }
 #undef PHASE
 #undef STEP
 #undef STEP_START
-    __syncthreads();
-    for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
-    if (item_smem)
-        for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
-            gstat[i] = stat[i];
-            gmstale[i] = mstale[i];
-        }
+    // after this barrier no rank reaches rank 0's shared memory again
+    cl.sync();
+    if (lead) {
+        for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) gr[w] = r[w];
+        if (item_smem)
+            for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
+                gstat[i] = stat[i];
+                gmstale[i] = mstale[i];
+            }
+    }
 }
 
 // X after resets with outcome 1 (r ^= z_a) and RESET_ERROR's Z (r ^= x_a),
@@ -2158,17 +2267,84 @@ static uint64_t graph_nodes(const HostProg &p) {
     return k;
 }
 
+// CTAs per tableau (cluster size) of k_meas_rand.  One or a few tableaux
+// leave most SMs idle and are bound by one SM's issue rate and the latency of
+// each wave's phases, so each tableau's waves are spread over a cluster of up
+// to 8 SMs; a batch that fills the GPU with one CTA per tableau keeps one.
+// STAB_RAND_CLUSTER (1..8) overrides.  A size the GPU cannot co-schedule with
+// this shared-memory footprint (cudaOccupancyMaxActiveClusters == 0) is
+// halved until it can.
+static uint32_t rand_cluster_size(const LaunchCfg &lc, uint32_t count, size_t rsm) {
+    static const int env = [] {
+        const char *v = getenv("STAB_RAND_CLUSTER");
+        const int k = v ? atoi(v) : 0;
+        return k >= 1 && k <= 8 ? k : 0;
+    }();
+    uint32_t want = env ? (uint32_t)env
+                        : (uint32_t)std::max(1, std::min(8, lc.sm_count / (int)std::max<uint32_t>(1, count)));
+    static std::mutex mu;
+    static std::map<std::tuple<int, uint32_t, size_t>, bool> fits;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (; want > 1; want >>= 1) {
+        const auto key = std::make_tuple(dev, want, rsm);
+        auto it = fits.find(key);
+        if (it == fits.end()) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = want;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(want, 1, 1);
+            cfg.blockDim = dim3(RAND_THREADS, 1, 1);
+            cfg.dynamicSmemBytes = rsm;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            const cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, (const void *)k_meas_rand, &cfg);
+            if (e) cudaGetLastError();
+            it = fits.emplace(key, e == cudaSuccess && nc > 0).first;
+        }
+        if (it->second) break;
+    }
+    return want;
+}
+
+static cudaError_t launch_meas_rand(const LArgs &a, uint32_t layer, uint32_t count, uint32_t ncl, size_t rsm,
+                                    cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ncl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(ncl, count, 1);
+    cfg.blockDim = dim3(RAND_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = rsm;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_meas_rand, a, layer);
+}
+
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
-                        const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
+                        const LaunchCfg &lc0, cudaStream_t s, KernelProf *kp,
                         unsigned long long *d_stats, GraphSlot *gsl) {
     {
-        const int lim = (int)(lc.smem_optin - 1024);
+        const int lim = (int)(lc0.smem_optin - 1024);
         smem_attr_once(0, (const void *)k_gate_run, lim);
         smem_attr_once(1, (const void *)k_meas_det, lim);
         smem_attr_once(2, (const void *)k_meas_late, lim);
         smem_attr_once(3, (const void *)k_meas_rand, lim);
     }
+    LaunchCfg lc = lc0;
+    lc.rand_cluster = rand_cluster_size(lc0, b.count, rand_smem(b.n, b.H));
     // this call's inputs, read by the kernels from device memory (a pageable
     // source is staged before cudaMemcpyAsync returns)
     CallArgs ca{};
@@ -2185,9 +2361,10 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     HostProg &hp = const_cast<HostProg &>(p);
     LArgs ka = make_args(&p, b, &ms, d_err);
     ka.stats = nullptr;                  // (this path runs only with profiling off)
-    std::vector<unsigned char> key(sizeof(LArgs) + 1);
+    std::vector<unsigned char> key(sizeof(LArgs) + 2);
     memcpy(key.data(), &ka, sizeof ka);
     key[sizeof ka] = b.rm_valid ? 1 : 0;
+    key[sizeof ka + 1] = (unsigned char)lc.rand_cluster;
     if (!hp.gdone && cudaEventCreateWithFlags(&hp.gdone, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
@@ -2289,15 +2466,17 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
             });
             const uint32_t nb = (L.count + DET_WARPS - 1) / DET_WARPS;
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
-                k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);
+                k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * det_smem_words(b.H) * 4, s>>>(a, l);
             });
             const uint32_t fixed = 4u * (uint32_t)lc.sm_count;
             launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
                 const unsigned long long pairs = (unsigned long long)b.H * b.count;
                 k_destab_to_rm<<<(uint32_t)std::min<unsigned long long>(pairs, fixed), 256, 0, s>>>(a);
             });
+            cudaError_t er = cudaSuccess;
             launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
-                   [&] { k_meas_rand<<<b.count, RAND_THREADS, rsm, s>>>(a, l); });
+                   [&] { er = launch_meas_rand(a, l, b.count, lc.rand_cluster, rsm, s); });
+            if (er != cudaSuccess) return er;
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 const unsigned long long ctas = ((unsigned long long)L.count * b.count + DET_WARPS - 1) / DET_WARPS;
                 k_meas_late<<<(uint32_t)std::min<unsigned long long>(ctas, 2ull * fixed), DET_WARPS * 32,

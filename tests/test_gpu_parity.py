@@ -261,6 +261,30 @@ def test_wave_list_overflow_fallbacks_match_oracle():
         assert r.returncode == 0 and "ok" in r.stdout, (caps, r.stdout[-2000:], r.stderr[-4000:])
 
 
+def test_wave_cluster_sizes_match_oracle():
+    """The random-measurement kernel spreads each tableau's waves over a
+    cluster of CTAs (rank 0 holds the wave state in shared memory); every
+    cluster size gives the oracle's records and tableaux, also with shrunken
+    list capacities (the fallback loops run cluster-wide too)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import tests.test_gpu_parity as t\n"
+            "from paper_2507_03092_gb300 import binding as B\n"
+            "s = B.Simulator(0)\n"
+            "t._check_wave_cases(s)\n"
+            "s.close()\nprint('ok')\n")
+    for ncl, caps in (("1", None), ("2", None), ("3", None), ("8", None), ("4", "8,2,4,4,16"),
+                      ("8", "64,1,2,2,1")):
+        env = dict(os.environ, STAB_RAND_CLUSTER=ncl)
+        if caps:
+            env["STAB_WAVE_CAPS"] = caps
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and "ok" in r.stdout, (ncl, caps, r.stdout[-2000:], r.stderr[-4000:])
+
+
 _GUARD_CODE = """
 import numpy as np
 import oracle
