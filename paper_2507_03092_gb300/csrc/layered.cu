@@ -1107,7 +1107,8 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
         }
 }
 
-// The random measurements of one measurement layer of one tableau (one CTA),
+// The random measurements of one measurement layer of one tableau (one
+// cluster of CTAs),
 // in waves.  Sequential CHP applies them one by one in circuit order (Sec. 2.4:
 // pivot, rowsum of the pivot into every other row with an X or Y on the
 // measured qubit, destabilizer copy, +-Z_a with a random sign).  Two of them,
@@ -1136,6 +1137,13 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
 // Column updates and row copies touch other data and run in the same phase.
 // A chain holding a pivot with more than PWS nonzero words is applied by one
 // warp with full or word-listed rowsums, before the row copies.
+// Cluster: rank 0's shared memory holds the wave state (lists, hash, window);
+// every rank's warps take items of each phase (cluster-wide thread and warp
+// indices) through distributed shared memory, and phases end at cluster
+// barriers (release/acquire, so global and shared writes of one phase are
+// seen by every rank in the next).  The pending-list compaction runs on rank
+// 0 alone; per-warp scratch, the qubit -> item map and the pending-qubit mask
+// are each rank's own.
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t s_wt[32], s_tot, s_any;              // this CTA's block scans and first test
@@ -1208,32 +1216,40 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     int *const wacc = (int *)(smraw + Lo.wacc) + warp * 32;                 //   powers of i per pair
     uint32_t *const qmask = (uint32_t *)(sm + Lo.qmask);  // destabilizer partners of the wave's pivots
     uint32_t *const blocked = (uint32_t *)(sm + Lo.blocked);   // per item: an earlier window op conflicts
-    // per qubit: its layer item is still random or became deterministic during
-    // the layer (the items whose measured columns are kept current); scans of
-    // pivot and destabilizer rows test only these bits
-    uint32_t *const pmask = (uint32_t *)(sm + Lo.pmask);
+    // per qubit: its layer item is still random and in no wave yet, or became
+    // deterministic during the layer (the items whose measured columns are kept
+    // current); scans of pivot and destabilizer rows test only these bits.
+    // Each rank keeps its own copy; an op's bit is cleared on every rank when
+    // it joins a wave.
+    uint32_t *const pmask = (uint32_t *)(smraw + Lo.pmask);
     uint32_t *const wq = (uint32_t *)(sm + Lo.wq);        // wave: measured qubit
-    uint16_t *const qmap = item_smem ? (uint16_t *)(sm + Lo.qmap) : a.qmap + (size_t)t * n;
+    // qubit -> layer item (each rank's own copy when it fits shared memory)
+    uint16_t *const qmap = item_smem ? (uint16_t *)(smraw + Lo.qmap) : a.qmap + (size_t)t * n;
     uint8_t *const stat = item_smem ? sm + Lo.stat : gstat;
     uint8_t *const mstale = item_smem ? sm + Lo.stale : gmstale;
     uint32_t *const r = (uint32_t *)(sm + Lo.r);          // sign column, copied back at the end
 
     for (uint32_t w = gtid; w < CW; w += GT) r[w] = gr[w];
-    for (uint32_t q = gtid; q < n; q += GT) qmap[q] = 0xffffu;
-    if (item_smem)
+    if (item_smem) {
+        for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) qmap[q] = 0xffffu;
         for (uint32_t i = gtid; i < M.count; i += GT) {
             stat[i] = gstat[i];
             mstale[i] = gmstale[i];
         }
+    } else {
+        for (uint32_t q = gtid; q < n; q += GT) qmap[q] = 0xffffu;
+    }
     wacc[lane] = 0;
     if (lane < 2) xcnt[2 * warp + lane] = 0u;
-    for (uint32_t w = gtid; w < H; w += GT) pmask[w] = 0u;
+    for (uint32_t w = threadIdx.x; w < H; w += blockDim.x) pmask[w] = 0u;
     cl.sync();
-    for (uint32_t i = gtid; i < M.count; i += GT) {
+    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x) {
         const uint32_t q = a.P.mitems[M.first + i].q;
-        qmap[q] = (uint16_t)i;
+        if (item_smem) qmap[q] = (uint16_t)i;
         if (gstat[i] == MS_RANDOM) atomicOr(&pmask[q >> 5], 1u << (q & 31));
     }
+    if (!item_smem)
+        for (uint32_t i = gtid; i < M.count; i += GT) qmap[a.P.mitems[M.first + i].q] = (uint16_t)i;
     cl.sync();
 
     unsigned long long tlast = clock64();
@@ -1468,6 +1484,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     sel[idx] = (uint16_t)k;
                     stat[i] = MS_WAVE;
                     atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
+                    // the op leaves every rank's pending-qubit mask
+                    const uint32_t q = a.P.mitems[M.first + i].q;
+                    for (uint32_t c = 0; c < ncl; c++)
+                        atomicAnd(cl.map_shared_rank(pmask, c) + (q >> 5), ~(1u << (q & 31)));
                 }
             }
         }
@@ -1528,14 +1548,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         mine += (xw[e] | zw[e]) != 0u;
-                        uint32_t mm = (xw[e] | qw[e]) & pmk[e];
-                        while (mm) {
-                            const int b = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            const uint32_t u = 32 * (4 * j + e) + b;
-                            const uint32_t jj = u < n ? qmap[u] : 0xffffu;
-                            ne += jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE);
-                        }
+                        ne += __popc((xw[e] | qw[e]) & pmk[e]);
                     }
                     if (__any_sync(FULL_MASK, ne != 0)) {
                         uint32_t ie = ne;
@@ -1552,12 +1565,9 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                             while (mm) {
                                 const int b = __ffs(mm) - 1;
                                 mm &= mm - 1;
-                                const uint32_t u = 32 * (4 * j + e) + b;
-                                const uint32_t jj = u < n ? qmap[u] : 0xffffu;
-                                if (jj != 0xffffu && (stat[jj] == MS_RANDOM || stat[jj] == MS_DETLATE)) {
-                                    if (ebase < jcap) ents[ebase] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
-                                    ebase++;
-                                }
+                                const uint32_t jj = qmap[32 * (4 * j + e) + b];
+                                if (ebase < jcap) ents[ebase] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
+                                ebase++;
                             }
                         }
                     }
@@ -1682,7 +1692,6 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 if (coin) atomicOr(&r[p >> 5], 1u << (p & 31));
                 else atomicAnd(&r[p >> 5], ~(1u << (p & 31)));
                 rowver[q]++;
-                atomicAnd(&pmask[m.q >> 5], ~(1u << (m.q & 31)));
                 out[i] = (uint8_t)coin;
                 stat[i] = MS_DONE;
                 write_record(a, t, m.rec, coin);
