@@ -117,12 +117,14 @@ struct HostProg {
     // Layered-engine launch sequence replayed as a CUDA graph.  The graph is
     // valid for the kernel arguments and entry state in `gkey`; a different
     // key recaptures it and updates the executable graph in place once its
-    // last launch has finished (event `gdone`).
+    // last launch has finished (event `gdone`); a different wave-kernel cluster
+    // size instantiates it anew instead (a launch attribute, not updated).
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t gdone = nullptr;
     std::vector<unsigned char> gkey;
     unsigned long long glaunches = 0;   // kernel launches in the graph
     bool grm_after = false;             // batch's row-packed copy valid after the run
+    uint32_t gcl = 0;                   // wave-kernel cluster size the executable graph was built with
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
     void *dmem = nullptr;       // device copy of the arrays

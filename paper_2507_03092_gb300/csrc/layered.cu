@@ -1154,6 +1154,13 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // distributed shared memory); per-warp scratch stays in each CTA's own
     const cg::cluster_group cl = cg::this_cluster();
     const uint32_t crank = cl.block_rank(), ncl = cl.num_blocks();
+    // one cluster per tableau: a grid row of any other size would give a
+    // tableau two leaders (checked before any rank touches another's memory;
+    // every CTA sees the same sizes, so all leave together)
+    if (ncl != gridDim.x) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) set_err(a.err, DERR_BOUNDS);
+        return;
+    }
     const uint32_t t = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t gtid = crank * blockDim.x + threadIdx.x, GT = ncl * blockDim.x;   // cluster-wide
@@ -2408,6 +2415,10 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
         hp.grm_after = b.rm_valid;
         // the executable graph is updated only after its last launch finished
         e = cudaEventSynchronize(hp.gdone);
+        if (!e && hp.gexec && hp.gcl != lc.rand_cluster) {
+            cudaGraphExecDestroy(hp.gexec);
+            hp.gexec = nullptr;
+        }
         if (!e && hp.gexec) {
             cudaGraphExecUpdateResultInfo info{};
             if (cudaGraphExecUpdate(hp.gexec, g, &info) != cudaSuccess) {
@@ -2416,7 +2427,10 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                 hp.gexec = nullptr;
             }
         }
-        if (!e && !hp.gexec) e = cudaGraphInstantiate(&hp.gexec, g, 0);
+        if (!e && !hp.gexec) {
+            e = cudaGraphInstantiate(&hp.gexec, g, 0);
+            if (!e) hp.gcl = lc.rand_cluster;
+        }
         cudaGraphDestroy(g);
         hp.gkey = e ? std::vector<unsigned char>() : key;
         if (!e) e = cudaGraphLaunch(hp.gexec, gsl->gs);

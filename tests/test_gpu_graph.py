@@ -109,3 +109,18 @@ def test_long_program_runs_without_one_graph():
             assert np.array_equal(got, want)
     finally:
         s.close()
+
+
+def test_graph_replay_across_wave_cluster_sizes(sim):
+    """The wave kernel's cluster size (CTAs per tableau) follows the batch
+    size: 8 for a few tableaux, fewer for larger batches, 1 from 77 on.  It
+    is a launch attribute of the captured graph, so one circuit sampled with
+    batch sizes that change it must still give the oracle's records each
+    time (the executable graph is instantiated anew, not updated in place)."""
+    circ = C.surface_code_memory(5, p=5e-3)
+    cid = sim.compile(circ)
+    for shots in (1, 20, 3, 40, 1, 77, 2, 20):
+        coins, noise = S.streams_for(circ, 100 + shots, range(shots))
+        got = _run(sim, cid, circ, coins, noise, profiled=False)
+        want, _ = oracle.sample(circ, coins, noise)
+        assert np.array_equal(got, want), shots
