@@ -133,17 +133,22 @@ __device__ __forceinline__ void set_err(int *err, int code) {
 }
 
 // 32x32 bit transpose across a warp: lane i holds row i (bit j = column j);
-// on return lane j holds column j (bit i = row i's bit j).
+// on return lane j holds column j (bit i = row i's bit j).  Stage s swaps the
+// off-diagonal s x s blocks between lanes i and i ^ s: each lane keeps its
+// half (mask m, or ~m in the upper lane of the pair) and sends the other half
+// already moved into its partner's bit positions (a rotation by s, right in
+// the lower lane and left in the upper one, masked), so a stage is a funnel
+// shift, an AND, a shuffle and one three-input logic op.
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v) {
     const int lane = threadIdx.x & 31;
     const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
     for (int k = 0; k < 5; k++) {
         const int s = 16 >> k;
-        const uint32_t m = masks[k];
-        uint32_t o = __shfl_xor_sync(FULL_MASK, v, s);
-        if (lane & s) v = (v & ~m) | ((o >> s) & m);
-        else v = (v & m) | ((o & m) << s);
+        const bool low = (lane & s) == 0;
+        const uint32_t keep = low ? masks[k] : ~masks[k];
+        const uint32_t send = __funnelshift_r(v, v, low ? s : 32 - s) & keep;
+        v = (v & keep) | __shfl_xor_sync(FULL_MASK, send, s);
     }
     return v;
 }
