@@ -124,3 +124,24 @@ def test_graph_replay_across_wave_cluster_sizes(sim):
         got = _run(sim, cid, circ, coins, noise, profiled=False)
         want, _ = oracle.sample(circ, coins, noise)
         assert np.array_equal(got, want), shots
+
+
+def test_graph_replay_many_measurement_layers(sim):
+    """A one-tableau program of 21 measurement layers (a d = 5 memory circuit
+    with 20 syndrome rounds), noiseless (later rounds have deterministic
+    outcomes only) and noisy: graph replay gives the records of plain
+    launches and of the oracle, with the same number of kernel launches."""
+    for p in (0.0, 5e-3):
+        circ = C.surface_code_memory(5, rounds=20, p=p)
+        cid = sim.compile(circ)
+        coins, noise = S.streams_for(circ, 17, [0])
+        B.stab_launch_count(sim.ctx, reset=True)
+        plain = _run(sim, cid, circ, coins, noise, profiled=True)
+        n_plain = B.stab_launch_count(sim.ctx, reset=True)
+        for _ in range(3):
+            graph = _run(sim, cid, circ, coins, noise, profiled=False)
+            n_graph = B.stab_launch_count(sim.ctx, reset=True)
+            assert np.array_equal(graph, plain), p
+            assert n_graph == n_plain, (n_plain, n_graph)
+        want, _ = oracle.sample(circ, coins, noise)
+        assert np.array_equal(plain, want), p
