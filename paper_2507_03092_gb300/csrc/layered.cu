@@ -1016,7 +1016,7 @@ struct RandShared {
 };
 struct RandLayout {
     uint32_t sh, pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
-        wkeys, wlist, wacc, qmask, blocked, pmask, wq, qmap, stat, stale, r, total;
+        hcnt, wkeys, wlist, wacc, qmask, blocked, pmask, wq, qmap, stat, stale, r, total;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
     const uint32_t at = o;
@@ -1041,6 +1041,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.dlist = rl_take(o, 2 * PAIRCAP);
     L.hkey = rl_take(o, 4 * HT);
     L.htail = rl_take(o, 4 * HT);
+    L.hcnt = rl_take(o, 4 * HT);
     L.ents = rl_take(o, 4 * JCAP);
     L.spc = rl_take(o, 2 * WCAP * PWS);
     L.spx = rl_take(o, 4 * WCAP * PWS);
@@ -1214,6 +1215,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint16_t *const dlist = (uint16_t *)(sm + Lo.dlist);  // rows (first pairs) applied by warps
     uint32_t *const hkey = (uint32_t *)(sm + Lo.hkey);    // hash: row
     uint32_t *const htail = (uint32_t *)(sm + Lo.htail);  // hash: first pair of the row's chain
+    uint32_t *const hcnt = (uint32_t *)(sm + Lo.hcnt);    // hash: pairs linked to the row
     uint32_t *const ents = (uint32_t *)(sm + Lo.ents);    // item | wave index << 16 | bp << 31
     uint16_t *const spc = (uint16_t *)(sm + Lo.spc);      // wave pivots' nonzero words: index,
     uint32_t *const spx = (uint32_t *)(sm + Lo.spx);      //   x word
@@ -1337,6 +1339,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             for (uint32_t h = threadIdx.x; h < HT; h += blockDim.x) {
                 hkey[h] = HEMPTY;
                 htail[h] = 0xffffffffu;
+                hcnt[h] = 0u;
             }
             for (uint32_t w = threadIdx.x; w < CW; w += blockDim.x) qmask[w] = 0u;
             __syncthreads();
@@ -1633,6 +1636,8 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 const uint32_t prev = atomicExch(&htail[h], f);
                 nxt[f] = prev == 0xffffffffu ? (uint16_t)0xffffu : (uint16_t)prev;
                 hslot[f] = (uint16_t)h;
+                // a row's second pair lists it for a warp (by hash slot)
+                if (atomicAdd(&hcnt[h], 1u) == 1u) dlist[atomicAdd(&S->nmulti, 1u)] = (uint16_t)h;
             };
             if (nb <= SUPCAP) {
                 // one append per warp and batch (a single shared counter would
@@ -1679,9 +1684,9 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // pivot rows become +-Z_a (16-byte stores over the Hr-word rows; the
         // words past H are zero in every row), with the coin as sign, and the
         // outcome; row q already holds the old pivot row (work lists)
-        auto row_copies = [&]() {
+        auto row_copies = [&](uint32_t st) {
             const uint32_t per = 2 * H4, tot = nsel * per;
-            for (uint32_t tt = gtid; tt < tot; tt += GT) {
+            for (uint32_t tt = st; tt < tot; tt += GT) {
                 const uint32_t x = tt / per, c = tt % per, p = 32 * H + wpiv[sel[x]], mq = wq[x];
                 uint4 z = make_uint4(0u, 0u, 0u, 0u);
                 if (c == H4 + (mq >> 7)) {
@@ -1691,7 +1696,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 reinterpret_cast<uint4 *>(rm + (size_t)p * RS)[c] = z;
             }
             // sign, outcome, record, pending mask: a thread per wave op
-            for (uint32_t x = gtid; x < nsel; x += GT) {
+            for (uint32_t x = st; x < nsel; x += GT) {
                 const uint32_t k = sel[x], i = pend[k], q = wpiv[k], p = 32 * H + q;
                 const MItem m = a.P.mitems[M.first + i];
                 const uint32_t coin = (m.flags & MF_RESET_ERR) ? (noise_word(a.call->st, t, m.nl + 1) & 1u)
@@ -1705,285 +1710,310 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 outcome_flips(a, t, layer, m, coin);
             }
         };
-        // ---- (5a) rows with one pivot: a thread each; the others listed for warps
-        if (npair <= paircap) {
-            for (uint32_t e = gtid; e < npair; e += GT) {
-                const uint32_t f0 = chain_first(e);
-                const uint32_t x = pairs[e] >> 16, row = pairs[e] & 0xffffu;
-                const uint32_t nwd = pwn[x];
-                if (f0 != e || nxt[e] != 0xffffu || nwd > PWS) {
-                    if (f0 == e) dlist[atomicAdd(&S->nmulti, 1u)] = (uint16_t)e;
-                    continue;
-                }
-                uint32_t *rs = rm + (size_t)row * RS;
-                uint32_t xs[PWS], zs[PWS];
-#pragma unroll
-                for (uint32_t w = 0; w < PWS; w++) {
-                    const bool o = w < nwd;
-                    const uint32_t c = o ? spc[x * PWS + w] : 0u;
-                    xs[w] = o ? rs[c] : 0u;
-                    zs[w] = o ? rs[Hr + c] : 0u;
-                }
-                int acc = 0;
-#pragma unroll
-                for (uint32_t w = 0; w < PWS; w++) {
-                    if (w >= nwd) continue;
-                    const uint32_t c = spc[x * PWS + w], px_ = spx[x * PWS + w], pz_ = spz[x * PWS + w];
-                    acc += phase_word(px_, pz_, xs[w], zs[w]);
-                    rs[c] = xs[w] ^ px_;
-                    rs[Hr + c] = zs[w] ^ pz_;
-                }
-                if (pair_flip(x, acc)) atomicXor(&r[row >> 5], 1u << (row & 31));
-                if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
-            }
-        }
-        // ---- (5b) measured columns of the remaining ops: x ^= x_{p,b} on the
-        // pivot's column rows (not the pivot, not the wave's destabilizer
-        // partners, which end as copies of their pivots); then row q's bit is
-        // x_{p,b} and row p's is 0.  Touches no bit of another wave op's p or q.
-        if (nent <= jcap) {
-            // 8 lanes per listed update whose wave op has a listed support (at
-            // most SUPCAP rows, 8 per lane loaded at once); larger columns by a
-            // warp each below
-            {
-                const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
-                for (uint32_t e0 = 4 * gwarp; e0 < nent; e0 += 4 * GW) {
-                    const uint32_t e = e0 + sub;
-                    const bool act = e < nent;
-                    const uint32_t j = act ? ents[e] & 0xffffu : 0u, x = act ? (ents[e] >> 16) & 0x7fffu : 0u;
-                    const uint32_t bp = act ? ents[e] >> 31 : 0u;
-                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                    if (!act || (bp && wbsz[k] > SUPCAP)) continue;
-                    uint32_t *cj = cols + (size_t)j * CW;
-                    if (bp) {
-                        const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
-                        const uint32_t nb = wbsz[k];
-                        uint32_t rows[SUPCAP / 8];
-#pragma unroll
-                        for (uint32_t f = 0; f < SUPCAP / 8; f++) {
-                            const uint32_t idx = sl + 8 * f;
-                            rows[f] = idx < nb ? sp[idx] : 0xffffffffu;
-                        }
-                        // this lane's rows: every 8th of the list, in increasing
-                        // word order, so rows of one word are often adjacent
-                        uint32_t cw = 0xffffffffu, cm = 0u;
-#pragma unroll
-                        for (uint32_t f = 0; f < SUPCAP / 8; f++) {
-                            const uint32_t row = rows[f];
-                            if (row == 0xffffffffu || row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
-                            if ((row >> 5) != cw) {
-                                if (cm) atomicXor(&cj[cw], cm);
-                                cw = row >> 5;
-                                cm = 0u;
-                            }
-                            cm |= 1u << (row & 31);
-                        }
-                        if (cm) atomicXor(&cj[cw], cm);
+        auto singles = [&](uint32_t st) {
+            // ---- (5a) rows with one pivot: a thread each; the others listed for warps
+            if (npair <= paircap) {
+                for (uint32_t e = st; e < npair; e += GT) {
+                    const uint32_t f0 = chain_first(e);
+                    const uint32_t x = pairs[e] >> 16, row = pairs[e] & 0xffffu;
+                    const uint32_t nwd = pwn[x];
+                    if (f0 != e || nxt[e] != 0xffffu) continue;     // a row of several pairs (listed when linked)
+                    if (nwd > PWS) {                                 // one dense pivot (only in serial waves)
+                        dlist[atomicAdd(&S->nmulti, 1u)] = (uint16_t)hslot[e];
+                        continue;
                     }
-                    if (sl == 0) {
-                        if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
-                        else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                    uint32_t *rs = rm + (size_t)row * RS;
+                    uint32_t xs[PWS], zs[PWS];
+    #pragma unroll
+                    for (uint32_t w = 0; w < PWS; w++) {
+                        const bool o = w < nwd;
+                        const uint32_t c = o ? spc[x * PWS + w] : 0u;
+                        xs[w] = o ? rs[c] : 0u;
+                        zs[w] = o ? rs[Hr + c] : 0u;
+                    }
+                    int acc = 0;
+    #pragma unroll
+                    for (uint32_t w = 0; w < PWS; w++) {
+                        if (w >= nwd) continue;
+                        const uint32_t c = spc[x * PWS + w], px_ = spx[x * PWS + w], pz_ = spz[x * PWS + w];
+                        acc += phase_word(px_, pz_, xs[w], zs[w]);
+                        rs[c] = xs[w] ^ px_;
+                        rs[Hr + c] = zs[w] ^ pz_;
+                    }
+                    if (pair_flip(x, acc)) atomicXor(&r[row >> 5], 1u << (row & 31));
+                    if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
+                }
+            }
+        };
+        auto col_updates = [&](uint32_t gw) {
+            // ---- (5b) measured columns of the remaining ops: x ^= x_{p,b} on the
+            // pivot's column rows (not the pivot, not the wave's destabilizer
+            // partners, which end as copies of their pivots); then row q's bit is
+            // x_{p,b} and row p's is 0.  Touches no bit of another wave op's p or q.
+            if (nent <= jcap) {
+                // 8 lanes per listed update whose wave op has a listed support (at
+                // most SUPCAP rows, 8 per lane loaded at once); larger columns by a
+                // warp each below
+                {
+                    const uint32_t sub = (uint32_t)lane >> 3, sl = (uint32_t)lane & 7u;
+                    for (uint32_t e0 = 4 * gw; e0 < nent; e0 += 4 * GW) {
+                        const uint32_t e = e0 + sub;
+                        const bool act = e < nent;
+                        const uint32_t j = act ? ents[e] & 0xffffu : 0u, x = act ? (ents[e] >> 16) & 0x7fffu : 0u;
+                        const uint32_t bp = act ? ents[e] >> 31 : 0u;
+                        const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                        if (!act || (bp && wbsz[k] > SUPCAP)) continue;
+                        uint32_t *cj = cols + (size_t)j * CW;
+                        if (bp) {
+                            const uint16_t *sp = msup + (size_t)pend[k] * SUPCAP;
+                            const uint32_t nb = wbsz[k];
+                            uint32_t rows[SUPCAP / 8];
+    #pragma unroll
+                            for (uint32_t f = 0; f < SUPCAP / 8; f++) {
+                                const uint32_t idx = sl + 8 * f;
+                                rows[f] = idx < nb ? sp[idx] : 0xffffffffu;
+                            }
+                            // this lane's rows: every 8th of the list, in increasing
+                            // word order, so rows of one word are often adjacent
+                            uint32_t cw = 0xffffffffu, cm = 0u;
+    #pragma unroll
+                            for (uint32_t f = 0; f < SUPCAP / 8; f++) {
+                                const uint32_t row = rows[f];
+                                if (row == 0xffffffffu || row == p || ((qmask[row >> 5] >> (row & 31)) & 1u)) continue;
+                                if ((row >> 5) != cw) {
+                                    if (cm) atomicXor(&cj[cw], cm);
+                                    cw = row >> 5;
+                                    cm = 0u;
+                                }
+                                cm |= 1u << (row & 31);
+                            }
+                            if (cm) atomicXor(&cj[cw], cm);
+                        }
+                        if (sl == 0) {
+                            if (bp) atomicOr(&cj[q >> 5], 1u << (q & 31));
+                            else atomicAnd(&cj[q >> 5], ~(1u << (q & 31)));
+                            atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
+                            mstale[j] = 1;
+                        }
+                    }
+                }
+                for (uint32_t e = gw; e < nent; e += GW) {
+                    const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
+                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                    if (!bp || wbsz[k] <= SUPCAP) continue;
+                    uint32_t *cj = cols + (size_t)j * CW;
+                    const uint32_t *col = cols + (size_t)pend[k] * CW;
+                    for (uint32_t w = lane; w < CW; w += 32) {
+                        uint32_t v = col[w] & ~qmask[w];
+                        if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                        if (v) atomicXor(&cj[w], v);
+                    }
+                    if (lane == 0) {
+                        atomicOr(&cj[q >> 5], 1u << (q & 31));
                         atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
                         mstale[j] = 1;
                     }
                 }
-            }
-            for (uint32_t e = gwarp; e < nent; e += GW) {
-                const uint32_t j = ents[e] & 0xffffu, x = (ents[e] >> 16) & 0x7fffu, bp = ents[e] >> 31;
-                const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                if (!bp || wbsz[k] <= SUPCAP) continue;
-                uint32_t *cj = cols + (size_t)j * CW;
-                const uint32_t *col = cols + (size_t)pend[k] * CW;
-                for (uint32_t w = lane; w < CW; w += 32) {
-                    uint32_t v = col[w] & ~qmask[w];
-                    if (w == (p >> 5)) v &= ~(1u << (p & 31));
-                    if (v) atomicXor(&cj[w], v);
-                }
-                if (lane == 0) {
-                    atomicOr(&cj[q >> 5], 1u << (q & 31));
-                    atomicAnd(&cj[p >> 5], ~(1u << (p & 31)));
-                    mstale[j] = 1;
-                }
-            }
-        } else {
-            // list overflow: every remaining op's column from the wave's columns
-            // and the (not yet overwritten) pivot rows
-            for (uint32_t j = gwarp; j < M.count; j += GW) {
-                if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
-                uint32_t *cj = cols + (size_t)j * CW;
-                const uint32_t qb = a.P.mitems[M.first + j].q;
-                for (uint32_t x = 0; x < nsel; x++) {
-                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                    const uint32_t bp = (rm[(size_t)p * RS + (qb >> 5)] >> (qb & 31)) & 1u;
-                    if (bp) {
-                        const uint32_t *col = cols + (size_t)pend[k] * CW;
-                        for (uint32_t w = lane; w < CW; w += 32) {
-                            uint32_t v = col[w] & ~qmask[w];
-                            if (w == (p >> 5)) v &= ~(1u << (p & 31));
-                            cj[w] ^= v;
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        const uint32_t bq = (cj[q >> 5] >> (q & 31)) & 1u;
-                        if (bp != bq) cj[q >> 5] ^= 1u << (q & 31);
-                        cj[p >> 5] &= ~(1u << (p & 31));
-                    }
-                    __syncwarp();
-                }
-                if (lane == 0) mstale[j] = 1;
-            }
-        }
-        if (!serial) row_copies();               // pivots are staged: copies may overwrite them
-        cl.sync();
-        PHASE(6);
-        // ---- (5c) rows with several pivots (or a dense one): a warp each
-        if (npair <= paircap) {
-            const uint32_t nm = S->nmulti;
-            for (uint32_t d = gwarp; d < nm; d += GW) {
-                const uint32_t e0 = dlist[d], row = pairs[e0] & 0xffffu;
-                bool dense = false;
-                for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++)
-                    dense |= pwn[pairs[f] >> 16] > PWS;
-                if (dense) {
-                    // pivots in chain order with warp rowsums (signs set inside;
-                    // pivot rows unchanged: the copies come after in this case)
-                    for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++) {
-                        const uint32_t x = pairs[f] >> 16, p = 32 * H + wpiv[sel[x]];
-                        if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
-                        else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
-                        __syncwarp();
-                    }
-                    if (lane == 0 && row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
-                    continue;
-                }
-                uint32_t *rs = rm + (size_t)row * RS;
-                uint32_t cur = e0, flips = 0;
-                STEP_START();
-                for (uint32_t pass = 0; cur < PAIRCAP && pass < PAIRCAP; pass++) {
-                    // up to 32 pairs of the chain, in chain order
-                    uint32_t cnt = 0;
-                    if (lane == 0) {
-                        while (cur < PAIRCAP && cnt < 32) {
-                            wlist[cnt++] = (uint16_t)cur;
-                            cur = nxt[cur];
-                        }
-                    }
-                    cur = __shfl_sync(FULL_MASK, cur, 0);
-                    cnt = __shfl_sync(FULL_MASK, cnt, 0);
-                    __syncwarp();
-                    // sort keys (word, chain position, word slot)
-                    uint32_t nk = 32;
-                    while (nk < PWS * cnt) nk <<= 1;
-                    const uint32_t lx = (uint32_t)lane < cnt ? pairs[wlist[lane]] >> 16 : 0u;
-                    const uint32_t lnw = (uint32_t)lane < cnt ? pwn[lx] : 0u;
-                    for (uint32_t idx = lane; idx < nk; idx += 32) wkeys[idx] = 0xffffffffu;
-                    __syncwarp();
-#pragma unroll
-                    for (uint32_t w = 0; w < PWS; w++)
-                        if (w < lnw) wkeys[PWS * lane + w] = ((uint32_t)spc[lx * PWS + w] << 7) | ((uint32_t)lane << 2) | w;
-                    __syncwarp();
-                    STEP(DC_W0_MULTI_WALK);
-                    warp_sort_keys(wkeys, nk);
-                    STEP(DC_W0_MULTI_SORT);
-                    // the sorted keys, 32 at a time: a segmented XOR prefix scan
-                    // over each word's keys (chain order) gives every pivot the
-                    // row word it meets, so all phases are computed at once;
-                    // a word's last key stores the word (carries run across rows)
-                    uint32_t carry_c = 0xffffffffu, carry_x = 0u, carry_z = 0u;
-                    uint32_t pre_x[CKEYS / 32], pre_z[CKEYS / 32];      // row words, loaded at once
-#pragma unroll
-                    for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
-                        const uint32_t key = 32 * rr < nk ? wkeys[32 * rr + lane] : 0xffffffffu;
-                        pre_x[rr] = key != 0xffffffffu ? rs[key >> 7] : 0u;
-                        pre_z[rr] = key != 0xffffffffu ? rs[Hr + (key >> 7)] : 0u;
-                    }
-#pragma unroll
-                    for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
-                        const uint32_t r0 = 32 * rr;
-                        if (r0 >= nk) break;
-                        const uint32_t key = wkeys[r0 + lane];
-                        const bool valid = key != 0xffffffffu;
-                        const uint32_t c = valid ? key >> 7 : 0xffffffffu;
-                        const uint32_t ml = (key >> 2) & 31u, ms = key & 3u;
-                        uint32_t px_ = 0u, pz_ = 0u;
-                        const uint32_t sx = pre_x[rr], sz = pre_z[rr];
-                        if (valid) {
-                            const uint32_t gx = pairs[wlist[ml]] >> 16;
-                            px_ = spx[gx * PWS + ms];
-                            pz_ = spz[gx * PWS + ms];
-                        }
-                        const uint32_t cprev = __shfl_up_sync(FULL_MASK, c, 1);
-                        const uint32_t cnext = __shfl_down_sync(FULL_MASK, c, 1);
-                        bool head = lane == 0 ? c != carry_c : c != cprev;
-                        uint32_t ix = px_, iz = pz_;
-                        bool hacc = head;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t yx = __shfl_up_sync(FULL_MASK, ix, o);
-                            const uint32_t yz = __shfl_up_sync(FULL_MASK, iz, o);
-                            const bool yh = __shfl_up_sync(FULL_MASK, hacc, o);
-                            if (lane >= o && !hacc) {
-                                ix ^= yx;
-                                iz ^= yz;
-                                hacc = yh;
+            } else {
+                // list overflow: every remaining op's column from the wave's columns
+                // and the (not yet overwritten) pivot rows
+                for (uint32_t j = gw; j < M.count; j += GW) {
+                    if (stat[j] != MS_RANDOM && stat[j] != MS_DETLATE) continue;
+                    uint32_t *cj = cols + (size_t)j * CW;
+                    const uint32_t qb = a.P.mitems[M.first + j].q;
+                    for (uint32_t x = 0; x < nsel; x++) {
+                        const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                        const uint32_t bp = (rm[(size_t)p * RS + (qb >> 5)] >> (qb & 31)) & 1u;
+                        if (bp) {
+                            const uint32_t *col = cols + (size_t)pend[k] * CW;
+                            for (uint32_t w = lane; w < CW; w += 32) {
+                                uint32_t v = col[w] & ~qmask[w];
+                                if (w == (p >> 5)) v &= ~(1u << (p & 31));
+                                cj[w] ^= v;
                             }
                         }
-                        if (!hacc) {               // segment continues from the previous row
-                            ix ^= carry_x;
-                            iz ^= carry_z;
+                        __syncwarp();
+                        if (lane == 0) {
+                            const uint32_t bq = (cj[q >> 5] >> (q & 31)) & 1u;
+                            if (bp != bq) cj[q >> 5] ^= 1u << (q & 31);
+                            cj[p >> 5] &= ~(1u << (p & 31));
                         }
-                        if (valid) {
-                            const uint32_t rx = sx ^ ix ^ px_, rz = sz ^ iz ^ pz_;   // row word before this pivot
-                            atomicAdd(&wacc[ml], phase_word(px_, pz_, rx, rz));
-                            const bool last = lane == 31 ? (r0 + 32 >= nk || (wkeys[r0 + 32] >> 7) != c) : cnext != c;
-                            if (last) {
-                                rs[c] = sx ^ ix;
-                                rs[Hr + c] = sz ^ iz;
+                        __syncwarp();
+                    }
+                    if (lane == 0) mstale[j] = 1;
+                }
+            }
+        };
+        auto multi_rows = [&]() {
+            // ---- (5c) rows with several pivots (or a dense one): a warp each
+            if (npair <= paircap) {
+                const uint32_t nm = S->nmulti;
+                for (uint32_t d = gwarp; d < nm; d += GW) {
+                    const uint32_t e0 = htail[dlist[d]], row = pairs[e0] & 0xffffu;
+                    bool dense = false;                  // (only serial waves hold dense pivots)
+                    if (serial)
+                        for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++)
+                            dense |= pwn[pairs[f] >> 16] > PWS;
+                    if (dense) {
+                        // pivots in chain order with warp rowsums (signs set inside;
+                        // pivot rows unchanged: the copies come after in this case)
+                        for (uint32_t f = e0, it_ = 0; f < PAIRCAP && it_ < PAIRCAP; f = nxt[f], it_++) {
+                            const uint32_t x = pairs[f] >> 16, p = 32 * H + wpiv[sel[x]];
+                            if (pwn[x] <= PWCAP) rowsum_warp_sparse(rm, RS, Hr, r, row, p, pwl + x * PWCAP, pwn[x], a.err);
+                            else rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                            __syncwarp();
+                        }
+                        if (lane == 0 && row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
+                        continue;
+                    }
+                    uint32_t *rs = rm + (size_t)row * RS;
+                    uint32_t cur = e0, flips = 0;
+                    STEP_START();
+                    for (uint32_t pass = 0; cur < PAIRCAP && pass < PAIRCAP; pass++) {
+                        // up to 32 pairs of the chain, in chain order
+                        uint32_t cnt = 0;
+                        if (lane == 0) {
+                            while (cur < PAIRCAP && cnt < 32) {
+                                wlist[cnt++] = (uint16_t)cur;
+                                cur = nxt[cur];
                             }
                         }
-                        carry_c = __shfl_sync(FULL_MASK, c, 31);
-                        carry_x = __shfl_sync(FULL_MASK, ix, 31);
-                        carry_z = __shfl_sync(FULL_MASK, iz, 31);
+                        cur = __shfl_sync(FULL_MASK, cur, 0);
+                        cnt = __shfl_sync(FULL_MASK, cnt, 0);
+                        __syncwarp();
+                        // sort keys (word, chain position, word slot)
+                        uint32_t nk = 32;
+                        while (nk < PWS * cnt) nk <<= 1;
+                        const uint32_t lx = (uint32_t)lane < cnt ? pairs[wlist[lane]] >> 16 : 0u;
+                        const uint32_t lnw = (uint32_t)lane < cnt ? pwn[lx] : 0u;
+                        for (uint32_t idx = lane; idx < nk; idx += 32) wkeys[idx] = 0xffffffffu;
+                        __syncwarp();
+    #pragma unroll
+                        for (uint32_t w = 0; w < PWS; w++)
+                            if (w < lnw) wkeys[PWS * lane + w] = ((uint32_t)spc[lx * PWS + w] << 7) | ((uint32_t)lane << 2) | w;
+                        __syncwarp();
+                        STEP(DC_W0_MULTI_WALK);
+                        warp_sort_keys(wkeys, nk);
+                        STEP(DC_W0_MULTI_SORT);
+                        // the sorted keys, 32 at a time: a segmented XOR prefix scan
+                        // over each word's keys (chain order) gives every pivot the
+                        // row word it meets, so all phases are computed at once;
+                        // a word's last key stores the word (carries run across rows)
+                        uint32_t carry_c = 0xffffffffu, carry_x = 0u, carry_z = 0u;
+                        uint32_t pre_x[CKEYS / 32], pre_z[CKEYS / 32];      // row words, loaded at once
+    #pragma unroll
+                        for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
+                            const uint32_t key = 32 * rr < nk ? wkeys[32 * rr + lane] : 0xffffffffu;
+                            pre_x[rr] = key != 0xffffffffu ? rs[key >> 7] : 0u;
+                            pre_z[rr] = key != 0xffffffffu ? rs[Hr + (key >> 7)] : 0u;
+                        }
+    #pragma unroll
+                        for (uint32_t rr = 0; rr < CKEYS / 32; rr++) {
+                            const uint32_t r0 = 32 * rr;
+                            if (r0 >= nk) break;
+                            const uint32_t key = wkeys[r0 + lane];
+                            const bool valid = key != 0xffffffffu;
+                            const uint32_t c = valid ? key >> 7 : 0xffffffffu;
+                            const uint32_t ml = (key >> 2) & 31u, ms = key & 3u;
+                            uint32_t px_ = 0u, pz_ = 0u;
+                            const uint32_t sx = pre_x[rr], sz = pre_z[rr];
+                            if (valid) {
+                                const uint32_t gx = pairs[wlist[ml]] >> 16;
+                                px_ = spx[gx * PWS + ms];
+                                pz_ = spz[gx * PWS + ms];
+                            }
+                            const uint32_t cprev = __shfl_up_sync(FULL_MASK, c, 1);
+                            const uint32_t cnext = __shfl_down_sync(FULL_MASK, c, 1);
+                            bool head = lane == 0 ? c != carry_c : c != cprev;
+                            uint32_t ix = px_, iz = pz_;
+                            bool hacc = head;
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const uint32_t yx = __shfl_up_sync(FULL_MASK, ix, o);
+                                const uint32_t yz = __shfl_up_sync(FULL_MASK, iz, o);
+                                const bool yh = __shfl_up_sync(FULL_MASK, hacc, o);
+                                if (lane >= o && !hacc) {
+                                    ix ^= yx;
+                                    iz ^= yz;
+                                    hacc = yh;
+                                }
+                            }
+                            if (!hacc) {               // segment continues from the previous row
+                                ix ^= carry_x;
+                                iz ^= carry_z;
+                            }
+                            if (valid) {
+                                const uint32_t rx = sx ^ ix ^ px_, rz = sz ^ iz ^ pz_;   // row word before this pivot
+                                atomicAdd(&wacc[ml], phase_word(px_, pz_, rx, rz));
+                                const bool last = lane == 31 ? (r0 + 32 >= nk || (wkeys[r0 + 32] >> 7) != c) : cnext != c;
+                                if (last) {
+                                    rs[c] = sx ^ ix;
+                                    rs[Hr + c] = sz ^ iz;
+                                }
+                            }
+                            carry_c = __shfl_sync(FULL_MASK, c, 31);
+                            carry_x = __shfl_sync(FULL_MASK, ix, 31);
+                            carry_z = __shfl_sync(FULL_MASK, iz, 31);
+                            __syncwarp();
+                        }
+                        __syncwarp();
+                        STEP(DC_W0_MULTI_ROWS);
+                        if ((uint32_t)lane < cnt) {
+                            flips ^= pair_flip(lx, wacc[lane]);
+                            wacc[lane] = 0;
+                        }
                         __syncwarp();
                     }
-                    __syncwarp();
-                    STEP(DC_W0_MULTI_ROWS);
-                    if ((uint32_t)lane < cnt) {
-                        flips ^= pair_flip(lx, wacc[lane]);
-                        wacc[lane] = 0;
+                    flips = __reduce_xor_sync(FULL_MASK, flips);
+                    if (lane == 0) {
+                        if (flips) atomicXor(&r[row >> 5], 1u << (row & 31));
+                        if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
                     }
-                    __syncwarp();
                 }
-                flips = __reduce_xor_sync(FULL_MASK, flips);
-                if (lane == 0) {
-                    if (flips) atomicXor(&r[row >> 5], 1u << (row & 31));
-                    if (row >= 32 * H) atomicAdd(&rowver[row - 32 * H], 1u);
-                }
-            }
-        } else {
-            // pair-list overflow: one warp applies the pivots row by row, in wave order
-            for (uint32_t w = gwarp; w < CW; w += GW) {
-                for (uint32_t x = 0; x < nsel; x++) {
-                    const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
-                    uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
-                    if (w == (p >> 5)) m &= ~(1u << (p & 31));
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        const uint32_t row = 32 * w + b;
-                        rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
-                        __syncwarp();
-                        if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+            } else {
+                // pair-list overflow: one warp applies the pivots row by row, in wave order
+                for (uint32_t w = gwarp; w < CW; w += GW) {
+                    for (uint32_t x = 0; x < nsel; x++) {
+                        const uint32_t k = sel[x], q = wpiv[k], p = 32 * H + q;
+                        uint32_t m = cols[(size_t)pend[k] * CW + w] & ~qmask[w];
+                        if (w == (p >> 5)) m &= ~(1u << (p & 31));
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t row = 32 * w + b;
+                            rowsum_warp(rm, RS, Hr, H, r, row, p, a.err);
+                            __syncwarp();
+                            if (lane == 0 && row >= 32 * H) rowver[row - 32 * H]++;
+                        }
                     }
                 }
             }
-        }
-        if (serial) {
+        };
+        // A wave without a dense pivot applies everything in one phase: rank
+        // 0's warps take the rows of several pivots (its shared memory holds
+        // their chains), the other ranks' threads the single-pivot rows, the
+        // column updates and the row copies (the multi-pivot rows read the
+        // staged pivot words, not the pivot rows the copies overwrite).  A
+        // serial wave applies the rows of several pivots, and the dense ones,
+        // after the single ones, then the row copies.
+        if (!serial) {
+            multi_rows();
+            singles(GT - 1 - gtid);
+            col_updates(GW - 1 - gwarp);
+            row_copies(GT - 1 - gtid);
             cl.sync();
-            row_copies();
+            PHASE(6);
+            PHASE(7);
+        } else {
+            singles(gtid);
+            col_updates(gwarp);
+            cl.sync();
+            PHASE(6);
+            multi_rows();
+            cl.sync();
+            row_copies(gtid);
+            cl.sync();
+            PHASE(7);
         }
-        cl.sync();
-        PHASE(7);
     }
 #undef PHASE
 #undef STEP
