@@ -1349,68 +1349,45 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 S->firstrand = 0xffffffffu; S->nrand = 0; S->cut = 0xffffffffu;
                 S->serial = 0; S->nmulti = 0;
             }
+            __syncthreads();
+            // ---- (2) window: cached pivots and X supports, on rank 0 (at
+            // most WCAP ops).  Ops whose measured column changed are listed in
+            // `pairs` (free until the work lists) for a column rescan; ops whose
+            // pivot row changed (or is new) in `ents` for an X-support rescan.
+            const uint32_t np0 = S->np;
+            if (np0) {
+                const uint32_t nl = min(np0, wmax);
+                for (uint32_t k = threadIdx.x; k < nl; k += blockDim.x) {
+                    const uint32_t i = pend[k];
+                    if (mstale[i]) {
+                        pairs[atomicAdd(&S->nstale, 1u)] = k;
+                        continue;
+                    }
+                    const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
+                    wpiv[k] = (uint16_t)pv;
+                    wbsz[k] = (uint16_t)min(bs, 65535u);
+                    wxn[k] = (uint8_t)xn;
+                    if (xn == XS_UNKNOWN || rowver[pv] != xv) ents[atomicAdd(&S->nent, 1u)] = k;
+                }
+                for (uint32_t w = (pend[0] >> 5) + threadIdx.x; w <= (pend[nl - 1] >> 5); w += blockDim.x) blocked[w] = 0u;
+            }
         }
         cl.sync();
         PHASE(0);
+        PHASE(1);
         const uint32_t np = S->np;
         if (np == 0) break;
         const uint32_t nlook = min(np, wmax);
         const uint32_t wfirst = pend[0], wlast = pend[nlook - 1];
-        // ---- (2) window: cached pivots and X supports.  Ops whose measured
-        // column changed are listed in `pairs` (free until the work lists) for
-        // a column rescan; ops whose pivot row changed (or is new) in `ents`
-        // for an X-support rescan.
-        for (uint32_t k = gtid; k < nlook; k += GT) {
-            const uint32_t i = pend[k];
-            if (mstale[i]) {
-                pairs[atomicAdd(&S->nstale, 1u)] = k;
-                continue;
-            }
-            const uint32_t pv = mpiv[i], bs = mbsz[i], xn = mxn[i], xv = mxver[i];
-            wpiv[k] = (uint16_t)pv;
-            wbsz[k] = (uint16_t)min(bs, 65535u);
-            wxn[k] = (uint8_t)xn;
-            if (xn == XS_UNKNOWN || rowver[pv] != xv) ents[atomicAdd(&S->nent, 1u)] = k;
-        }
-        for (uint32_t w = (wfirst >> 5) + gtid; w <= (wlast >> 5); w += GT) blocked[w] = 0u;
-        cl.sync();
-        PHASE(1);
-        // column rescans, a warp each; an op with a new pivot joins the X-support list
+        // Column rescans (a warp each) and X supports of the pivot rows over the
+        // layer's items (16 lanes per op, 16-byte vectors of the x plane), in
+        // one phase: a warp whose rescan finds a new pivot computes its X
+        // support next, with one half; ops listed by the window pass for an
+        // X-support rescan alone go two per warp.
         {
-            const uint32_t nst = S->nstale;
-            for (uint32_t x = gwarp; x < nst; x += GW) {
-                const uint32_t k = pairs[x], i = pend[k];
-                uint32_t pv, bs;
-                warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
-                if (lane == 0) {
-                    mpiv[i] = pv;
-                    mbsz[i] = bs;
-                    mstale[i] = 0;
-                    count(a, DC_PIV_RECOMP, 1);
-                    wbsz[k] = (uint16_t)min(bs, 65535u);
-                    if (pv == 0xffffffffu) {             // became deterministic
-                        wpiv[k] = NOPIV;
-                        stat[i] = MS_DETLATE;
-                        count(a, DC_DET_NOW, 1);
-                    } else {
-                        wpiv[k] = (uint16_t)pv;
-                        ents[atomicAdd(&S->nent, 1u)] = k;
-                    }
-                }
-            }
-        }
-        cl.sync();
-        PHASE(2);
-        // X supports of the listed pivot rows over the layer's items: 16 lanes
-        // per op (two ops per warp at once), 16-byte vectors of the x plane
-        {
-            const uint32_t nxs = S->nent;
+            const uint32_t nst = S->nstale, nx0 = S->nent;
             const uint32_t sub = (uint32_t)lane >> 4, sl = (uint32_t)lane & 15u;
-            for (uint32_t x0 = 2 * gwarp; x0 < nxs; x0 += 2 * GW) {
-                const uint32_t x = x0 + sub;
-                const bool act = x < nxs;
-                const uint32_t k = act ? ents[x] : 0u, i = act ? pend[k] : 0u;
-                const uint32_t pv = act ? wpiv[k] : 0u;
+            auto xs_one = [&](bool act, uint32_t k, uint32_t i, uint32_t pv) {
                 uint32_t ver = 0;
                 if (act) {
                     ver = rowver[pv];
@@ -1453,55 +1430,85 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     count(a, DC_XS_RECOMP, 1);
                 }
                 __syncwarp();
-            }
-        }
-        cl.sync();
-        PHASE(3);
-        // ---- (3) selection: for every conflicting pair of window ops the
-        // later one is blocked; an op whose X support overflowed its list
-        // blocks every later op (and itself, unless it is the first)
-        for (uint32_t k = gtid; k < nlook; k += GT) {
-            if (wpiv[k] == NOPIV) continue;
-            atomicMin(&S->firstrand, k);
-            atomicAdd(&S->nrand, 1u);
-            const uint32_t i = pend[k], xn = wxn[k];
-            if (xn == XS_OVER) {
-                atomicMin(&S->cut, k);
-                continue;
-            }
-            const uint16_t *xl = mxs + (size_t)i * XSCAP;
-            for (uint32_t e = 0; e < xn; e++) {
-                const uint32_t j = xl[e];
-                if (j == i || j < wfirst || j > wlast || stat[j] != MS_RANDOM) continue;
-                const uint32_t late = max(i, j);
-                atomicOr(&blocked[late >> 5], 1u << (late & 31));
-            }
-        }
-        cl.sync();
-        if (S->nrand == 0) {             // block-uniform: the window became deterministic
-            PHASE(4);
-            continue;
-        }
-        if (gtid == 0) S->nent = 0;   // the X-support list is done with
-        {
-            const uint32_t cut = S->cut, fr = S->firstrand;
-            for (uint32_t k = gtid; k < nlook; k += GT) {
-                const uint32_t i = pend[k];
-                if (wpiv[k] == NOPIV || ((blocked[i >> 5] >> (i & 31)) & 1u)) continue;
-                if (k > cut || (k == cut && k != fr)) continue;
-                const uint32_t idx = atomicAdd(&S->nsel, 1u);
-                if (idx < wcap) {
-                    sel[idx] = (uint16_t)k;
-                    stat[i] = MS_WAVE;
-                    atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
-                    // the op leaves every rank's pending-qubit mask
-                    const uint32_t q = a.P.mitems[M.first + i].q;
-                    for (uint32_t c = 0; c < ncl; c++)
-                        atomicAnd(cl.map_shared_rank(pmask, c) + (q >> 5), ~(1u << (q & 31)));
+            };
+            for (uint32_t it = gwarp; it < nst + (nx0 + 1) / 2; it += GW) {
+                if (it < nst) {
+                    const uint32_t k = pairs[it], i = pend[k];
+                    uint32_t pv, bs;
+                    warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
+                    if (lane == 0) {
+                        mpiv[i] = pv;
+                        mbsz[i] = bs;
+                        mstale[i] = 0;
+                        count(a, DC_PIV_RECOMP, 1);
+                        wbsz[k] = (uint16_t)min(bs, 65535u);
+                        if (pv == 0xffffffffu) {             // became deterministic
+                            wpiv[k] = NOPIV;
+                            stat[i] = MS_DETLATE;
+                            count(a, DC_DET_NOW, 1);
+                        } else {
+                            wpiv[k] = (uint16_t)pv;
+                        }
+                    }
+                    xs_one(sub == 0 && pv != 0xffffffffu, k, i, pv);
+                } else {
+                    const uint32_t x = 2 * (it - nst) + sub;
+                    const bool act = x < nx0;
+                    const uint32_t k = act ? ents[x] : 0u, i = act ? pend[k] : 0u;
+                    xs_one(act, k, i, act ? wpiv[k] : 0u);
                 }
             }
         }
         cl.sync();
+        PHASE(2);
+        PHASE(3);
+        // ---- (3) selection: for every conflicting pair of window ops the
+        // later one is blocked; an op whose X support overflowed its list
+        // blocks every later op (and itself, unless it is the first)
+        if (lead) {        // (rank 0: at most WCAP window ops)
+            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+                if (wpiv[k] == NOPIV) continue;
+                atomicMin(&S->firstrand, k);
+                atomicAdd(&S->nrand, 1u);
+                const uint32_t i = pend[k], xn = wxn[k];
+                if (xn == XS_OVER) {
+                    atomicMin(&S->cut, k);
+                    continue;
+                }
+                const uint16_t *xl = mxs + (size_t)i * XSCAP;
+                for (uint32_t e = 0; e < xn; e++) {
+                    const uint32_t j = xl[e];
+                    if (j == i || j < wfirst || j > wlast || stat[j] != MS_RANDOM) continue;
+                    const uint32_t late = max(i, j);
+                    atomicOr(&blocked[late >> 5], 1u << (late & 31));
+                }
+            }
+            __syncthreads();
+            if (S->nrand != 0) {          // (otherwise the window became deterministic)
+                if (threadIdx.x == 0) S->nent = 0;   // the X-support list is done with
+                const uint32_t cut = S->cut, fr = S->firstrand;
+                for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+                    const uint32_t i = pend[k];
+                    if (wpiv[k] == NOPIV || ((blocked[i >> 5] >> (i & 31)) & 1u)) continue;
+                    if (k > cut || (k == cut && k != fr)) continue;
+                    const uint32_t idx = atomicAdd(&S->nsel, 1u);
+                    if (idx < wcap) {
+                        sel[idx] = (uint16_t)k;
+                        stat[i] = MS_WAVE;
+                        atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
+                        // the op leaves every rank's pending-qubit mask
+                        const uint32_t q = a.P.mitems[M.first + i].q;
+                        for (uint32_t c = 0; c < ncl; c++)
+                            atomicAnd(cl.map_shared_rank(pmask, c) + (q >> 5), ~(1u << (q & 31)));
+                    }
+                }
+            }
+        }
+        cl.sync();
+        if (S->nrand == 0) {             // cluster-uniform: the window became deterministic
+            PHASE(4);
+            continue;
+        }
         PHASE(4);
         // ---- (4) work lists, one warp per wave op
         const uint32_t nsel = min(S->nsel, wcap);
