@@ -1034,7 +1034,7 @@ __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t 
     L.wxn = rl_take(o, WCAP);
     L.sel = rl_take(o, 2 * WCAP);
     L.sr = rl_take(o, WCAP);
-    L.pwn = rl_take(o, 2 * WCAP);
+    L.pwn = rl_take(o, 4 * WCAP);
     L.pairs = rl_take(o, 4 * PAIRCAP);
     L.nxt = rl_take(o, 2 * PAIRCAP);
     L.hslot = rl_take(o, 2 * PAIRCAP);
@@ -1208,7 +1208,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint8_t *const wxn = sm + Lo.wxn;                     // window: X-support length / XS_OVER
     uint16_t *const sel = (uint16_t *)(sm + Lo.sel);      // wave: window positions
     uint8_t *const sr = sm + Lo.sr;                       // wave: pivot sign before the wave
-    uint16_t *const pwn = (uint16_t *)(sm + Lo.pwn);      // wave: nonzero words of the pivot row
+    uint32_t *const pwn = (uint32_t *)(sm + Lo.pwn);      // wave: nonzero words of the pivot row
     uint32_t *const pairs = (uint32_t *)(sm + Lo.pairs);  // row | wave index << 16
     uint16_t *const nxt = (uint16_t *)(sm + Lo.nxt);      // next pair of the same row (0xffff ends)
     uint16_t *const hslot = (uint16_t *)(sm + Lo.hslot);  // hash slot of the pair's row
@@ -1494,6 +1494,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                     const uint32_t idx = atomicAdd(&S->nsel, 1u);
                     if (idx < wcap) {
                         sel[idx] = (uint16_t)k;
+                        pwn[idx] = 0u;
                         stat[i] = MS_WAVE;
                         atomicOr(&qmask[wpiv[k] >> 5], 1u << (wpiv[k] & 31));
                         // the op leaves every rank's pending-qubit mask
@@ -1510,9 +1511,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             continue;
         }
         PHASE(4);
-        // ---- (4) work lists, one warp per wave op
+        // ---- (4) work lists: a wave op's rows are split among W warps (32
+        // 16-byte vectors of each row per warp and block); the op's first warp
+        // also links its rowsum pairs
         const uint32_t nsel = min(S->nsel, wcap);
-        for (uint32_t x = gwarp; x < nsel; x += GW) {
+        const uint32_t W = max(1u, min(8u, (H4 + 31) / 32));
+        for (uint32_t tk = gwarp; tk < nsel * W; tk += GW) {
+            const uint32_t x = tk / W, part = tk - x * W;
+            const bool first = part == 0;
             STEP_START();
             const uint32_t k = sel[x], i = pend[k];
             const uint32_t q = wpiv[k], p = 32 * H + q;
@@ -1520,80 +1526,76 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             // first: its support list (two entries per lane) and its qubit
             const uint32_t nb = wbsz[k];
             const uint16_t *sp = msup + (size_t)i * SUPCAP;
-            const uint32_t sup0 = nb <= SUPCAP && (uint32_t)lane < nb ? sp[lane] : 0u;
-            const uint32_t sup1 = nb <= SUPCAP && (uint32_t)lane + 32 < nb ? sp[lane + 32] : 0u;
-            const uint32_t mq = lane == 0 ? a.P.mitems[M.first + i].q : 0u;
+            const uint32_t sup0 = first && nb <= SUPCAP && (uint32_t)lane < nb ? sp[lane] : 0u;
+            const uint32_t sup1 = first && nb <= SUPCAP && (uint32_t)lane + 32 < nb ? sp[lane + 32] : 0u;
+            const uint32_t mq = first && lane == 0 ? a.P.mitems[M.first + i].q : 0u;
             // pending ops whose qubit has X or Y in row p or row q (their
             // measured columns change), and the nonzero words of row p: 16-byte
             // vectors of rows p (x, z) and q (x)
             const uint4 *px4 = reinterpret_cast<const uint4 *>(rm + (size_t)p * RS);
             const uint4 *pz4 = px4 + H4;
             const uint4 *qx4 = reinterpret_cast<const uint4 *>(rm + (size_t)q * RS);
-            uint32_t nzcnt = 0;
-            for (uint32_t j0 = 0; j0 < H4; j0 += 64) {
-                uint4 vx[2], vz[2], vq[2];
-#pragma unroll
-                for (int kk = 0; kk < 2; kk++) {
-                    const uint32_t j = j0 + 32 * kk + lane;
-                    const bool in = j < H4;
-                    vx[kk] = in ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
-                    vz[kk] = in ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
-                    vq[kk] = in ? qx4[j] : make_uint4(0u, 0u, 0u, 0u);
-                }
+            uint4 *rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
+            for (uint32_t j0 = 32 * part; j0 < H4; j0 += 32 * W) {
+                const uint32_t j = j0 + lane;
+                const bool in = j < H4;
+                const uint4 vx = in ? px4[j] : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 vz = in ? pz4[j] : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 vq = in ? qx4[j] : make_uint4(0u, 0u, 0u, 0u);
                 // row q <- row p: no other op of the wave reads or writes row q
-                // (it is no rowsum target), and this lane stores only the
-                // elements it has just read
-                uint4 *rq4 = reinterpret_cast<uint4 *>(rm + (size_t)q * RS);
-#pragma unroll
-                for (int kk = 0; kk < 2; kk++) {
-                    const uint32_t j = j0 + 32 * kk + lane;
-                    if (j < H4) {
-                        rq4[j] = vx[kk];
-                        rq4[H4 + j] = vz[kk];
-                    }
+                // (it is no rowsum target), and each lane of each part stores
+                // only the elements it has just read
+                if (in) {
+                    rq4[j] = vx;
+                    rq4[H4 + j] = vz;
                 }
+                const uint32_t xw[4] = {vx.x, vx.y, vx.z, vx.w};
+                const uint32_t zw[4] = {vz.x, vz.y, vz.z, vz.w};
+                const uint32_t qw[4] = {vq.x, vq.y, vq.z, vq.w};
+                uint32_t pmk[4];
 #pragma unroll
-                for (int kk = 0; kk < 2; kk++) {
-                    const uint32_t j = j0 + 32 * kk + lane;
-                    const uint32_t xw[4] = {vx[kk].x, vx[kk].y, vx[kk].z, vx[kk].w};
-                    const uint32_t zw[4] = {vz[kk].x, vz[kk].y, vz[kk].z, vz[kk].w};
-                    const uint32_t qw[4] = {vq[kk].x, vq[kk].y, vq[kk].z, vq[kk].w};
-                    uint32_t pmk[4];
+                for (int e = 0; e < 4; e++) pmk[e] = 4 * j + e < H ? pmask[4 * j + e] : 0u;
+                uint32_t mine = 0, ne = 0;
 #pragma unroll
-                    for (int e = 0; e < 4; e++) pmk[e] = 4 * j + e < H ? pmask[4 * j + e] : 0u;
-                    uint32_t mine = 0, ne = 0;
+                for (int e = 0; e < 4; e++) {
+                    mine += (xw[e] | zw[e]) != 0u;
+                    ne += __popc((xw[e] | qw[e]) & pmk[e]);
+                }
+                if (__any_sync(FULL_MASK, ne != 0)) {
+                    uint32_t ie = ne;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL_MASK, ie, o);
+                        if (lane >= o) ie += y;
+                    }
+                    uint32_t ebase = 0;
+                    if (lane == 31) ebase = atomicAdd(&S->nent, ie);
+                    ebase = __shfl_sync(FULL_MASK, ebase, 31) + ie - ne;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        mine += (xw[e] | zw[e]) != 0u;
-                        ne += __popc((xw[e] | qw[e]) & pmk[e]);
-                    }
-                    if (__any_sync(FULL_MASK, ne != 0)) {
-                        uint32_t ie = ne;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t y = __shfl_up_sync(FULL_MASK, ie, o);
-                            if (lane >= o) ie += y;
-                        }
-                        uint32_t ebase = 0;
-                        if (lane == 31) ebase = atomicAdd(&S->nent, ie);
-                        ebase = __shfl_sync(FULL_MASK, ebase, 31) + ie - ne;
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            uint32_t mm = ne ? ((xw[e] | qw[e]) & pmk[e]) : 0u;
-                            while (mm) {
-                                const int b = __ffs(mm) - 1;
-                                mm &= mm - 1;
-                                const uint32_t jj = qmap[32 * (4 * j + e) + b];
-                                if (ebase < jcap) ents[ebase] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
-                                ebase++;
-                            }
+                        uint32_t mm = ne ? ((xw[e] | qw[e]) & pmk[e]) : 0u;
+                        while (mm) {
+                            const int b = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            const uint32_t jj = qmap[32 * (4 * j + e) + b];
+                            if (ebase < jcap) ents[ebase] = jj | (x << 16) | (((xw[e] >> b) & 1u) << 31);
+                            ebase++;
                         }
                     }
+                }
+                // nonzero words of row p: placed after those the op's other
+                // warps have counted (the list's order does not matter)
+                if (__any_sync(FULL_MASK, mine != 0)) {
                     uint32_t incl = mine;
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
                         if (lane >= o) incl += y;
                     }
-                    uint32_t pos = nzcnt + incl - mine;
+                    uint32_t base = 0;
+                    if (lane == 31) {
+                        base = atomicAdd(&pwn[x], incl);
+                        if (base + incl > PWS) S->serial = 1;
+                    }
+                    uint32_t pos = __shfl_sync(FULL_MASK, base, 31) + incl - mine;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         if ((xw[e] | zw[e]) == 0u) continue;
@@ -1606,21 +1608,19 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                         }
                         pos++;
                     }
-                    nzcnt += __shfl_sync(FULL_MASK, incl, 31);
                 }
             }
-            if (lane == 0) {
-                pwn[x] = (uint16_t)min(nzcnt, 0xffffu);
+            if (first && lane == 0) {
                 sr[x] = (uint8_t)rbit(r, p);
                 wq[x] = mq;
                 // row q's sign is the pivot's (read by no other op of the wave)
                 if (sr[x]) atomicOr(&r[q >> 5], 1u << (q & 31));
                 else atomicAnd(&r[q >> 5], ~(1u << (q & 31)));
-                if (nzcnt > PWS) S->serial = 1;
                 dirty[p >> 5] = 1;
                 dirty[q >> 5] = 1;
             }
             STEP(DC_W0_LIST_SCAN);
+            if (!first) continue;       // (the op's rowsum pairs: its first warp)
             // rowsum pairs: rows of the measured column except the pivot and
             // the wave's destabilizer partners, linked per row
             // link pair f (row, this wave op) into its row's chain
