@@ -1513,11 +1513,14 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         PHASE(4);
         // ---- (4) work lists: a wave op's rows are split among W warps (32
         // 16-byte vectors of each row per warp and block); the op's first warp
-        // also links its rowsum pairs
+        // also links its rowsum pairs (shared-memory atomics on rank 0's hash)
         const uint32_t nsel = min(S->nsel, wcap);
         const uint32_t W = max(1u, min(8u, (H4 + 31) / 32));
         for (uint32_t tk = gwarp; tk < nsel * W; tk += GW) {
-            const uint32_t x = tk / W, part = tk - x * W;
+            // tasks 0..nsel-1: each op's first part (with the pair linking, on
+            // rank 0's warps for the first 32 ops); then the other parts
+            const uint32_t x = tk < nsel ? tk : (tk - nsel) / (W - 1);
+            const uint32_t part = tk < nsel ? 0u : 1u + (tk - nsel) % (W - 1);
             const bool first = part == 0;
             STEP_START();
             const uint32_t k = sel[x], i = pend[k];
