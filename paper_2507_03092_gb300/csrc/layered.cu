@@ -1435,7 +1435,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 if (it < nst) {
                     const uint32_t k = pairs[it], i = pend[k];
                     uint32_t pv, bs;
-                    warp_column_scan(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
+                    warp_column_scan<5>(cols + (size_t)i * CW, H, CW, pv, bs, msup + (size_t)i * SUPCAP);
                     if (lane == 0) {
                         mpiv[i] = pv;
                         mbsz[i] = bs;
