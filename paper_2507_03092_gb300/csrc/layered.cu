@@ -1466,17 +1466,22 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // later one is blocked; an op whose X support overflowed its list
         // blocks every later op (and itself, unless it is the first)
         if (lead) {        // (rank 0: at most WCAP window ops)
-            for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
+            // two threads per window op, each walking every other entry of its
+            // X-support list
+            for (uint32_t tt = threadIdx.x; tt < 2 * nlook; tt += blockDim.x) {
+                const uint32_t k = tt >> 1, half = tt & 1u;
                 if (wpiv[k] == NOPIV) continue;
-                atomicMin(&S->firstrand, k);
-                atomicAdd(&S->nrand, 1u);
+                if (!half) {
+                    atomicMin(&S->firstrand, k);
+                    atomicAdd(&S->nrand, 1u);
+                }
                 const uint32_t i = pend[k], xn = wxn[k];
                 if (xn == XS_OVER) {
-                    atomicMin(&S->cut, k);
+                    if (!half) atomicMin(&S->cut, k);
                     continue;
                 }
                 const uint16_t *xl = mxs + (size_t)i * XSCAP;
-                for (uint32_t e = 0; e < xn; e++) {
+                for (uint32_t e = half; e < xn; e += 2) {
                     const uint32_t j = xl[e];
                     if (j == i || j < wfirst || j > wlast || stat[j] != MS_RANDOM) continue;
                     const uint32_t late = max(i, j);
