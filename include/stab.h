@@ -347,10 +347,13 @@ int stab_launch_count(stab_ctx *ctx, uint64_t *count, int reset);
  * [4] sum over deterministic measurements of |K| (stabilizer rows multiplied),
  * [5] sum over random measurements of |A| (rows that received a rowsum),
  * [6] cached pivots recomputed, [7] rowsum passes (one per wave), [8..15] SM clock cycles spent by
- * the random-measurement kernel in its eight per-wave phases (pending list,
- * cached-state pass, column rescans, X-support rescans, selection, work
- * lists, single-pivot rows with column updates and row copies, multi-pivot
- * rows), [19] pivot-row X supports recomputed.
+ * the random-measurement kernel in its per-wave phases (pending list with
+ * the window pass [8], [9] unused, column and X-support rescans [10], [11]
+ * unused, selection [12], work lists [13], rowsums with column updates and
+ * row copies [14], the separate multi-pivot phase of serial waves [15]),
+ * [16..18], [20], [21] sub-step cycles of the kernel's first warp,
+ * [19] pivot-row X supports recomputed, [22] waves applied serially (a dense
+ * pivot or an overflowed list), [23] waves with a dense pivot.
  * n <= 24 entries are written. */
 int stab_engine_counters(stab_ctx *ctx, uint64_t *out, size_t n, int reset);
 

@@ -361,7 +361,7 @@ COUNTER_NAMES = ("waves", "wave_ops", "det_in_wave_kernel", "det", "sum_K", "sum
                  "pivot_recomputes", "rowsum_passes",
                  "cyc_pending", "cyc_cached", "cyc_col_rescans", "cyc_xs_rescans", "cyc_select",
                  "cyc_lists", "cyc_apply_single", "cyc_apply_multi", "w0_list_scan", "w0_list_pairs",
-                 "w0_multi_walk", "xsupport_recomputes", "w0_multi_sort", "w0_multi_rows", "unused22", "unused23")
+                 "w0_multi_walk", "xsupport_recomputes", "w0_multi_sort", "w0_multi_rows", "serial_waves", "dense_waves")
 
 
 def stab_engine_counters(ctx, reset=True) -> dict:

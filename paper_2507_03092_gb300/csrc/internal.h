@@ -313,7 +313,7 @@ enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K
              // SM cycles of warp 0's sub-steps: work lists (row scans, pair lists),
              // multi-pivot rows (chain walk and keys, sort, scan rows)
              DC_W0_LIST_SCAN = 16, DC_W0_LIST_PAIRS = 17, DC_W0_MULTI_WALK = 18, DC_W0_MULTI_SORT = 20,
-             DC_W0_MULTI_ROWS = 21 };
+             DC_W0_MULTI_ROWS = 21, DC_SERIAL_WAVES = 22, DC_DENSE_WAVES = 23 };
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,

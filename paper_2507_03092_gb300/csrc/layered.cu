@@ -1696,6 +1696,10 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // serial: a dense pivot, or an overflowed list whose fallback reads
         // pivot rows from the tableau -- the row copies wait for them
         const bool serial = S->serial || npair > paircap || nent > jcap;
+        if (gtid == 0) {
+            count(a, DC_SERIAL_WAVES, serial ? 1u : 0u);
+            count(a, DC_DENSE_WAVES, S->serial ? 1u : 0u);
+        }
         // pivot rows become +-Z_a (16-byte stores over the Hr-word rows; the
         // words past H are zero in every row), with the coin as sign, and the
         // outcome; row q already holds the old pivot row (work lists)
