@@ -902,6 +902,11 @@ __global__ void __launch_bounds__(DET_WARPS * 32) k_meas_late(LArgs a, uint32_t 
     const uint32_t H = a.P.H, CW = a.P.CW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Layer M = a.P.layers[layer];
+    // the layer is done with its random measurements: k_destab_to_rm made the
+    // destabilizer half current where it was not, and the flag is cleared
+    if (blockIdx.x == 0)
+        for (uint32_t t = threadIdx.x; t < a.B; t += blockDim.x)
+            if (a.tflags[t] & TF_RAND_LAYER) a.tflags[t] = TF_DESTAB_FRESH;
     const unsigned long long total = (unsigned long long)M.count * a.B;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * DET_WARPS;
     for (unsigned long long idx = (unsigned long long)blockIdx.x * DET_WARPS + warp; idx < total; idx += nwarps) {
@@ -1147,7 +1152,7 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
 // are each rank's own.
 __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t layer) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ uint32_t s_wt[32], s_tot, s_any;              // this CTA's block scans and first test
+    __shared__ uint32_t s_wt[32], s_tot;                     // rank 0's block scans
     __shared__ uint32_t xcnt[2 * RAND_WARPS];                // X-support counts of the 16-lane groups
     const uint32_t n = a.P.n, H = a.P.H, CW = a.P.CW, RS = a.RS, Hr = a.Hr, H4 = Hr >> 2;
     // one cluster of CTAs per tableau: rank 0 holds the wave state in its
@@ -1186,19 +1191,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     uint32_t *const rowver = a.rowver + (size_t)t * 32 * H;
     uint16_t *const pwl = a.pwl + (size_t)t * WCAP * PWCAP;
     const bool item_smem = n <= QMAP_SMEM_MAX;
-    // every rank's first test reads only global memory, so all ranks leave
-    // together or none does (no rank may leave while others can still reach
-    // rank 0's shared memory)
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < M.count; i += blockDim.x)
-        if (gstat[i] == MS_RANDOM) s_any = 1;
-    __syncthreads();
-    if (lead && threadIdx.x == 0) {
-        // k_destab_to_rm has made the destabilizer half current if it was not
-        if (a.tflags[t] & TF_RAND_LAYER) a.tflags[t] = TF_DESTAB_FRESH;
-    }
-    if (!s_any) return;
+    // every rank's first test reads a flag that no kernel changes while this
+    // one runs (k_meas_det sets it when an op of the layer is random,
+    // k_meas_late clears it), so all ranks leave together or none does (no
+    // rank may leave while others can still reach rank 0's shared memory)
+    if (!(a.tflags[t] & TF_RAND_LAYER)) return;
     cl.sync();                         // every rank has started: rank 0's shared memory is reachable
     unsigned char *const sm = lead ? smraw : static_cast<unsigned char *>(cl.map_shared_rank((void *)smraw, 0));
     RandShared *const S = reinterpret_cast<RandShared *>(sm + Lo.sh);
