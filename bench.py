@@ -41,10 +41,12 @@ METRIC = "surface-code d=71 gate+measure ops/s"
 # entry records the SHA-256 (first 16 hex digits) of the source files, and a
 # kernel whose sources changed since reports traffic null.
 NCU_TRAFFIC = {
-    "k_meas_rand": {"bytes_per_launch": 607.3e3, "src_sha": "5d6f8aa304a4d89e",
-                    "tag": "ncu capture, mean over the 72 launches of a d=71 step (43.45 MB read + 0.27 MB written)"},
-    "k_gate_run": {"bytes_per_launch": 70.24e6, "src_sha": "5d6f8aa304a4d89e",
-                   "tag": "ncu capture, steady syndrome-round launch (51.30 MB read + 18.94 MB written)"},
+    "k_meas_rand": {"bytes_per_launch": 408.6e3, "src_sha": "5d6f8aa304a4d89e",
+                    "tag": "ncu capture without cache flushing, mean over the 72 launches of a d=71 step "
+                           "(12.36 MB read + 17.06 MB written)"},
+    "k_gate_run": {"bytes_per_launch": 83.30e6, "src_sha": "5d6f8aa304a4d89e",
+                   "tag": "ncu capture without cache flushing, steady syndrome-round launch "
+                          "(20.04 MB read + 63.26 MB written, the writes mostly dirty lines evicted from L2)"},
 }
 KERNEL_SOURCES = ("paper_2507_03092_gb300/csrc/layered.cu", "paper_2507_03092_gb300/csrc/device_common.cuh",
                   "paper_2507_03092_gb300/csrc/internal.h")
