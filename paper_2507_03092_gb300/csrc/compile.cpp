@@ -26,6 +26,62 @@ static bool is_two(uint8_t k) { return k == STAB_CX || k == STAB_CZ || k == STAB
 static bool is_noise(uint8_t k) { return k == STAB_DEP1 || k == STAB_DEP2 || k == STAB_PC1; }
 static bool is_meas_class(uint8_t k) { return k == STAB_M || k == STAB_R || k == STAB_RESET_ERR; }
 
+// Order of one gate layer's items for the slice kernel, whose threads take 16
+// consecutive items per half-warp and read each operand's 8-byte slot: aligned
+// groups of 16 items whose first operands lie in 16 distinct bank pairs (slot
+// mod 16), and whose second operands do too, as far as the layer allows.
+// Greedy: per group, the bank pairs of the first operand in order of the items
+// left in them, each taking an item whose second operand's bank pair is not
+// yet used (the fullest such class); a group left short is filled with the
+// items that add the fewest repeats.  Any order of a layer's items gives the
+// same tableau, since they act on disjoint qubits.
+static void bank_order(const GItem *g, uint32_t count, std::vector<uint32_t> &perm) {
+    std::vector<uint32_t> cls[16][16];
+    uint32_t deg[16] = {0};
+    for (uint32_t i = 0; i < count; i++) {
+        const uint32_t ca = gate_slot(g[i].a) & 15u, cb = gate_slot(g[i].b) & 15u;
+        cls[ca][cb].push_back(i);
+        deg[ca]++;
+    }
+    perm.clear();
+    perm.reserve(count);
+    while (perm.size() < count) {
+        uint32_t order[16];
+        for (uint32_t c = 0; c < 16; c++) order[c] = c;
+        std::stable_sort(order, order + 16, [&](uint32_t x, uint32_t y) { return deg[x] > deg[y]; });
+        uint32_t na[16] = {0}, nb[16] = {0}, got = 0;
+        const uint32_t want = (uint32_t)std::min<size_t>(16, count - perm.size());
+        for (uint32_t k = 0; k < 16 && got < want; k++) {
+            const uint32_t ca = order[k];
+            if (!deg[ca]) break;
+            int best = -1;
+            for (uint32_t cb = 0; cb < 16; cb++)
+                if (!nb[cb] && !cls[ca][cb].empty() && (best < 0 || cls[ca][cb].size() > cls[ca][best].size()))
+                    best = (int)cb;
+            if (best < 0) continue;
+            perm.push_back(cls[ca][best].back());
+            cls[ca][best].pop_back();
+            deg[ca]--; na[ca]++; nb[best]++; got++;
+        }
+        while (got < want) {
+            int ba = -1, bb = -1;
+            uint32_t bs = 0;
+            size_t bl = 0;
+            for (uint32_t ca = 0; ca < 16; ca++)
+                for (uint32_t cb = 0; cb < 16; cb++) {
+                    if (cls[ca][cb].empty()) continue;
+                    const uint32_t sc = na[ca] + nb[cb];
+                    if (ba < 0 || sc < bs || (sc == bs && cls[ca][cb].size() > bl)) {
+                        ba = (int)ca; bb = (int)cb; bs = sc; bl = cls[ca][cb].size();
+                    }
+                }
+            perm.push_back(cls[ba][bb].back());
+            cls[ba][bb].pop_back();
+            deg[ba]--; na[ba]++; nb[bb]++; got++;
+        }
+    }
+}
+
 // Pauli-product measurement as a Clifford conjugation (the PBC rewriting of
 // Sec. 2.8: a measurement absorbs the Cliffords around it).  U maps the
 // product P of the factors to +Z on the last factor's qubit t:
@@ -290,13 +346,14 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         return STAB_ERR_UNSUPPORTED;
     }
     if (n > 65535) {
-        // the packed items below hold 16-bit qubit indices; engines reject such n anyway
+        // the packed items below hold 16-bit slots; engines reject such n anyway
     }
     // ---- packed items, item -> layer map, noise-event capacities ----
     P.sitems.resize(P.gitems.size());
     P.sab.resize(P.gitems.size());
     P.item_layer.resize(P.gitems.size());
     uint32_t ev_total = 0;
+    std::vector<uint32_t> perm;
     for (uint32_t l = 0; l < P.layers.size(); l++) {
         Layer &L = P.layers[l];
         L.ev_off = ev_total;
@@ -305,10 +362,12 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         L.uniform = 0;
         if (L.type != LT_GATE) continue;
         L.uniform = L.count ? P.gitems[L.first].gate : 0u;
+        bank_order(P.gitems.data() + L.first, L.count, perm);
         for (uint32_t i = L.first; i < L.first + L.count; i++) {
             const GItem &g = P.gitems[i];
-            P.sitems[i].ab = (g.a & 0xffffu) | ((g.b & 0xffffu) << 16);
-            P.sitems[i].g = g.gate;
+            const GItem &gp = P.gitems[L.first + perm[i - L.first]];
+            P.sitems[i].ab = (gate_slot(gp.a) & 0xffffu) | ((gate_slot(gp.b) & 0xffffu) << 16);
+            P.sitems[i].g = gp.gate;
             P.sab[i] = P.sitems[i].ab;
             P.item_layer[i] = l;
             if (g.nn) L.n_noisy++;

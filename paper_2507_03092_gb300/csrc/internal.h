@@ -67,10 +67,26 @@ struct Layer {
 };
 
 // Packed gate item for the layered engine's slice kernel (noise handled by
-// the event pre-pass): ab = a | b << 16, g = gate kind.
+// the event pre-pass): ab = a | b << 16 with a, b the operands' slots
+// (gate_slot below), g = gate kind.
 struct SItem {
     uint32_t ab, g;
 };
+
+// Shared-memory slot of column j in the slice kernel: j with its low four bits
+// XORed with a hash of bits 4..9.  A slice holds 8 bytes per column, so 16
+// consecutive slots fill the 32 banks once.  Within every aligned block of 16
+// columns the map is a permutation, which keeps loops over consecutive
+// columns free of bank conflicts.  The columns that one gate layer touches
+// are often every other qubit; the hash spreads them over all 16 bank pairs,
+// and the compiler orders each layer's items so that every aligned group of
+// 16 items reads 16 distinct bank pairs as far as the layer allows.  Slots
+// stay below n rounded up to a multiple of 16.  For columns j = i + k * 1024
+// the XOR is the same for every k.
+__host__ __device__ __forceinline__ uint32_t gate_slot(uint32_t j) {
+    const uint32_t m = j >> 4;
+    return j ^ ((m ^ (m >> 2)) & 15u);
+}
 
 struct Thr {              // floor(p_i * 2^32) for the three parameters of a row
     unsigned long long t[3];

@@ -327,12 +327,16 @@ __device__ __noinline__ uint32_t layer_noise_all(const GItem *items, uint32_t co
         if (!gi.nn) continue;
         uint32_t Pa, Pb;
         item_noise(gi, call->st, t, thr, Pa, Pb);
-        racc ^= xz_flip(Pa, sxz[gi.a].x, sxz[gi.a].y) ^ xz_flip(Pb, sxz[gi.b].x, sxz[gi.b].y);
+        const uint2 va = sxz[gate_slot(gi.a)], vb = sxz[gate_slot(gi.b)];
+        racc ^= xz_flip(Pa, va.x, va.y) ^ xz_flip(Pb, vb.x, vb.y);
     }
     return racc;
 }
 
 constexpr uint32_t RUN_STAGE = 16;       // layers of a run whose descriptors are staged
+// FIXED: blockDim.x is 1024, so the slot of every column a thread visits in
+// its strided loops is the column XOR one per-thread constant.
+template <bool FIXED>
 __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t sred[32];
@@ -350,9 +354,13 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         s_layer[threadIdx.x] = a.P.layers[l];
         s_evc[threadIdx.x] = a.ev_cnt ? a.ev_cnt[(size_t)t * a.P.n_layers + l] : 0u;
     }
-    // the slice: word w of column j's x and z planes side by side (one 8-byte
-    // shared-memory access per column and gate operand)
+    // the slice: word w of column j's x and z planes side by side in slot
+    // gate_slot(j) (one 8-byte shared-memory access per column and gate
+    // operand; the items carry their operands' slots)
     uint2 *sxz = reinterpret_cast<uint2 *>(smem);
+    const uint32_t tx = gate_slot(threadIdx.x) ^ threadIdx.x;
+    // slot of column j in the loops over j = threadIdx.x + k * blockDim.x
+    auto cslot = [&](uint32_t j) { return FIXED ? (j ^ tx) : gate_slot(j); };
     uint32_t *qx = a.qm + t * a.qm_stride, *qz = qx + (size_t)CW * n;
     uint32_t *rm = a.rm + t * a.rm_stride;
     uint8_t *dirty = a.dirty + (size_t)t * CW;
@@ -375,11 +383,12 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t j = j0 + k * bd;
-                if (j < n) sxz[j] = make_uint2(vx[k], vz[k]);
+                if (j < n) sxz[cslot(j)] = make_uint2(vx[k], vz[k]);
             }
         }
     } else {
-        slice_load_rm(rm, a.RS, a.Hr, H, n, w, [&](uint32_t j, uint32_t x, uint32_t z) { sxz[j] = make_uint2(x, z); });
+        slice_load_rm(rm, a.RS, a.Hr, H, n, w,
+                      [&](uint32_t j, uint32_t x, uint32_t z) { sxz[gate_slot(j)] = make_uint2(x, z); });
     }
     __syncthreads();
     uint32_t racc = 0;
@@ -390,8 +399,9 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
         const uint32_t cnt = a.flip_cnt[(size_t)t * a.P.n_layers + (uint32_t)g.cond_layer];
         const uint32_t *fl = a.flips + t * 2 * a.m_stride;
         for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const uint32_t f = fl[e], q = f & 0x3fffffffu;
-            racc ^= (f >> 30) == 1u ? sxz[q].y : sxz[q].x;
+            const uint32_t f = fl[e];
+            const uint2 v = sxz[gate_slot(f & 0x3fffffffu)];
+            racc ^= (f >> 30) == 1u ? v.y : v.x;
         }
         __syncthreads();          // every flip has read its pre-gate word
     }
@@ -425,13 +435,14 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
             const uint32_t cnt = ecnt;
             if (cnt <= L.ev_cap) {
                 if (threadIdx.x < cnt) {
-                    const uint2 v = sxz[my_ev & 0x3fffffffu];
+                    const uint2 v = sxz[gate_slot(my_ev & 0x3fffffffu)];
                     racc ^= xz_flip(my_ev >> 30, v.x, v.y);
                 }
                 const uint32_t *ev = a.ev + (size_t)t * a.P.ev_total + L.ev_off;
                 for (uint32_t e = threadIdx.x + blockDim.x; e < cnt; e += blockDim.x) {
-                    const uint32_t v = ev[e], q = v & 0x3fffffffu;
-                    racc ^= xz_flip(v >> 30, sxz[q].x, sxz[q].y);
+                    const uint32_t v = ev[e];
+                    const uint2 c = sxz[gate_slot(v & 0x3fffffffu)];
+                    racc ^= xz_flip(v >> 30, c.x, c.y);
                 }
             } else {
                 racc ^= layer_noise_all(a.P.gitems + L.first, L.count, a.P.thr, a.call, t, sxz);
@@ -444,7 +455,7 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) sred[warp] = racc;
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const uint2 v = sxz[j];
+        const uint2 v = sxz[cslot(j)];
         qx[(size_t)w * n + j] = v.x;
         qz[(size_t)w * n + j] = v.y;
     }
@@ -460,8 +471,8 @@ __global__ void __launch_bounds__(1024, 2) k_gate_run(LArgs a, GRun g) {
     if (w == 0 && threadIdx.x == 0) a.tflags[t] &= ~TF_DESTAB_FRESH;
     if (g.want_rm && w >= H) {        // stabilizer half only (see TF_DESTAB_FRESH)
         slice_store_rm(rm, a.RS, a.Hr, H, w,
-                       [&](uint32_t j) { return j < n ? sxz[j].x : 0u; },
-                       [&](uint32_t j) { return j < n ? sxz[j].y : 0u; });
+                       [&](uint32_t j) { return j < n ? sxz[gate_slot(j)].x : 0u; },
+                       [&](uint32_t j) { return j < n ? sxz[gate_slot(j)].y : 0u; });
     }
 }
 
@@ -2076,7 +2087,7 @@ __global__ void k_cond(LArgs a, uint32_t layer) {
 }
 
 // ---------------------------------------------------------------- host side
-size_t layered_gate_smem(uint32_t n) { return (size_t)8 * n; }
+size_t layered_gate_smem(uint32_t n) { return (size_t)8 * ((n + 15u) & ~15u); }   // slots below round16(n)
 
 size_t rand_smem(uint32_t n, uint32_t H);
 
@@ -2400,7 +2411,8 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
                         unsigned long long *d_stats, GraphSlot *gsl) {
     {
         const int lim = (int)(lc0.smem_optin - 1024);
-        smem_attr_once(0, (const void *)k_gate_run, lim);
+        smem_attr_once(0, (const void *)k_gate_run<true>, lim);
+        smem_attr_once(4, (const void *)k_gate_run<false>, lim);
         smem_attr_once(1, (const void *)k_meas_det, lim);
         smem_attr_once(2, (const void *)k_meas_late, lim);
         smem_attr_once(3, (const void *)k_meas_rand, lim);
@@ -2519,7 +2531,12 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
             const bool next_meas = k + 1 < p.runs.size() && p.runs[k + 1].type == LT_MEAS;
             g.want_rm = next_meas ? 1u : 0u;
             launch(kp, STAB_KERNEL_GATE_RUN, s, R.alg_bytes * b.count,
-                   [&] { k_gate_run<<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g); });
+                   [&] {
+                       if (gthreads == 1024)
+                           k_gate_run<true><<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g);
+                       else
+                           k_gate_run<false><<<dim3(b.CW, b.count), gthreads, gsm, s>>>(a, g);
+                   });
             b.rm_valid = next_meas;
         } else {
             const uint32_t l = R.l0;
