@@ -233,15 +233,17 @@ struct LaunchCfg {
 struct WaveCaps {
     // Maxima size k_meas_rand's shared memory, which shares each SM's 256 KB
     // with its L1 cache; larger lists only fall back to slower loops when
-    // they overflow.  The window (pending measurements examined per wave) is
-    // at most WCAP_MAX, so every selected measurement fits the wave.
-    static constexpr uint32_t PCAP_MAX = 4096, WCAP_MAX = 512, PAIRCAP_MAX = 2048, JCAP_MAX = 2048;
+    // they overflow.  The window (pending measurements examined per wave,
+    // at most WINDOW_MAX) may hold more selectable measurements than a wave
+    // takes (WCAP_MAX): those beyond it stay pending for the next wave.
+    static constexpr uint32_t PCAP_MAX = 4096, WCAP_MAX = 512, PAIRCAP_MAX = 2048, JCAP_MAX = 2048,
+                              WINDOW_MAX = 1024;
     uint32_t pcap = PCAP_MAX;          // pending measurements considered per wave
     uint32_t wcap = WCAP_MAX;          // measurements applied per wave
     uint32_t paircap = PAIRCAP_MAX;    // (row, pivot) rowsum pairs listed per wave
     uint32_t jcap = JCAP_MAX;          // measured-column updates listed per wave
     uint32_t mark_budget = 0;          // unused (kept so that the test variable keeps its fields)
-    uint32_t window = WCAP_MAX;        // pending measurements examined per wave
+    uint32_t window = WINDOW_MAX;      // pending measurements examined per wave
     // Waves allowed per measurement layer before the kernel gives up with a
     // bounds error (the loop's own bound, 2 x ops + 3, applies as well);
     // lowered only by tests, to see the guard fire and the context survive.

@@ -63,6 +63,7 @@ enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2, MS_WAVE = 3, MS_DETLAT
 // k_destab_to_rm fills the other half when a layer turns out to have random ops.
 enum : uint32_t { TF_DESTAB_FRESH = 1u, TF_RAND_LAYER = 2u };
 
+
 struct LArgs {
     DevProg P;
     uint32_t *qm;
@@ -1012,7 +1013,14 @@ __device__ __forceinline__ void rowsum_warp_sparse(uint32_t *rm, uint32_t RS, ui
 constexpr int RAND_THREADS = 1024;
 constexpr int RAND_WARPS = RAND_THREADS / 32;
 constexpr uint32_t PCAP = WaveCaps::PCAP_MAX;
-constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;
+constexpr uint32_t WCAP = WaveCaps::WCAP_MAX;     // ops applied per wave
+// Pending ops examined per wave.  A d = 71 surface code's final layer takes 70
+// waves with 1024 and 82 with 512: its first ops in circuit order conflict with
+// one another, so a short window holds few that can join a wave.  Only the
+// window's 5 bytes per op scale with it; the wave's per-op arrays (51 bytes)
+// scale with WCAP, which keeps the layout small enough for the L1 cache's share
+// of each SM (a layout 29 KB larger measured 7 % slower).
+constexpr uint32_t WIN = WaveCaps::WINDOW_MAX;
 constexpr uint32_t PAIRCAP = WaveCaps::PAIRCAP_MAX;
 constexpr uint32_t JCAP = WaveCaps::JCAP_MAX;
 constexpr uint32_t HT = 4096;                 // row hash slots (> PAIRCAP: never full)
@@ -1022,32 +1030,35 @@ constexpr uint16_t NOPIV = 0xffffu;
 constexpr uint32_t HEMPTY = 0xffffffffu;
 constexpr uint32_t QMAP_SMEM_MAX = 16384;     // qubits whose item map fits shared memory
 static_assert(PCAP <= 8 * RAND_THREADS, "pending-list compaction keeps 8 entries per thread");
-static_assert(WCAP <= RAND_THREADS, "one thread per window op");
+static_assert(WIN <= RAND_THREADS && WCAP <= WIN, "one thread per window op");
 static_assert(HT > PAIRCAP && (HT & (HT - 1)) == 0, "row hash larger than the pair list, power of two");
 
-// k_meas_rand's dynamic shared memory, byte offsets (16-byte aligned blocks).
-// The wave state's scalars, read and written by every CTA of the cluster.
-struct RandShared {
-    uint32_t np, nsel, npair, nent, firstrand, nrand, nstale, cut, serial, nmulti;
-};
+// k_meas_rand's dynamic shared memory: byte offsets of its blocks (rand_layout)
 struct RandLayout {
     uint32_t sh, pend, wpiv, wbsz, wxn, sel, sr, pwn, pairs, nxt, hslot, dlist, hkey, htail, ents, spc, spx, spz,
         hcnt, wkeys, wlist, wacc, qmask, blocked, pmask, wq, qmap, stat, stale, r, total;
+};
+
+// The wave state's scalars in k_meas_rand's dynamic shared memory, read and
+// written by every CTA of the cluster.
+struct RandShared {
+    uint32_t np, nsel, npair, nent, firstrand, nrand, nstale, cut, serial, nmulti, npw;
 };
 __host__ __device__ __forceinline__ uint32_t rl_take(uint32_t &o, uint32_t bytes) {
     const uint32_t at = o;
     o = (o + bytes + 15u) & ~15u;
     return at;
 }
+// The layout's blocks, 16-byte aligned.
 __host__ __device__ __forceinline__ RandLayout rand_layout(uint32_t n, uint32_t H) {
     RandLayout L;
     uint32_t o = 0;
     const bool item_smem = n <= QMAP_SMEM_MAX;
     L.sh = rl_take(o, sizeof(RandShared));
     L.pend = rl_take(o, 2 * PCAP);
-    L.wpiv = rl_take(o, 2 * WCAP);
-    L.wbsz = rl_take(o, 2 * WCAP);
-    L.wxn = rl_take(o, WCAP);
+    L.wpiv = rl_take(o, 2 * WIN);
+    L.wbsz = rl_take(o, 2 * WIN);
+    L.wxn = rl_take(o, WIN);
     L.sel = rl_take(o, 2 * WCAP);
     L.sr = rl_take(o, WCAP);
     L.pwn = rl_take(o, 4 * WCAP);
@@ -1135,7 +1146,7 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t *keys, uint32_t nk) {
 // read from each pending op's cached pivot-row X support over the layer's
 // items (mxs), recomputed only when the op's measured column changed (mstale)
 // or its pivot row did (row versions), so selection needs no pass over
-// columns and a window of up to WCAP pending ops costs the same as a small one.
+// columns and a window of up to WIN pending ops costs the same as a small one.
 //
 // Per wave: (1) ordered list of pending random ops; (2) refresh of stale
 // pivots, X supports and pivot word counts of the window; (3) selection: an
@@ -1187,7 +1198,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     const RandLayout Lo = rand_layout(n, H);
     const uint32_t pcap = a.caps.pcap, wcap = min(a.caps.wcap, WCAP), paircap = a.caps.paircap,
                    jcap = a.caps.jcap;
-    const uint32_t wmax = max(1u, min(a.caps.window, WCAP));
+    const uint32_t wmax = max(1u, min(a.caps.window, WIN));
     uint8_t *const gstat = a.mstat + t * a.m_stride, *out = a.mout + t * a.m_stride;
     uint32_t *const cols = a.cols + t * a.cols_stride;
     uint32_t *const rm = a.rm + t * a.rm_stride;
@@ -1355,11 +1366,11 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
                 S->np = min(s_tot, pcap);
                 S->nsel = 0; S->npair = 0; S->nent = 0; S->nstale = 0;
                 S->firstrand = 0xffffffffu; S->nrand = 0; S->cut = 0xffffffffu;
-                S->serial = 0; S->nmulti = 0;
+                S->serial = 0; S->nmulti = 0; S->npw = 0;
             }
             __syncthreads();
             // ---- (2) window: cached pivots and X supports, on rank 0 (at
-            // most WCAP ops).  Ops whose measured column changed are listed in
+            // most WIN ops).  Ops whose measured column changed are listed in
             // `pairs` (free until the work lists) for a column rescan; ops whose
             // pivot row changed (or is new) in `ents` for an X-support rescan.
             const uint32_t np0 = S->np;
@@ -1473,7 +1484,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
         // ---- (3) selection: for every conflicting pair of window ops the
         // later one is blocked; an op whose X support overflowed its list
         // blocks every later op (and itself, unless it is the first)
-        if (lead) {        // (rank 0: at most WCAP window ops)
+        if (lead) {        // (rank 0: at most WIN window ops)
             // two threads per window op, each walking every other entry of its
             // X-support list
             for (uint32_t tt = threadIdx.x; tt < 2 * nlook; tt += blockDim.x) {
@@ -1500,10 +1511,19 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
             if (S->nrand != 0) {          // (otherwise the window became deterministic)
                 if (threadIdx.x == 0) S->nent = 0;   // the X-support list is done with
                 const uint32_t cut = S->cut, fr = S->firstrand;
-                for (uint32_t k = threadIdx.x; k < nlook; k += blockDim.x) {
-                    const uint32_t i = pend[k];
-                    if (wpiv[k] == NOPIV || ((blocked[i >> 5] >> (i & 31)) & 1u)) continue;
-                    if (k > cut || (k == cut && k != fr)) continue;
+                // one window op per thread (the window is at most WIN <=
+                // RAND_THREADS ops).  A selectable op commutes with every earlier
+                // pending op, so any subset of them is a wave (those left out
+                // stay pending).  The wave takes them while their rowsum pairs
+                // (at most the column size less the pivot row) fit the pair
+                // list, so that only a wave whose first op alone overflows it
+                // takes the serial path.
+                const uint32_t k = threadIdx.x, i = k < nlook ? pend[k] : 0u;
+                const bool ok = k < nlook && wpiv[k] != NOPIV && !((blocked[i >> 5] >> (i & 31)) & 1u) &&
+                                !(k > cut || (k == cut && k != fr));
+                const uint32_t wt = ok ? max(1u, (uint32_t)wbsz[k]) - 1u : 0u;
+                const uint32_t before = ok ? atomicAdd(&S->npw, wt) : 0u;
+                if (ok && (before == 0 || before + wt <= paircap)) {
                     const uint32_t idx = atomicAdd(&S->nsel, 1u);
                     if (idx < wcap) {
                         sel[idx] = (uint16_t)k;

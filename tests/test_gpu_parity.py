@@ -340,13 +340,14 @@ def test_wave_loop_guard_reports_an_error_and_the_context_survives():
     assert "after True" in lines, r.stdout
 
 
-def test_layered_wide_layer_item_state_in_global_memory(sim):
-    """n = 16 400 > 16 384: the wave kernel keeps the layer's qubit map, item
-    status and stale flags in global memory instead of shared memory, and the
-    one measurement layer of 16 400 ops overflows the 4096-entry pending list
-    (rebuilt from all items).  Bell pairs joined into chains of four make
-    rowsums that touch several rows per random measurement."""
-    n = 16400
+@pytest.mark.parametrize("n", [14000, 16400])
+def test_layered_wide_measurement_layer(sim, n):
+    """One measurement layer of n ops overflows the 4096-entry pending list
+    (rebuilt from all items).  n = 16 400 > 16 384: the wave kernel keeps the
+    layer's qubit map, item status and stale flags in global memory instead of
+    shared memory; n = 14 000 keeps them in shared memory.  Bell pairs joined
+    into chains of four make rowsums that touch several rows per random
+    measurement."""
     b = C.Builder(n)
     for q in range(n):
         b.gate1(C.H, q)
@@ -363,7 +364,7 @@ def test_layered_wide_layer_item_state_in_global_memory(sim):
     rec, tabs = _apply_layered(sim, circ, coins[0], noise[0])
     orec, otab = _oracle(circ, coins[0], noise[0])
     assert np.array_equal(rec[0], orec)
-    _assert_tableau_equal(tabs[0], otab, "n=16400")
+    _assert_tableau_equal(tabs[0], otab, "n=%d" % n)
 
 
 def test_layered_largest_n_and_one_past_it(sim):
