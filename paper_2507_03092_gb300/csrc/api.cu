@@ -206,13 +206,14 @@ stab_tune lookup_tune(const stab_ctx *ctx, uint32_t n) {
 
 // One device allocation holds every array of a compiled program, followed by
 // its DevProg descriptor (used by the resident engine's job table).
-static constexpr int PROG_ARRAYS = 8;
+static constexpr int PROG_ARRAYS = 9;
 static size_t prog_layout(const HostProg &P, size_t off[PROG_ARRAYS + 1]) {
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
                                     P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
                                     P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
-                                    P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t)};
+                                    P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t),
+                                    P.layers.size()};
     size_t o = 0;
     for (int k = 0; k < PROG_ARRAYS; k++) {
         off[k] = o;
@@ -225,6 +226,13 @@ static size_t prog_layout(const HostProg &P, size_t off[PROG_ARRAYS + 1]) {
 static void free_prog(HostProg &P) {
     if (P.lay) free_prog(*P.lay);
     prog_graphs_free(P);
+    if (P.rand_ev) {
+        cudaEventSynchronize(P.rand_ev);
+        cudaEventDestroy(P.rand_ev);
+    }
+    if (P.rand_host) cudaFreeHost(P.rand_host);
+    P.rand_ev = nullptr;
+    P.rand_host = nullptr;
     if (P.dmem) cudaFree(P.dmem);
     P.dmem = nullptr;
 }
@@ -246,14 +254,15 @@ static int upload_prog(HostProg &P) {
     P.dev.item_layer = (const uint32_t *)(b + off[5]);
     P.dev.mfactors = (const uint32_t *)(b + off[6]);
     P.dev.sab = (const uint32_t *)(b + off[7]);
-    const void *src[PROG_ARRAYS] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
-                                    P.sitems.data(), P.item_layer.data(), P.mfactors.data(), P.sab.data()};
-    const size_t sz[PROG_ARRAYS] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
-                                    P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
-                                    P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
-                                    P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t)};
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < PROG_ARRAYS && !e; k++)
+    P.dev.layer_rand = (uint8_t *)(b + off[8]);
+    const void *src[PROG_ARRAYS - 1] = {P.layers.data(), P.gitems.data(), P.mitems.data(), P.thr.data(),
+                                        P.sitems.data(), P.item_layer.data(), P.mfactors.data(), P.sab.data()};
+    const size_t sz[PROG_ARRAYS - 1] = {P.layers.size() * sizeof(Layer), P.gitems.size() * sizeof(GItem),
+                                        P.mitems.size() * sizeof(MItem), P.thr.size() * sizeof(Thr),
+                                        P.sitems.size() * sizeof(SItem), P.item_layer.size() * sizeof(uint32_t),
+                                        P.mfactors.size() * sizeof(uint32_t), P.sab.size() * sizeof(uint32_t)};
+    cudaError_t e = cudaMemset(b + off[8], 0, P.layers.size() + 1);   // no layer marked yet
+    for (int k = 0; k < PROG_ARRAYS - 1 && !e; k++)
         if (sz[k]) e = cudaMemcpy(b + off[k], src[k], sz[k], cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(b + off[PROG_ARRAYS], &P.dev, sizeof(DevProg), cudaMemcpyHostToDevice);
     if (e) return cuda_fail(e, "uploading the compiled circuit");
@@ -301,7 +310,7 @@ int run_layered_shots(stab_ctx *ctx, const HostProg &user_prog, uint32_t shots, 
         }
         GraphSlot *gsl = (s == ctx->stream && graph_slot_init(ctx->gslot) == 0) ? &ctx->gslot : nullptr;
         e = layered_run(p, b, ms, ds, (unsigned long long *)(d_record + (size_t)s0 * record_words),
-                        record_words, ctx->d_err, ctx->lc, s, &ctx->prof, ctx->d_stats, gsl);
+                        record_words, ctx->d_err, ctx->lc, s, &ctx->prof, ctx->d_stats, gsl, true);
         if (e) return cuda_fail(e, "layered run");
         work.rm_valid = b.rm_valid;
     }
@@ -498,6 +507,7 @@ int stab_sync(stab_ctx *ctx) {
         const char *what = flag == DERR_ODD_PHASE ? "odd power of i in a stabilizer product"
                          : flag == DERR_BAD_PRODUCT ? "deterministic product is not +-Z_a"
                          : flag == DERR_TIMEOUT ? "bounded device wait expired"
+                         : flag == DERR_SKIPPED ? "random outcome in a measurement layer run as deterministic"
                          : "device bounds check failed";
         return fail(flag == DERR_TIMEOUT ? STAB_ERR_TIMEOUT : STAB_ERR_INTERNAL,
                     std::string("device consistency check: ") + what);

@@ -335,11 +335,14 @@ int compile_program(uint32_t n, const stab_op *ops, size_t n_ops, const double *
         if (L.count) P.layers.push_back(L);
     }
     // folded resets may have flagged items of layers closed earlier
+    P.rand_learn = true;
     for (auto &L : P.layers)
         if (L.type == LT_MEAS) {
             L.has_cond = 0;
-            for (uint32_t i = L.first; i < L.first + L.count; i++)
+            for (uint32_t i = L.first; i < L.first + L.count; i++) {
                 if (P.mitems[i].flags & (MF_RESET | MF_RESET_ERR | MF_RESET_AFTER)) L.has_cond = 1;
+                if (P.mitems[i].flags & MF_RESET_ERR) P.rand_learn = false;   // resets drawn by noise
+            }
         }
     if (m_ord > 0xfffffff0ull || c_ord > 0xfffffff0ull || l_ord > 0xfffffff0ull) {
         *err = "circuit too long (more than 2^32 measurements or noise draws)";

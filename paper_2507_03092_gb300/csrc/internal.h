@@ -105,6 +105,7 @@ struct DevProg {          // by-value descriptor handed to kernels
     uint32_t max_gitems, n_gitems, n_mitems, ev_total;
     const uint32_t *mfactors;   // MPP factors (MF_MPP items)
     uint32_t n_mfactors, pad;
+    uint8_t *layer_rand;        // [n_layers] set by k_meas_rand in a layer with a random op
 };
 
 struct Run {              // layered engine schedule entry
@@ -141,6 +142,20 @@ struct HostProg {
     unsigned long long glaunches = 0;   // kernel launches in the graph
     bool grm_after = false;             // batch's row-packed copy valid after the run
     uint32_t gcl = 0;                   // wave-kernel cluster size the executable graph was built with
+    // Measurement layers that never have a random outcome.  Whether a Z
+    // measurement is random depends only on the stabilizer group up to signs,
+    // which Pauli noise, measurement outcomes and the X of resets leave alone:
+    // from |0...0>, it is fixed by the circuit unless the circuit holds
+    // RESET_ERROR (whose reset happens or not by a noise draw).  k_meas_rand
+    // marks each layer that has a random op (dev.layer_rand); after a run
+    // from |0...0> without device errors the host reads the marks once, and
+    // later such runs leave out the random-measurement launches of unmarked
+    // layers.  k_meas_det reports an error if one of those finds a random op.
+    bool rand_learn = false;            // the circuit allows it (no RESET_ERROR)
+    int rand_state = 0;                 // 0 unknown, 1 read-back queued, 2 known
+    cudaEvent_t rand_ev = nullptr;
+    uint8_t *rand_host = nullptr;       // pinned: [n_layers] marks, then the device error flag (int)
+    std::vector<uint8_t> rand_skip;     // per layer: leave out k_destab_to_rm, k_meas_rand, k_meas_late
     stab_circuit_info info{};
     uint64_t cost = 0;          // rough work estimate (for scheduling)
     void *dmem = nullptr;       // device copy of the arrays
@@ -297,7 +312,7 @@ void prog_graphs_free(HostProg &p);
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
-                        unsigned long long *d_stats, GraphSlot *gsl = nullptr);
+                        unsigned long long *d_stats, GraphSlot *gsl = nullptr, bool fresh = false);
 cudaError_t layered_sync_qm(Batch &b, cudaStream_t s);
 cudaError_t layered_commute(Batch &b, uint32_t index, const unsigned long long *px, const unsigned long long *pz,
                             size_t m, unsigned long long *out, cudaStream_t s, KernelProf *kp);
@@ -335,6 +350,6 @@ enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,
-             DERR_BOUNDS = 4 };
+             DERR_BOUNDS = 4, DERR_SKIPPED = 5 };
 
 }  // namespace stab

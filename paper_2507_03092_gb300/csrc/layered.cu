@@ -843,8 +843,12 @@ __device__ __noinline__ int det_outcome_warp_ool(const uint32_t *__restrict__ rm
 // product, at least SUPCAP 16-bit support entries
 __host__ __device__ constexpr uint32_t det_smem_words(uint32_t H) { return 2 * H > SUPCAP / 2 ? 2 * H : SUPCAP / 2; }
 
-__global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_t layer) {
+// layer | DET_SKIPPED: the layer's random-measurement kernels were left out,
+// the circuit having shown that it has no random op (a random op is an error)
+constexpr uint32_t DET_SKIPPED = 0x80000000u;
+__global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_t layer_arg) {
     extern __shared__ uint32_t smem[];
+    const uint32_t layer = layer_arg & ~DET_SKIPPED;
     const uint32_t H = a.P.H, CW = a.P.CW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = blockIdx.y;
@@ -880,6 +884,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_
         if (lane == 0) {
             stat[i] = MS_RANDOM;
             atomicOr(&a.tflags[t], TF_RAND_LAYER);
+            if (layer_arg & DET_SKIPPED) set_err(a.err, DERR_SKIPPED);
             a.mpiv[ci] = pv;
             a.mbsz[ci] = csize;
             a.mstale[ci] = 0;
@@ -1218,6 +1223,7 @@ __global__ void __launch_bounds__(RAND_THREADS, 1) k_meas_rand(LArgs a, uint32_t
     // k_meas_late clears it), so all ranks leave together or none does (no
     // rank may leave while others can still reach rank 0's shared memory)
     if (!(a.tflags[t] & TF_RAND_LAYER)) return;
+    if (gtid == 0) a.P.layer_rand[layer] = 1;    // the layer has a random op (for the host's skip list)
     cl.sync();                         // every rank has started: rank 0's shared memory is reachable
     unsigned char *const sm = lead ? smraw : static_cast<unsigned char *>(cl.map_shared_rank((void *)smraw, 0));
     RandShared *const S = reinterpret_cast<RandShared *>(sm + Lo.sh);
@@ -2319,7 +2325,7 @@ void set_wave_caps(const WaveCaps &c) {
 
 static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, int *d_err,
                                  const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
-                                 unsigned long long *d_stats);
+                                 unsigned long long *d_stats, const uint8_t *skip);
 
 int graph_slot_init(GraphSlot &g) {
     if (g.gs) return 0;
@@ -2425,10 +2431,64 @@ static cudaError_t launch_meas_rand(const LArgs &a, uint32_t layer, uint32_t cou
     return cudaLaunchKernelEx(&cfg, k_meas_rand, a, layer);
 }
 
+static cudaError_t layered_run_seq(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
+                                   unsigned long long *record, size_t rec_stride, int *d_err,
+                                   const LaunchCfg &lc0, cudaStream_t s, KernelProf *kp,
+                                   unsigned long long *d_stats, GraphSlot *gsl, const uint8_t *skip);
+
+// A run of the program on the batch; `fresh`: the batch holds |0...0> tableaux
+// (the runs whose random layers the circuit fixes, see HostProg::rand_learn).
 cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
                         unsigned long long *record, size_t rec_stride, int *d_err,
                         const LaunchCfg &lc0, cudaStream_t s, KernelProf *kp,
-                        unsigned long long *d_stats, GraphSlot *gsl) {
+                        unsigned long long *d_stats, GraphSlot *gsl, bool fresh) {
+    HostProg &hp = const_cast<HostProg &>(p);
+    const bool learn = fresh && hp.rand_learn;
+    const uint32_t nl = (uint32_t)p.layers.size();
+    if (learn && hp.rand_state == 1) {
+        // the marks of an earlier run, once its read-back has landed
+        const cudaError_t q = cudaEventQuery(hp.rand_ev);
+        if (q == cudaSuccess) {
+            int derr = 0;
+            memcpy(&derr, hp.rand_host + nl, sizeof derr);
+            if (derr == DERR_NONE) {
+                hp.rand_skip.assign(nl, 0);
+                for (uint32_t l = 0; l < nl; l++)
+                    hp.rand_skip[l] = p.layers[l].type == LT_MEAS && !hp.rand_host[l];
+                hp.rand_state = 2;
+            } else {
+                hp.rand_state = 0;       // learn again from a run without device errors
+            }
+        } else {
+            cudaGetLastError();          // (not ready yet: clear the status)
+        }
+    }
+    const uint8_t *skip = learn && hp.rand_state == 2 ? hp.rand_skip.data() : nullptr;
+    cudaError_t e = layered_run_seq(p, b, ms, st, record, rec_stride, d_err, lc0, s, kp, d_stats, gsl, skip);
+    if (!e && learn && hp.rand_state == 0) {
+        // queue the read-back of this run's marks and of the device error flag
+        if (!hp.rand_host && cudaMallocHost(&hp.rand_host, nl + sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            hp.rand_host = nullptr;
+            return cudaSuccess;          // (no learning without the pinned buffer)
+        }
+        if (!hp.rand_ev && cudaEventCreateWithFlags(&hp.rand_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            hp.rand_ev = nullptr;
+            return cudaSuccess;
+        }
+        e = cudaMemcpyAsync(hp.rand_host, p.dev.layer_rand, nl, cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(hp.rand_host + nl, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaEventRecord(hp.rand_ev, s);
+        if (!e) hp.rand_state = 1;
+    }
+    return e;
+}
+
+static cudaError_t layered_run_seq(const HostProg &p, Batch &b, MeasScratch &ms, const DevStreams &st,
+                                   unsigned long long *record, size_t rec_stride, int *d_err,
+                                   const LaunchCfg &lc0, cudaStream_t s, KernelProf *kp,
+                                   unsigned long long *d_stats, GraphSlot *gsl, const uint8_t *skip) {
     {
         const int lim = (int)(lc0.smem_optin - 1024);
         smem_attr_once(0, (const void *)k_gate_run<true>, lim);
@@ -2448,20 +2508,21 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
     cudaError_t e = cudaMemcpyAsync(ms.call, &ca, sizeof ca, cudaMemcpyHostToDevice, s);
     if (e) return e;
     if (!gsl || !gsl->gs || (kp && kp->mask) || graph_nodes(p) > GRAPH_MAX_NODES)
-        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
+        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats, skip);
     // Graph replay on the slot's stream, after the work already queued on s.
     // The captured sequence depends only on the kernel arguments (per-call
     // inputs excluded) and on whether the row-packed copy is valid on entry.
     HostProg &hp = const_cast<HostProg &>(p);
     LArgs ka = make_args(&p, b, &ms, d_err);
     ka.stats = nullptr;                  // (this path runs only with profiling off)
-    std::vector<unsigned char> key(sizeof(LArgs) + 2);
+    std::vector<unsigned char> key(sizeof(LArgs) + 3);
     memcpy(key.data(), &ka, sizeof ka);
     key[sizeof ka] = b.rm_valid ? 1 : 0;
     key[sizeof ka + 1] = (unsigned char)lc.rand_cluster;
+    key[sizeof ka + 2] = skip ? 1 : 0;
     if (!hp.gdone && cudaEventCreateWithFlags(&hp.gdone, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats);
+        return layered_issue(p, b, ms, d_err, lc, s, kp, d_stats, skip);
     }
     e = cudaEventRecord(gsl->in, s);
     if (!e) e = cudaStreamWaitEvent(gsl->gs, gsl->in, 0);
@@ -2475,13 +2536,13 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
         if (e) {
             // no capture on this stream: run the launches plainly on it instead
             cudaGetLastError();
-            e = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats);
+            e = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats, skip);
             if (!e) e = cudaEventRecord(gsl->out, gsl->gs);
             if (!e) e = cudaStreamWaitEvent(s, gsl->out, 0);
             return e;
         }
         const unsigned long long n0 = kp ? kp->launches : 0;
-        const cudaError_t ei = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats);
+        const cudaError_t ei = layered_issue(p, b, ms, d_err, lc, gsl->gs, kp, d_stats, skip);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(gsl->gs, &g);
         if (ei || ec) {
@@ -2521,7 +2582,7 @@ cudaError_t layered_run(const HostProg &p, Batch &b, MeasScratch &ms, const DevS
 
 static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, int *d_err,
                                  const LaunchCfg &lc, cudaStream_t s, KernelProf *kp,
-                                 unsigned long long *d_stats) {
+                                 unsigned long long *d_stats, const uint8_t *skip) {
     LArgs a = make_args(&p, b, &ms, d_err);
     a.stats = (kp && kp->mask) ? d_stats : nullptr;     // counters only while profiling
     const size_t rsm = rand_smem(b.n, b.H);
@@ -2571,19 +2632,21 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
                                 2 * GATHER_ITEMS, 0, s>>>(a, l);
             });
             const uint32_t nb = (L.count + DET_WARPS - 1) / DET_WARPS;
+            const bool skipped = skip && skip[l];
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
-                k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * det_smem_words(b.H) * 4, s>>>(a, l);
+                k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * det_smem_words(b.H) * 4, s>>>(
+                    a, skipped ? l | DET_SKIPPED : l);
             });
             const uint32_t fixed = 4u * (uint32_t)lc.sm_count;
-            launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
+            if (!skipped) launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
                 const unsigned long long pairs = (unsigned long long)b.H * b.count;
                 k_destab_to_rm<<<(uint32_t)std::min<unsigned long long>(pairs, fixed), 256, 0, s>>>(a);
             });
             cudaError_t er = cudaSuccess;
-            launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
-                   [&] { er = launch_meas_rand(a, l, b.count, lc.rand_cluster, rsm, s); });
+            if (!skipped) launch(kp, STAB_KERNEL_MEAS_RAND, s, 0.0,
+                                 [&] { er = launch_meas_rand(a, l, b.count, lc.rand_cluster, rsm, s); });
             if (er != cudaSuccess) return er;
-            launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
+            if (!skipped) launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 const unsigned long long ctas = ((unsigned long long)L.count * b.count + DET_WARPS - 1) / DET_WARPS;
                 k_meas_late<<<(uint32_t)std::min<unsigned long long>(ctas, 2ull * fixed), DET_WARPS * 32,
                               (size_t)DET_WARPS * 2 * b.H * 4, s>>>(a, l);

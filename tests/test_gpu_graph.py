@@ -130,11 +130,13 @@ def test_graph_replay_many_measurement_layers(sim):
     """A one-tableau program of 21 measurement layers (a d = 5 memory circuit
     with 20 syndrome rounds), noiseless (later rounds have deterministic
     outcomes only) and noisy: graph replay gives the records of plain
-    launches and of the oracle, with the same number of kernel launches."""
+    launches and of the oracle, with the same number of kernel launches
+    (after a first run that finds the layers without random outcomes)."""
     for p in (0.0, 5e-3):
         circ = C.surface_code_memory(5, rounds=20, p=p)
         cid = sim.compile(circ)
         coins, noise = S.streams_for(circ, 17, [0])
+        _run(sim, cid, circ, coins, noise, profiled=False)
         B.stab_launch_count(sim.ctx, reset=True)
         plain = _run(sim, cid, circ, coins, noise, profiled=True)
         n_plain = B.stab_launch_count(sim.ctx, reset=True)
@@ -145,3 +147,54 @@ def test_graph_replay_many_measurement_layers(sim):
             assert n_graph == n_plain, (n_plain, n_graph)
         want, _ = oracle.sample(circ, coins, noise)
         assert np.array_equal(plain, want), p
+
+
+def test_deterministic_layers_leave_out_random_kernels(sim):
+    """Which Z measurements are random is fixed by the circuit from |0...0>
+    (Pauli noise, outcomes and reset corrections change signs only): after
+    the first run of a program the engine leaves out the random-measurement
+    launches of the layers that had no random op, and every run, before and
+    after, gives the oracle's records on fresh streams.  A circuit with
+    RESET_ERROR (a reset drawn by noise) keeps every launch."""
+    circ = C.surface_code_memory(5, rounds=20, p=5e-3)
+    cid = sim.compile(circ)
+    counts = []
+    for rep in range(4):
+        coins, noise = S.streams_for(circ, 300 + rep, range(3))
+        B.stab_launch_count(sim.ctx, reset=True)
+        got = _run(sim, cid, circ, coins, noise, profiled=rep == 3)
+        counts.append(B.stab_launch_count(sim.ctx, reset=True))
+        want, _ = oracle.sample(circ, coins, noise)
+        assert np.array_equal(got, want), rep
+    # two measurement layers have random ops (the first round's, whose X-type
+    # ancillas are random, and the final data layer): every other one runs
+    # 3 launches fewer
+    n_ml = sim.info(cid)["n_meas_layers"]
+    assert counts[0] - counts[1] == (n_ml - 2) * 3, (counts, n_ml)
+    assert counts[1] == counts[2] == counts[3], counts
+
+    # a qubit in |+> then RESET_ERROR: its measurement is random or not by the
+    # reset's own draw, so no layer may be left out
+    b = C.Builder(6)
+    rng = np.random.default_rng(1)
+    for _ in range(30):
+        for q in range(6):
+            b.gate1(C.H, q)
+        for q in range(6):
+            b.reset_error(q, 0.5, 0.1)
+        for q in range(0, 6, 2):
+            b.gate2(C.CX, q, q + 1)
+        for q in range(6):
+            if rng.integers(2):
+                b.measure(q)
+    circ = b.build()
+    cid = sim.compile(circ)
+    counts = []
+    for rep in range(3):
+        coins, noise = S.streams_for(circ, 400 + rep, range(3))
+        B.stab_launch_count(sim.ctx, reset=True)
+        got = _run(sim, cid, circ, coins, noise, profiled=False)
+        counts.append(B.stab_launch_count(sim.ctx, reset=True))
+        want, _ = oracle.sample(circ, coins, noise)
+        assert np.array_equal(got, want), rep
+    assert counts[0] == counts[1] == counts[2], counts
