@@ -507,7 +507,6 @@ int stab_sync(stab_ctx *ctx) {
         const char *what = flag == DERR_ODD_PHASE ? "odd power of i in a stabilizer product"
                          : flag == DERR_BAD_PRODUCT ? "deterministic product is not +-Z_a"
                          : flag == DERR_TIMEOUT ? "bounded device wait expired"
-                         : flag == DERR_SKIPPED ? "random outcome in a measurement layer run as deterministic"
                          : "device bounds check failed";
         return fail(flag == DERR_TIMEOUT ? STAB_ERR_TIMEOUT : STAB_ERR_INTERNAL,
                     std::string("device consistency check: ") + what);

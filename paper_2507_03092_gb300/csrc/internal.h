@@ -150,7 +150,8 @@ struct HostProg {
     // marks each layer that has a random op (dev.layer_rand); after a run
     // from |0...0> without device errors the host reads the marks once, and
     // later such runs leave out the random-measurement launches of unmarked
-    // layers.  k_meas_det reports an error if one of those finds a random op.
+    // layers (and the stabilizer half of their measured columns, see
+    // DET_SKIPPED; a random op there fails k_meas_det's product check).
     bool rand_learn = false;            // the circuit allows it (no RESET_ERROR)
     int rand_state = 0;                 // 0 unknown, 1 read-back queued, 2 known
     cudaEvent_t rand_ev = nullptr;
@@ -350,6 +351,6 @@ enum : int { DC_WAVES = 0, DC_WAVE_OPS = 1, DC_DET_NOW = 2, DC_DET = 3, DC_SUM_K
 
 // device error flag values
 enum : int { DERR_NONE = 0, DERR_ODD_PHASE = 1, DERR_BAD_PRODUCT = 2, DERR_TIMEOUT = 3,
-             DERR_BOUNDS = 4, DERR_SKIPPED = 5 };
+             DERR_BOUNDS = 4 };
 
 }  // namespace stab

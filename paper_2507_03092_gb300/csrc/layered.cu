@@ -53,6 +53,13 @@ namespace cg = cooperative_groups;
 namespace stab {
 
 enum : uint8_t { MS_DONE = 0, MS_RANDOM = 1, MS_SKIP = 2, MS_WAVE = 3, MS_DETLATE = 4 };
+// layer | DET_SKIPPED (k_gather_cols, k_meas_det): the circuit has shown that
+// the layer has no random op, so its random-measurement kernels are left out
+// and only the destabilizer half of each measured column is gathered and
+// scanned: its set rows name the stabilizers whose product is +-Z_a.  Were
+// an op random after all, that product would not be +-Z_a (Z_a would not be
+// in the stabilizer group), which the product check reports.
+constexpr uint32_t DET_SKIPPED = 0x80000000u;
 // MS_DETLATE: an op that was random when the layer started but became
 // deterministic after earlier random ops of the layer.  Its outcome does not
 // change under the layer's remaining Z measurements, so k_meas_late resolves
@@ -531,14 +538,16 @@ __global__ void k_rm_to_qm(LArgs a) {
 // the row-packed one for dirty slices) and storing them as one 16-byte half
 // of the item's 32-byte segment, so a warp's stores fill whole sectors.
 constexpr uint32_t GATHER_ITEMS = 128;
-__global__ void __launch_bounds__(2 * GATHER_ITEMS) k_gather_cols(LArgs a, uint32_t layer) {
+__global__ void __launch_bounds__(2 * GATHER_ITEMS) k_gather_cols(LArgs a, uint32_t layer_arg) {
     const uint32_t n = a.P.n, CW = a.P.CW;
+    const uint32_t layer = layer_arg & ~DET_SKIPPED;
+    const uint32_t wl = (layer_arg & DET_SKIPPED) ? a.P.H : CW;    // words gathered
     const uint32_t t = blockIdx.z;
     const Layer M = a.P.layers[layer];
     const uint32_t i = blockIdx.y * GATHER_ITEMS + (threadIdx.x >> 1);
     if (i >= M.count) return;
     const uint32_t w0 = 8 * blockIdx.x + 4 * (threadIdx.x & 1);
-    if (w0 >= CW) return;
+    if (w0 >= wl) return;
     const uint32_t q = a.P.mitems[M.first + i].q;
     const uint8_t *dirty = a.dirty + (size_t)t * CW;
     const uint32_t *qx = a.qm + t * a.qm_stride;
@@ -548,14 +557,14 @@ __global__ void __launch_bounds__(2 * GATHER_ITEMS) k_gather_cols(LArgs a, uint3
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const uint32_t w = w0 + k;
-        v[k] = w >= CW ? 0u : dirty[w] ? rm_col_word(rm, a.RS, a.Hr, w, q, false) : qx[(size_t)w * n + q];
+        v[k] = w >= wl ? 0u : dirty[w] ? rm_col_word(rm, a.RS, a.Hr, w, q, false) : qx[(size_t)w * n + q];
     }
-    if ((CW & 3u) == 0 && ((uintptr_t)col & 15u) == 0) {
+    if ((CW & 3u) == 0 && ((uintptr_t)col & 15u) == 0 && w0 + 4 <= wl) {
         *reinterpret_cast<uint4 *>(col + w0) = make_uint4(v[0], v[1], v[2], v[3]);
     } else {
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (w0 + k < CW) col[w0 + k] = v[k];
+            if (w0 + k < wl) col[w0 + k] = v[k];
     }
 }
 
@@ -843,9 +852,6 @@ __device__ __noinline__ int det_outcome_warp_ool(const uint32_t *__restrict__ rm
 // product, at least SUPCAP 16-bit support entries
 __host__ __device__ constexpr uint32_t det_smem_words(uint32_t H) { return 2 * H > SUPCAP / 2 ? 2 * H : SUPCAP / 2; }
 
-// layer | DET_SKIPPED: the layer's random-measurement kernels were left out,
-// the circuit having shown that it has no random op (a random op is an error)
-constexpr uint32_t DET_SKIPPED = 0x80000000u;
 __global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_t layer_arg) {
     extern __shared__ uint32_t smem[];
     const uint32_t layer = layer_arg & ~DET_SKIPPED;
@@ -876,7 +882,7 @@ __global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_
     // the op is random)
     uint32_t pv, csize;
     const size_t ci = t * a.m_stride + i;
-    warp_column_scan<5>(col, H, CW, pv, csize, lst);
+    warp_column_scan<5>(col, H, (layer_arg & DET_SKIPPED) ? H : CW, pv, csize, lst);
     __syncwarp();
     if (pv != 0xffffffffu) {
         uint16_t *sup = a.msup + ci * SUPCAP;
@@ -884,7 +890,6 @@ __global__ void __launch_bounds__(DET_WARPS * 32, 9) k_meas_det(LArgs a, uint32_
         if (lane == 0) {
             stat[i] = MS_RANDOM;
             atomicOr(&a.tflags[t], TF_RAND_LAYER);
-            if (layer_arg & DET_SKIPPED) set_err(a.err, DERR_SKIPPED);
             a.mpiv[ci] = pv;
             a.mbsz[ci] = csize;
             a.mstale[ci] = 0;
@@ -2627,12 +2632,13 @@ static cudaError_t layered_issue(const HostProg &p, Batch &b, MeasScratch &ms, i
                        [&] { k_qm_to_rm<<<dim3(b.CW, b.count), 256, 0, s>>>(a); });
                 b.rm_valid = true;
             }
+            const bool skipped = skip && skip[l];
             launch(kp, STAB_KERNEL_OTHER, s, 0.0, [&] {
-                k_gather_cols<<<dim3((b.CW + 7) / 8, (L.count + GATHER_ITEMS - 1) / GATHER_ITEMS, b.count),
-                                2 * GATHER_ITEMS, 0, s>>>(a, l);
+                k_gather_cols<<<dim3(((skipped ? b.H : b.CW) + 7) / 8, (L.count + GATHER_ITEMS - 1) / GATHER_ITEMS,
+                                     b.count),
+                                2 * GATHER_ITEMS, 0, s>>>(a, skipped ? l | DET_SKIPPED : l);
             });
             const uint32_t nb = (L.count + DET_WARPS - 1) / DET_WARPS;
-            const bool skipped = skip && skip[l];
             launch(kp, STAB_KERNEL_MEAS_DET, s, 0.0, [&] {
                 k_meas_det<<<dim3(nb, b.count), DET_WARPS * 32, (size_t)DET_WARPS * det_smem_words(b.H) * 4, s>>>(
                     a, skipped ? l | DET_SKIPPED : l);
