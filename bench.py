@@ -41,12 +41,13 @@ METRIC = "surface-code d=71 gate+measure ops/s"
 # entry records the SHA-256 (first 16 hex digits) of the source files, and a
 # kernel whose sources changed since reports traffic null.
 NCU_TRAFFIC = {
-    "k_meas_rand": {"bytes_per_launch": 408.6e3, "src_sha": "5d6f8aa304a4d89e",
-                    "tag": "ncu capture without cache flushing, mean over the 72 launches of a d=71 step "
-                           "(12.36 MB read + 17.06 MB written)"},
-    "k_gate_run": {"bytes_per_launch": 83.30e6, "src_sha": "5d6f8aa304a4d89e",
+    "k_meas_rand": {"bytes_per_launch": 11.948e6, "src_sha": "5d8a546e25319846",
+                    "tag": "ncu capture without cache flushing, mean over the 2 launches of a d=71 step "
+                           "(9.51 MB read + 14.39 MB written; the other 70 measurement layers have no "
+                           "random op and launch no wave kernel)"},
+    "k_gate_run": {"bytes_per_launch": 64.20e6, "src_sha": "5d8a546e25319846",
                    "tag": "ncu capture without cache flushing, steady syndrome-round launch "
-                          "(20.04 MB read + 63.26 MB written, the writes mostly dirty lines evicted from L2)"},
+                          "(6.80 MB read + 57.40 MB written, the writes mostly dirty lines evicted from L2)"},
 }
 KERNEL_SOURCES = ("paper_2507_03092_gb300/csrc/layered.cu", "paper_2507_03092_gb300/csrc/device_common.cuh",
                   "paper_2507_03092_gb300/csrc/internal.h")
